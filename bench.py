@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Benchmark: batched SPHINCS+-SHA2-128f-simple signing on one GB300.
+
+Workload (one "step"): one hs_sign_batch call over 16384 random 32-byte
+messages signed by 16 seeded keys (key i mod 16), i.e. the whole hot path --
+message stage, FORS_Sign, TREE_Sign, WOTS+_Sign -- for one batch.  Inputs
+are device-resident when the timed region starts; the 280 MB of signatures
+written per step exceed L2, and L2 is additionally flushed (256 MB write)
+between timed steps, outside the timed events.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores instead (the reference arm for this workload).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "signatures/s at 128f/192f/256f on 1 GB300; % integer-pipe peak; p99 sign latency"
+WORKLOAD = "SPHINCS+-SHA2-128f-simple, 16 keys, 16384 x 32 B messages, one batched call per step"
+
+# Algorithmic SHA-2 compressions per signature of each stage (after the
+# per-key PK.seed midstate), from the scheme's structure:
+#   TREE: d 2^h' leaves x len chains x 16 (PRF + 15 F), + T_len blocks per leaf, + H per tree
+#   FORS: k 2^a x 2 (PRF + F) + k (2^a - 1) H + T_k blocks
+#   WOTS: d len PRF + expected digit sum (7.5 per chain) F
+# and the idealised integer instructions per compression (rounds 14 ops,
+# schedule 10 ops per word, feed-forward 8): 1384 per SHA-256 block; a
+# SHA-512 block on 32-bit lanes ~4000.
+OPS_C256 = 1384
+OPS_C512 = 4000
+STAGE_WORK = {
+    # set: {stage: (c256, c512)}
+    "128f": {"tree": (22 * 8 * 35 * 16 + 22 * 8 * 10 + 22 * 7, 0),
+             "fors": (33 * 64 * 2 + 33 * 63 + 9, 0),
+             "wots": (22 * 35 * (1 + 7.5), 0)},
+    "192f": {"tree": (22 * 8 * 51 * 16, 22 * 8 * 10 + 22 * 7),
+             "fors": (33 * 256 * 2, 33 * 255 + 7),
+             "wots": (22 * 51 * (1 + 7.5), 0)},
+    "256f": {"tree": (17 * 16 * 67 * 16, 17 * 16 * 18 + 17 * 15),
+             "fors": (35 * 512 * 2, 35 * 511 + 10),
+             "wots": (17 * 67 * (1 + 7.5), 0)},
+}
+
+
+def ops_per_sig(ps, stage):
+    c256, c512 = STAGE_WORK[ps][stage]
+    return c256 * OPS_C256 + c512 * OPS_C512
+
+
+def int_peak_tops(sm_count, sm_mhz):
+    """Integer issue peak: every SM issues one warp instruction per cycle on
+    each of its 4 sub-partitions, 32 lanes wide -> SMs x 128 lane-ops/clk."""
+    return sm_count * 4 * 32 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_rate(ps, sks, wl, seconds, idx_start=0):
+    """Sign messages of the workload with the CPU oracle on every host core
+    (ctypes releases the GIL) until 'seconds' have passed; return
+    (sig/s, signatures done, cores)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    done = [0]
+    stop = time.perf_counter() + seconds
+    lock = threading.Lock()
+
+    def worker(tid):
+        i = idx_start + tid
+        n = 0
+        while time.perf_counter() < stop:
+            m = i % wl.count
+            O.sign(ps, sks[int(wl.key_idx[m])], wl.message(m))
+            n += 1
+            i += cores
+        with lock:
+            done[0] += n
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(worker, range(cores)))
+    dt = time.perf_counter() - t0
+    return done[0] / dt, done[0], cores
+
+
+def oracle_keys(ps, seeds):
+    from oracle import oracle as O
+    return [O.keygen(ps, bytes(s))[1] for s in seeds]
+
+
+# ------------------------------------------------------------------ arms
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """CPU oracle arm: bounded oracle signing per step on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2512_23969_gb300 import inputs
+    wl = inputs.config(1)
+    sks = oracle_keys("128f", wl.seeds)
+    per_step = max(1.0, args.ref_step_seconds)
+    for _ in range(args.warmup):
+        oracle_rate("128f", sks, wl, 0.5)
+    rates, total = [], 0
+    for k in range(args.steps):
+        r, n, cores = oracle_rate("128f", sks, wl, per_step, idx_start=k * 977)
+        rates.append(r)
+        total += n
+    value = sum(rates) / len(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "signatures/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(per_step * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "params": "128f", "global_batch": 16384, "msg_bytes": 32,
+                   "keys": 16, "parallelism": "none (CPU oracle)"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "signatures/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d signatures of the workload (messages i mod 16384, keys i mod 16), "
+                                   "%.0f s per step on all host cores" % (total, per_step)},
+        "e2e": {"value": round(value, 3), "unit": "signatures/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_own(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2512_23969_gb300 import build as hs_build
+    hs_build.build()
+    from paper_2512_23969_gb300 import hs, inputs
+    hs.load()
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+
+    ps = args.params
+    if ps == "128f" and args.count == 16384:
+        wl = inputs.config(1)
+    else:
+        wl = inputs.make(ps, args.count, 16, 32, inputs.BASE_SEED + 1, "%s-16keys-%dx32B" % (ps, args.count))
+    count = wl.count
+    S = hs.sig_bytes(ps)
+    stream = torch.cuda.current_stream()
+    seeds = torch.from_numpy(wl.seeds).cuda()
+    pk, sk = hs.hs_keygen(ps, seeds)
+    msgs = torch.from_numpy(wl.msgs).cuda()
+    lens = torch.from_numpy(wl.lens).cuda()
+    kidx = torch.from_numpy(wl.key_idx).cuda()
+    sigs = torch.empty(count * S, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        hs.hs_sign_batch(ps, sk, msgs, lens, key_idx=kidx, sigs=sigs, num_keys=wl.num_keys, stream=stream)
+
+    hs.hs_profile_enable(True)
+    for i in range(args.warmup):
+        flush.fill_(i & 0xFF)
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, stage_ms = [], {}
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_((k + 7) & 0xFF)          # L2 flush, outside the timed events
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+        evs[k][1].synchronize()
+        for name, v in hs.hs_profile_read().items():
+            stage_ms.setdefault(name, []).append(v)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    for a, b in evs:
+        step_ms.append(a.elapsed_time(b))
+    hs.hs_profile_enable(False)
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * count * args.steps / (total_ms / 1e3)
+
+    # correctness guard on the timed output: GPU verify of every signature
+    ok = hs.hs_verify_batch(ps, pk, msgs, lens, sigs.view(count, S), key_idx=kidx, num_keys=wl.num_keys)
+    n_ok = int(ok.sum().item())
+
+    # end to end through the C ABI with pinned host buffers (copies inside the call)
+    e2e = None
+    if args.e2e_steps > 0:
+        sk_h = sk.cpu().pin_memory()
+        msgs_h = torch.from_numpy(wl.msgs).pin_memory()
+        lens_h = torch.from_numpy(wl.lens).pin_memory()
+        kidx_h = torch.from_numpy(wl.key_idx).pin_memory()
+        sigs_h = torch.empty(count * S, dtype=torch.uint8).pin_memory()
+        hs.hs_sign_batch(ps, sk_h, msgs_h, lens_h, key_idx=kidx_h, sigs=sigs_h, num_keys=wl.num_keys)
+        e2e_t = []
+        for k in range(args.e2e_steps):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hs.hs_sign_batch(ps, sk_h, msgs_h, lens_h, key_idx=kidx_h, sigs=sigs_h, num_keys=wl.num_keys)
+            e2e_t.append(time.perf_counter() - t0)
+        h2d = sk_h.numel() + msgs_h.numel() + lens_h.numel() * 8 + kidx_h.numel() * 4
+        e2e = {"value": round(count / (sum(e2e_t) / len(e2e_t)), 1), "unit": "signatures/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(sigs_h.numel()),
+               "path": "hs_sign_batch with pinned host buffers (staged H2D, kernels, D2H, stream sync)"}
+        if not torch.equal(sigs_h, sigs.cpu()):
+            e2e["mismatch"] = True
+
+    # roofline of the dominant kernel (TREE_Sign), from its CUDA-event durations
+    tree_ms = sum(stage_ms.get("tree", [0])) / max(1, len(stage_ms.get("tree", [1])))
+    stage_avg = {k: round(sum(v) / len(v), 3) for k, v in stage_ms.items()}
+    sm_mhz_peak = 2070.0
+    peak = int_peak_tops(sm_count, sm_mhz_peak)
+    achieved = ops_per_sig(ps, "tree") * count / (tree_ms / 1e3) / 1e12 if tree_ms > 0 else None
+    traffic = None
+    prof_file = os.path.join(ROOT, "profiles", "tree_%s_traffic.json" % ps)
+    if os.path.exists(prof_file):
+        try:
+            traffic = json.load(open(prof_file)).get("bytes_per_launch_scaled")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "kernel": "tree_kernel<%s> (TREE_Sign)" % ps,
+                "achieved": round(achieved, 3) if achieved else None, "peak": round(peak, 3),
+                "unit": "Tops/s", "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,
+                "peak_basis": "issue peak %d SMs x 128 int lanes/clk x %.0f MHz (max SM clock)" % (sm_count, sm_mhz_peak),
+                "ops_per_launch": ops_per_sig(ps, "tree") * count}
+    if clk.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = round(achieved / int_peak_tops(sm_count, clk["sm_mhz"]), 4) \
+            if achieved else None
+
+    # CPU oracle baseline on a bounded sample
+    cpu = None
+    if rank == 0 and args.cpu_seconds > 0:
+        sks = oracle_keys(ps, wl.seeds)
+        r, n, cores = oracle_rate(ps, sks, wl, args.cpu_seconds)
+        cpu = {"value": round(r, 3), "unit": "signatures/s", "cores": cores, "kind": "oracle",
+               "sample": "%d signatures of this workload (messages i mod 16384) in %.0f s on %d host threads"
+                         % (n, args.cpu_seconds, cores)}
+
+    ms_sorted = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "signatures/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if (ps == "128f" and count == 16384) else wl.name, "params": ps,
+                   "global_batch": count * ws, "msg_bytes": 32,
+                   "keys": 16, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "flushed between timed steps (256 MB write, outside the events); outputs 280 MB > L2"},
+        "e2e": e2e,
+        "gpu_launches": hs.hs_sign_kernel_count() * args.steps,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "stage_ms": stage_avg,
+        "batch_latency_ms": {"p50": round(ms_sorted[len(ms_sorted) // 2], 3), "max": round(ms_sorted[-1], 3)},
+        "verified": "%d/%d signatures accepted by GPU verify" % (n_ok, count),
+        "wall_s": round(wall, 3),
+        "device": props.name, "sm_count": sm_count,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=10.0)
+    ap.add_argument("--params", choices=["128f", "192f", "256f"], default="128f",
+                    help="parameter set (the default workload is 128f)")
+    ap.add_argument("--count", type=int, default=16384,
+                    help="messages per step (smaller counts are for profiler captures)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "own":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_own(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

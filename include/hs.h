@@ -1,0 +1,144 @@
+/*
+ * hs.h -- C ABI of the GB300-native batched SPHINCS+ signer (libhs.so).
+ *
+ * Scheme: SPHINCS+ round 3.1, SHA2 "simple" instantiation, at the -f
+ * parameter sets of Table 1 of HERO-Sign (arxiv 2512.23969):
+ *   128f (n=16, h=66, d=22, h'=3, a=6, k=33)  17088-byte signatures
+ *   192f (n=24, h=66, d=22, h'=3, a=8, k=33)  35664-byte signatures
+ *   256f (n=32, h=68, d=17, h'=4, a=9, k=35)  49856-byte signatures
+ * F and PRF use SHA-256; H, T_l, H_msg and PRF_msg use SHA-256 at n=16 and
+ * SHA-512 at n=24/32.  Signing is deterministic (opt_rand = PK.seed).
+ * Signing follows the paper's decomposition (Sec. III, Fig. 2): a message
+ * stage (R and digest), FORS_Sign (Sec. III-B), TREE_Sign (Sec. III-A) and
+ * WOTS+_Sign, all as sm_103a kernels; nothing runs on the CPU.
+ *
+ * Conventions shared by every call:
+ *  - Byte strings are packed, unpadded uint8_t arrays.  Keys, messages and
+ *    signatures are laid out contiguously in index order.
+ *  - Every buffer is owned by the caller and must stay valid until the work
+ *    enqueued on 'stream' has completed.  The library keeps no pointer
+ *    after a call returns.
+ *  - 'stream' is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls whose buffers are all device memory are asynchronous:
+ *    they enqueue kernels on 'stream' and return HS_OK once the launches
+ *    succeeded.  If any input or output buffer is host memory (pageable or
+ *    pinned), the call stages it through device memory and synchronizes
+ *    'stream' before returning, so host outputs are ready on return.
+ *  - Argument errors are detected on the host and returned synchronously;
+ *    nothing is enqueued in that case.  Errors found by the kernels (a key
+ *    index out of range) are OR-ed into a per-device status word that
+ *    hs_check_status() reads.  No call traps, asserts or aborts.
+ *  - count == 0 is a valid no-op.
+ *  - Scratch memory is taken from the device's stream-ordered memory pool
+ *    (cudaMallocAsync on 'stream') and returned to it on the same stream.
+ */
+#ifndef HS_H_
+#define HS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Parameter sets.  HS_TOY is a test-only miniature (n=16, h=4, d=2, h'=2,
+ * a=3, k=4, 1456-byte signatures) with no security; it exists so that every
+ * tree of the hypertree can be brute-forced in tests. */
+typedef enum { HS_128F = 0, HS_192F = 1, HS_256F = 2, HS_TOY = 3 } hs_params;
+
+typedef enum {
+    HS_OK = 0,
+    HS_EINVAL = 1,   /* bad enum, NULL pointer, size overflow, mixed buffer kinds */
+    HS_ENOMEM = 2,   /* device memory for scratch or staging could not be obtained */
+    HS_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    HS_ETIMEOUT = 4, /* reserved for bounded device waits */
+    HS_EKEY = 5      /* status word: a key_idx entry was >= num_keys */
+} hs_status;
+
+/* Sizes in bytes for a parameter set; 0 for an invalid enum.
+ * seed = SK.seed || SK.prf || PK.seed (3n); pk = PK.seed || PK.root (2n);
+ * sk = SK.seed || SK.prf || PK.seed || PK.root (4n). */
+size_t hs_sig_bytes(hs_params p);
+size_t hs_pk_bytes(hs_params p);
+size_t hs_sk_bytes(hs_params p);
+size_t hs_seed_bytes(hs_params p);
+
+/*
+ * hs_keygen -- derive 'count' key pairs from 'count' seeds.
+ * Definition: PK.root is the root of the single XMSS tree of the top
+ * hypertree layer d-1 (tree 0), built from WOTS+ public keys (Sec. II-A-3/4).
+ *   seeds : count x 3n bytes (SK.seed || SK.prf || PK.seed), host or device
+ *   pk    : count x 2n bytes out, host or device
+ *   sk    : count x 4n bytes out, host or device
+ * Errors: HS_EINVAL for a bad enum or a NULL pointer with count > 0.
+ */
+hs_status hs_keygen(hs_params p, const uint8_t *seeds, uint32_t count,
+                    uint8_t *pk, uint8_t *sk, void *stream);
+
+/*
+ * hs_sign_batch -- sign 'count' messages (paper Fig. 2 per message:
+ * hash_message, message_to_indices, fors_sign, d x merkle_sign).
+ *   sk      : num_keys x 4n bytes (hs_keygen's sk layout)
+ *   key_idx : count x uint32, key of each message; NULL = key 0 for all
+ *   msgs    : all messages concatenated in order (sum(lens) bytes; may be
+ *             NULL when every length is 0)
+ *   lens    : count x uint64 message lengths in bytes
+ *   sigs    : count x hs_sig_bytes(p) bytes out; signature i at i*SIG
+ * Message i starts at the sum of lens[0..i-1]; the offsets are computed on
+ * the device.  If msgs is host memory, lens must be host memory too (its
+ * total sizes the staging copy).
+ * Errors: HS_EINVAL (bad enum, NULL sk/lens/sigs with count > 0,
+ * num_keys == 0), HS_ENOMEM, HS_ECUDA.  A key_idx entry >= num_keys sets
+ * HS_EKEY in the status word; that message's signature bytes are zero.
+ */
+hs_status hs_sign_batch(hs_params p, const uint8_t *sk, uint32_t num_keys,
+                        const uint32_t *key_idx, const uint8_t *msgs,
+                        const uint64_t *lens, uint32_t count, uint8_t *sigs,
+                        void *stream);
+
+/*
+ * hs_verify_batch -- verify 'count' signatures (the scheme's verification:
+ * FORS public key from the FORS signature, then d WOTS+ public keys from
+ * their signatures and auth-path climbs, compared with PK.root).
+ *   pk      : num_keys x 2n bytes (PK.seed || PK.root)
+ *   key_idx : count x uint32 or NULL (key 0)
+ *   msgs, lens : as in hs_sign_batch
+ *   sigs    : count x hs_sig_bytes(p)
+ *   ok      : count bytes out; 1 = valid, 0 = invalid (not an error)
+ * Errors: as hs_sign_batch; an out-of-range key gives ok = 0 and HS_EKEY.
+ */
+hs_status hs_verify_batch(hs_params p, const uint8_t *pk, uint32_t num_keys,
+                          const uint32_t *key_idx, const uint8_t *msgs,
+                          const uint64_t *lens, const uint8_t *sigs,
+                          uint32_t count, uint8_t *ok, void *stream);
+
+/*
+ * hs_check_status -- synchronize 'stream', then return and clear the status
+ * word of the current device (an OR of (1u << hs_status) bits raised by
+ * kernels since the last check).  *flags may be NULL.
+ */
+hs_status hs_check_status(void *stream, uint32_t *flags);
+
+/* Text of the most recent host-side error of the calling thread. */
+const char *hs_last_error(void);
+
+/*
+ * Per-stage timing for measurement.  While enabled, every hs_sign_batch call
+ * records CUDA events around each of its kernels on its own stream.
+ * hs_profile_read synchronizes those events and writes, for the most recent
+ * call, up to 'max' stage durations in milliseconds into ms[] and their
+ * names (static strings) into names[] (either may be NULL); it returns the
+ * number of stages, or -1 if no profiled call has happened.
+ * Stages: 0 keyprep, 1 offsets, 2 message, 3 fors, 4 fors_pk, 5 tree, 6 wots.
+ */
+void hs_profile_enable(int on);
+int hs_profile_read(float *ms, const char **names, int max);
+
+/* Number of kernels one hs_sign_batch call launches (for launch accounting). */
+int hs_sign_kernel_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HS_H_ */

@@ -1,0 +1,373 @@
+// hs_api.cu -- the C ABI of include/hs.h: argument checks, host-buffer
+// staging, stream-ordered scratch, and the per-call kernel sequence
+//   keyprep -> offsets -> message -> FORS_Sign -> FORS pk -> TREE_Sign -> WOTS+_Sign
+// (the paper's decomposition, Sec. III and Fig. 2; FORS_Sign and TREE_Sign
+// are independent given the digest, WOTS+_Sign consumes both).
+#include <cuda_runtime.h>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include "hs_launch.h"
+#include "../../include/hs.h"
+
+#define HS_API extern "C" __attribute__((visibility("default")))
+
+namespace hs {
+
+static thread_local std::string g_err;
+
+static hs_status fail(hs_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+static hs_status fail(hs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+static hs_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct SetInfo { int n, d, k, len, sig; };
+static bool set_info(int p, SetInfo* s) {
+    switch (p) {
+    case 0: *s = {P128f::N, P128f::D, P128f::K, P128f::LEN, P128f::SIG_BYTES}; return true;
+    case 1: *s = {P192f::N, P192f::D, P192f::K, P192f::LEN, P192f::SIG_BYTES}; return true;
+    case 2: *s = {P256f::N, P256f::D, P256f::K, P256f::LEN, P256f::SIG_BYTES}; return true;
+    case 3: *s = {PToy::N, PToy::D, PToy::K, PToy::LEN, PToy::SIG_BYTES}; return true;
+    }
+    return false;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count) {
+    SetInfo s;
+    if (!set_info(pset, &s)) return 0;
+    const size_t nw = (size_t)s.n / 4;
+    return align256(sizeof(uint32_t)) + align256((size_t)num_keys * sizeof(KeyBlock)) +
+           align256(((size_t)count + 1) * sizeof(uint64_t)) + align256((size_t)count * sizeof(MsgInfo)) +
+           align256((size_t)count * s.k * nw * 4) + align256((size_t)count * nw * 4) +
+           align256((size_t)count * s.d * nw * 4);
+}
+
+void carve_scratch(Batch& b, void* base) {
+    SetInfo s;
+    set_info(b.pset, &s);
+    const size_t nw = (size_t)s.n / 4;
+    char* p = static_cast<char*>(base);
+    p += align256(sizeof(uint32_t));   // reserved
+    b.keys = reinterpret_cast<KeyBlock*>(p);      p += align256((size_t)b.num_keys * sizeof(KeyBlock));
+    b.offsets = reinterpret_cast<uint64_t*>(p);   p += align256(((size_t)b.count + 1) * sizeof(uint64_t));
+    b.infos = reinterpret_cast<MsgInfo*>(p);      p += align256((size_t)b.count * sizeof(MsgInfo));
+    b.fors_roots = reinterpret_cast<uint32_t*>(p); p += align256((size_t)b.count * s.k * nw * 4);
+    b.pk_fors = reinterpret_cast<uint32_t*>(p);   p += align256((size_t)b.count * nw * 4);
+    b.roots = reinterpret_cast<uint32_t*>(p);
+}
+
+// ----------------------------------------------------------- device state
+struct DevState {
+    bool init = false;
+    cudaMemPool_t pool = nullptr;
+    uint32_t* status = nullptr;
+};
+static std::mutex g_mu;
+static DevState g_dev[64];
+
+static hs_status dev_state(DevState** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(HS_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState& d = g_dev[dev];
+    if (!d.init) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&d.pool, &props);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
+        uint64_t thr = UINT64_MAX;   // keep freed blocks cached for the next call
+        e = cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolSetAttribute");
+        e = cudaMalloc(&d.status, 256);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
+        e = cudaMemset(d.status, 0, 256);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+        d.init = true;
+    }
+    *out = &d;
+    return HS_OK;
+}
+
+// 1 if p is host memory (pageable or pinned), 0 if device or managed.
+static int is_host_ptr(const void* p) {
+    if (!p) return 0;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return 1; }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 0 : 1;
+}
+
+// ----------------------------------------------------------- profiling
+static const char* kStageNames[7] = {"keyprep", "offsets", "message", "fors", "fors_pk", "tree", "wots"};
+static bool g_prof = false;
+static bool g_prof_valid = false;
+static cudaEvent_t g_ev[8];
+static bool g_ev_init = false;
+
+static void prof_mark(int k, cudaStream_t s) {
+    if (!g_prof) return;
+    if (!g_ev_init) {
+        for (int i = 0; i < 8; i++) cudaEventCreate(&g_ev[i]);
+        g_ev_init = true;
+    }
+    cudaEventRecord(g_ev[k], s);
+}
+
+// ----------------------------------------------------------- staging
+struct Staging {
+    void* base = nullptr;
+    size_t off = 0;
+    size_t cap = 0;
+    char* take(size_t n) {
+        char* p = static_cast<char*>(base) + off;
+        off += align256(n);
+        return p;
+    }
+};
+
+}  // namespace hs
+
+using namespace hs;
+
+HS_API size_t hs_sig_bytes(hs_params p) { SetInfo s; return set_info(p, &s) ? (size_t)s.sig : 0; }
+HS_API size_t hs_pk_bytes(hs_params p) { SetInfo s; return set_info(p, &s) ? (size_t)2 * s.n : 0; }
+HS_API size_t hs_sk_bytes(hs_params p) { SetInfo s; return set_info(p, &s) ? (size_t)4 * s.n : 0; }
+HS_API size_t hs_seed_bytes(hs_params p) { SetInfo s; return set_info(p, &s) ? (size_t)3 * s.n : 0; }
+HS_API const char* hs_last_error(void) { return g_err.c_str(); }
+HS_API int hs_sign_kernel_count(void) { return 7; }
+HS_API void hs_profile_enable(int on) { g_prof = on != 0; g_prof_valid = false; }
+
+HS_API int hs_profile_read(float* ms, const char** names, int max) {
+    if (!g_prof_valid) return -1;
+    int n = 0;
+    for (int k = 0; k < 7 && n < max; k++, n++) {
+        float t = 0.f;
+        if (cudaEventSynchronize(g_ev[k + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t, g_ev[k], g_ev[k + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            t = -1.f;
+        }
+        if (ms) ms[n] = t;
+        if (names) names[n] = kStageNames[k];
+    }
+    return n;
+}
+
+HS_API hs_status hs_check_status(void* stream, uint32_t* flags) {
+    DevState* d;
+    hs_status st = dev_state(&d);
+    if (st != HS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    uint32_t v = 0;
+    e = cudaMemcpy(&v, d->status, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+    e = cudaMemset(d->status, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+    if (flags) *flags = v;
+    if (v & (1u << HS_EKEY)) return fail(HS_EKEY, "a key index was out of range");
+    return HS_OK;
+}
+
+HS_API hs_status hs_keygen(hs_params p, const uint8_t* seeds, uint32_t count, uint8_t* pk, uint8_t* sk,
+                           void* stream) {
+    SetInfo si;
+    if (!set_info(p, &si)) return fail(HS_EINVAL, "invalid parameter set %d", (int)p);
+    if (count == 0) return HS_OK;
+    if (!seeds || !pk || !sk) return fail(HS_EINVAL, "NULL buffer");
+    DevState* d;
+    hs_status st = dev_state(&d);
+    if (st != HS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t nseed = (size_t)count * 3 * si.n, npk = (size_t)count * 2 * si.n, nsk = (size_t)count * 4 * si.n;
+    const int hs_ = is_host_ptr(seeds), hp = is_host_ptr(pk), hk = is_host_ptr(sk);
+    Staging sg;
+    const size_t need = (hs_ ? align256(nseed) : 0) + (hp ? align256(npk) : 0) + (hk ? align256(nsk) : 0);
+    cudaError_t e;
+    if (need) {
+        e = cudaMallocFromPoolAsync(&sg.base, need, d->pool, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(keygen staging)");
+    }
+    const uint8_t* dseeds = seeds;
+    uint8_t* dpk = pk;
+    uint8_t* dsk = sk;
+    if (hs_) {
+        uint8_t* t = reinterpret_cast<uint8_t*>(sg.take(nseed));
+        e = cudaMemcpyAsync(t, seeds, nseed, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(seeds)");
+        dseeds = t;
+    }
+    if (hp) dpk = reinterpret_cast<uint8_t*>(sg.take(npk));
+    if (hk) dsk = reinterpret_cast<uint8_t*>(sg.take(nsk));
+    e = launch_keygen(p, dseeds, count, dpk, dsk, s);
+    if (e != cudaSuccess) return cuda_fail(e, "keygen launch");
+    if (hp && (e = cudaMemcpyAsync(pk, dpk, npk, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(pk)");
+    if (hk && (e = cudaMemcpyAsync(sk, dsk, nsk, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(sk)");
+    if (need) {
+        e = cudaFreeAsync(sg.base, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+    }
+    if (hs_ || hp || hk) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    return HS_OK;
+}
+
+// Shared driver for sign (verify = false) and verify (verify = true).
+static hs_status run_batch(bool verify, hs_params p, const uint8_t* keys_in, uint32_t num_keys,
+                           const uint32_t* key_idx, const uint8_t* msgs, const uint64_t* lens,
+                           const uint8_t* sigs_in, uint8_t* sigs_out, uint32_t count, uint8_t* ok, void* stream) {
+    SetInfo si;
+    if (!set_info(p, &si)) return fail(HS_EINVAL, "invalid parameter set %d", (int)p);
+    if (count == 0) return HS_OK;
+    if (!keys_in || !lens || (!verify && !sigs_out) || (verify && (!sigs_in || !ok)))
+        return fail(HS_EINVAL, "NULL buffer");
+    if (num_keys == 0) return fail(HS_EINVAL, "num_keys must be > 0");
+    DevState* d;
+    hs_status st = dev_state(&d);
+    if (st != HS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+
+    const size_t key_bytes = (size_t)num_keys * (verify ? 2 : 4) * si.n;
+    const size_t sig_total = (size_t)count * si.sig;
+    const int h_keys = is_host_ptr(keys_in), h_idx = is_host_ptr(key_idx), h_lens = is_host_ptr(lens);
+    const int h_msgs = is_host_ptr(msgs);
+    const int h_sig = verify ? is_host_ptr(sigs_in) : is_host_ptr(sigs_out);
+    const int h_ok = verify ? is_host_ptr(ok) : 0;
+    uint64_t msg_total = 0;
+    if (h_msgs) {
+        if (!h_lens) return fail(HS_EINVAL, "msgs is host memory but lens is device memory");
+        for (uint32_t i = 0; i < count; i++) {
+            if (lens[i] > (1ull << 60) || msg_total + lens[i] < msg_total)
+                return fail(HS_EINVAL, "message length overflow at %u", i);
+            msg_total += lens[i];
+        }
+    }
+    if (!msgs) {
+        // a NULL message buffer is only valid when every length is zero,
+        // which can only be checked when the lengths are host memory
+        if (!h_lens) return fail(HS_EINVAL, "msgs is NULL and lens is device memory");
+        for (uint32_t i = 0; i < count; i++)
+            if (lens[i]) return fail(HS_EINVAL, "msgs is NULL but lens[%u] = %llu", i, (unsigned long long)lens[i]);
+    }
+
+    Batch b;
+    memset(&b, 0, sizeof(b));
+    b.pset = p;
+    b.num_keys = num_keys;
+    b.count = count;
+    b.status = d->status;
+    const size_t scratch = scratch_bytes(p, num_keys, count);
+    const size_t stage = (h_keys ? align256(key_bytes) : 0) + (h_idx ? align256((size_t)count * 4) : 0) +
+                         (h_lens ? align256((size_t)count * 8) : 0) + (h_msgs ? align256(msg_total) : 0) +
+                         (h_sig ? align256(sig_total) : 0) + (h_ok ? align256(count) : 0);
+    void* base = nullptr;
+    e = cudaMallocFromPoolAsync(&base, scratch + stage, d->pool, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(scratch)");
+    carve_scratch(b, base);
+    Staging sg;
+    sg.base = static_cast<char*>(base) + scratch;
+
+    auto h2d = [&](const void* src, size_t n, const char* what) -> const void* {
+        void* t = sg.take(n);
+        if (n) {
+            cudaError_t ee = cudaMemcpyAsync(t, src, n, cudaMemcpyHostToDevice, s);
+            if (ee != cudaSuccess) { cuda_fail(ee, what); return nullptr; }
+        }
+        return t;
+    };
+    b.keys_in = h_keys ? static_cast<const uint8_t*>(h2d(keys_in, key_bytes, "copy keys")) : keys_in;
+    b.key_idx = (key_idx && h_idx) ? static_cast<const uint32_t*>(h2d(key_idx, (size_t)count * 4, "copy key_idx")) : key_idx;
+    b.lens = h_lens ? static_cast<const uint64_t*>(h2d(lens, (size_t)count * 8, "copy lens")) : lens;
+    b.msgs = h_msgs ? static_cast<const uint8_t*>(h2d(msgs, msg_total, "copy msgs")) : msgs;
+    if (verify) {
+        b.sigs = h_sig ? const_cast<uint8_t*>(static_cast<const uint8_t*>(h2d(sigs_in, sig_total, "copy sigs")))
+                       : const_cast<uint8_t*>(sigs_in);
+        b.ok = h_ok ? reinterpret_cast<uint8_t*>(sg.take(count)) : ok;
+    } else {
+        b.sigs = h_sig ? reinterpret_cast<uint8_t*>(sg.take(sig_total)) : sigs_out;
+    }
+    if (!b.keys_in || !b.lens || (h_msgs && !b.msgs) || !b.sigs) {
+        cudaFreeAsync(base, s);
+        return HS_ECUDA;
+    }
+    if (!b.msgs) b.msgs = reinterpret_cast<const uint8_t*>(b.offsets);   // never read: all lengths 0
+
+    const bool prof = g_prof && !verify;
+    if (prof) prof_mark(0, s);
+    e = launch_keyprep(b, verify, s);
+    if (prof) prof_mark(1, s);
+    if (e == cudaSuccess) e = launch_offsets(b, s);
+    if (prof) prof_mark(2, s);
+    if (e == cudaSuccess) e = launch_message(b, verify, s);
+    if (prof) prof_mark(3, s);
+    if (!verify) {
+        if (e == cudaSuccess) e = launch_fors(b, s);
+        if (prof) prof_mark(4, s);
+        if (e == cudaSuccess) e = launch_fors_pk(b, s);
+        if (prof) prof_mark(5, s);
+        if (e == cudaSuccess) e = launch_tree(b, s);
+        if (prof) prof_mark(6, s);
+        if (e == cudaSuccess) e = launch_wots(b, s);
+        if (prof) prof_mark(7, s);
+    } else {
+        if (e == cudaSuccess) e = launch_verify(b, s);
+    }
+    if (e != cudaSuccess) {
+        cudaFreeAsync(base, s);
+        return cuda_fail(e, "kernel launch");
+    }
+    if (prof) g_prof_valid = true;
+    if (!verify && h_sig) {
+        e = cudaMemcpyAsync(sigs_out, b.sigs, sig_total, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy sigs back");
+    }
+    if (verify && h_ok) {
+        e = cudaMemcpyAsync(ok, b.ok, count, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy ok back");
+    }
+    e = cudaFreeAsync(base, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+    if (h_keys || h_idx || h_lens || h_msgs || h_sig || h_ok) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    return HS_OK;
+}
+
+HS_API hs_status hs_sign_batch(hs_params p, const uint8_t* sk, uint32_t num_keys, const uint32_t* key_idx,
+                               const uint8_t* msgs, const uint64_t* lens, uint32_t count, uint8_t* sigs,
+                               void* stream) {
+    return run_batch(false, p, sk, num_keys, key_idx, msgs, lens, nullptr, sigs, count, nullptr, stream);
+}
+
+HS_API hs_status hs_verify_batch(hs_params p, const uint8_t* pk, uint32_t num_keys, const uint32_t* key_idx,
+                                 const uint8_t* msgs, const uint64_t* lens, const uint8_t* sigs, uint32_t count,
+                                 uint8_t* ok, void* stream) {
+    return run_batch(true, p, pk, num_keys, key_idx, msgs, lens, sigs, nullptr, count, ok, stream);
+}

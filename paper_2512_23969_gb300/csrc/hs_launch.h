@@ -1,0 +1,49 @@
+// hs_launch.h -- host-side launchers of the signer's kernels (library
+// internal; the public surface is include/hs.h).  Each launcher dispatches
+// on the parameter set id (0 128f, 1 192f, 2 256f, 3 toy) to the kernel
+// template instantiated for that set.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "hs_params.cuh"
+
+namespace hs {
+
+// Device buffers of one sign or verify call.  'sk' is the caller's key
+// buffer for signing (4n bytes per key) or public keys for verifying (2n).
+struct Batch {
+    int pset;
+    const uint8_t* keys_in;   // sk (sign) or pk (verify), num_keys entries
+    uint32_t num_keys;
+    const uint32_t* key_idx;  // may be null: key 0
+    const uint8_t* msgs;
+    const uint64_t* lens;
+    uint32_t count;
+    uint8_t* sigs;            // sign: out; verify: in (const)
+    uint8_t* ok;              // verify only
+    // scratch
+    KeyBlock* keys;           // num_keys
+    uint64_t* offsets;        // count + 1
+    MsgInfo* infos;           // count
+    uint32_t* fors_roots;     // count * K * NW words
+    uint32_t* pk_fors;        // count * NW words
+    uint32_t* roots;          // count * D * NW words
+    uint32_t* status;         // per-device status word
+};
+
+// Scratch bytes for a batch (each region 256-byte aligned).
+size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count);
+void carve_scratch(Batch& b, void* base);
+
+cudaError_t launch_keyprep(const Batch& b, bool from_pk, cudaStream_t s);
+cudaError_t launch_offsets(const Batch& b, cudaStream_t s);
+cudaError_t launch_message(const Batch& b, bool verify, cudaStream_t s);
+cudaError_t launch_fors(const Batch& b, cudaStream_t s);
+cudaError_t launch_fors_pk(const Batch& b, cudaStream_t s);
+cudaError_t launch_tree(const Batch& b, cudaStream_t s);
+cudaError_t launch_wots(const Batch& b, cudaStream_t s);
+cudaError_t launch_verify(const Batch& b, cudaStream_t s);
+cudaError_t launch_keygen(int pset, const uint8_t* seeds, uint32_t count, uint8_t* pk, uint8_t* sk,
+                          cudaStream_t s);
+
+}  // namespace hs

@@ -1,0 +1,185 @@
+// k_fors.cu -- FORS_Sign (paper Sec. III-B) and the FORS public key.
+//
+// What it computes (Sec. II-A-2): for each of the k trees of height a, the
+// leaves F(FORS_TREE(0, g), PRF(FORS_PRF(g))) with g = i 2^a + j, the
+// Merkle root by H up a levels, the secret of the selected leaf idx_i and
+// its a auth nodes.  PK_FORS = T_k(FORS_ROOTS, root_0 .. root_{k-1}).
+//
+// GB300 mapping (ours, not the paper's Tree Fusion): a tree is owned by an
+// aligned group of LPT lanes of one warp.  Each lane builds a subtree of
+// height R = a - log2(LPT) over 2^R consecutive leaves with a register
+// treehash (one H call site, left siblings kept in a small select-indexed
+// stack), then the top log2(LPT) levels are merged across the group with
+// warp shuffles.  No shared memory and no block barriers; the grid is flat
+// over (message, tree, lane), so every message's k trees run in parallel.
+#include <cuda_runtime.h>
+#include "hs_common.cuh"
+#include "hs_launch.h"
+
+namespace hs {
+
+template <class P> struct ForsShape;
+template <> struct ForsShape<P128f> { static constexpr int LPT = 8; };   // R = 3
+template <> struct ForsShape<P192f> { static constexpr int LPT = 32; };  // R = 3
+template <> struct ForsShape<P256f> { static constexpr int LPT = 32; };  // R = 4
+template <> struct ForsShape<PToy>  { static constexpr int LPT = 4; };   // R = 1
+
+template <int L> struct Log2 { static constexpr int v = 1 + Log2<L / 2>::v; };
+template <> struct Log2<1> { static constexpr int v = 0; };
+
+template <class P>
+__global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ keys,
+                                                   const MsgInfo* __restrict__ infos, uint32_t count,
+                                                   uint8_t* __restrict__ sigs, uint32_t* __restrict__ fors_roots) {
+    constexpr int NW = P::NW, A = P::A, K = P::K;
+    constexpr int LPT = ForsShape<P>::LPT;
+    constexpr int R = A - Log2<LPT>::v;           // height built inside one lane
+    static_assert(R >= 1 && R <= 4, "lane subtree height");
+    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t L = gid % LPT;                  // lane within the tree group
+    const uint32_t grp = gid / LPT;                // (message, tree)
+    const uint32_t m = grp / K;
+    const uint32_t i = grp % K;
+    if (m >= count) return;                        // whole groups exit together
+    const MsgInfo& info = infos[m];
+    if (info.key == KEY_INVALID) return;
+    const unsigned gmask = (LPT == 32) ? 0xFFFFFFFFu : (((1u << LPT) - 1u) << (lane & ~(uint32_t)(LPT - 1)));
+
+    const KeyBlock& kb = keys[info.key];
+    uint32_t ms256[8], ms512[P::BIG ? 16 : 1], skseed[NW];
+#pragma unroll
+    for (int w = 0; w < 8; w++) ms256[w] = kb.ms256[w];
+    if constexpr (P::BIG) {
+#pragma unroll
+        for (int w = 0; w < 16; w++) ms512[w] = kb.ms512[w];
+    }
+#pragma unroll
+    for (int w = 0; w < NW; w++) skseed[w] = kb.sk_seed[w];
+
+    const uint64_t tree = info.idx_tree;
+    const uint32_t kp = info.idx_leaf;
+    const uint32_t gs = info.fors_idx[i];          // selected leaf in tree i
+    uint8_t* sf = sigs + (size_t)m * P::SIG_BYTES + P::N + (size_t)i * (A + 1) * P::N;
+
+    uint32_t stk[R][NW];                           // left siblings, levels 0..R-1
+    uint32_t node[NW];
+    const uint32_t base = L << R;                  // first leaf of this lane (within tree)
+#pragma unroll 1
+    for (uint32_t p = 0; p < (1u << R); p++) {
+        const uint32_t t = base + p;               // leaf index within tree
+        const uint32_t g = (i << A) + t;           // global leaf index
+        uint32_t sk[NW];
+        hashF<P>(ms256, make_adrs(0, tree, T_FORS_PRF, kp, 0, g), skseed, sk);
+        if (t == gs) store_be<NW>(sf, sk);
+        hashF<P>(ms256, make_adrs(0, tree, T_FORS_TREE, kp, 0, g), sk, node);
+        if (t == (gs ^ 1u)) store_be<NW>(sf + P::N, node);
+        // merge with stacked left siblings while this node is a right child
+        uint32_t z = 0, idx = t;
+#pragma unroll 1
+        while ((idx & 1u) && z < (uint32_t)R) {
+            uint32_t lr[2 * NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) {
+                uint32_t v = stk[0][w];
+#pragma unroll
+                for (int zz = 1; zz < R; zz++) v = (z == (uint32_t)zz) ? stk[zz][w] : v;
+                lr[w] = v;
+                lr[NW + w] = node[w];
+            }
+            z++;
+            idx >>= 1;
+            hashH_ms<P>(ms256, ms512,
+                        make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node);
+            if (z < (uint32_t)A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
+        }
+        if (z < (uint32_t)R) {
+#pragma unroll
+            for (int zz = 0; zz < R; zz++)
+                if (z == (uint32_t)zz) {
+#pragma unroll
+                    for (int w = 0; w < NW; w++) stk[zz][w] = node[w];
+                }
+        }
+    }
+    // node = lane subtree root, level R, index L within the tree
+#pragma unroll
+    for (int z = R + 1; z <= A; z++) {
+        const int step = 1 << (z - R - 1);
+        uint32_t other[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) other[w] = __shfl_xor_sync(gmask, node[w], step);
+        if ((L & (2 * step - 1)) == 0) {
+            uint32_t lr[2 * NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) { lr[w] = node[w]; lr[NW + w] = other[w]; }
+            const uint32_t idx = L >> (z - R);
+            hashH_ms<P>(ms256, ms512, make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node);
+            if (z < A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
+        }
+    }
+    if (L == 0) {
+        uint32_t* r = fors_roots + ((size_t)m * K + i) * NW;
+#pragma unroll
+        for (int w = 0; w < NW; w++) r[w] = node[w];
+    }
+}
+
+// PK_FORS = T_k(FORS_ROOTS(layer 0, idx_tree, keypair idx_leaf), roots).
+template <class P>
+__global__ void fors_pk_kernel(const KeyBlock* __restrict__ keys, const MsgInfo* __restrict__ infos,
+                               uint32_t count, const uint32_t* __restrict__ fors_roots,
+                               uint32_t* __restrict__ pk_fors) {
+    const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    const MsgInfo& info = infos[m];
+    if (info.key == KEY_INVALID) return;
+    const KeyBlock& kb = keys[info.key];
+    constexpr int NW = P::NW;
+    TStream<P::BIG> ts;
+    ts.init(P::BIG ? kb.ms512 : kb.ms256, make_adrs(0, info.idx_tree, T_FORS_ROOTS, info.idx_leaf, 0, 0));
+    const uint32_t* r = fors_roots + (size_t)m * P::K * NW;
+    for (int i = 0; i < P::K; i++) ts.template push_n<NW>(r + i * NW);
+    uint32_t out[NW];
+    ts.template finish<NW>(P::K * P::N, out);
+#pragma unroll
+    for (int w = 0; w < NW; w++) pk_fors[(size_t)m * NW + w] = out[w];
+}
+
+template <class P>
+static cudaError_t launch_fors_t(const Batch& b, cudaStream_t s) {
+    const uint64_t threads = (uint64_t)b.count * P::K * ForsShape<P>::LPT;
+    const uint32_t T = 256;
+    const uint32_t G = (uint32_t)((threads + T - 1) / T);
+    fors_kernel<P><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.fors_roots);
+    return cudaGetLastError();
+}
+
+template <class P>
+static cudaError_t launch_fors_pk_t(const Batch& b, cudaStream_t s) {
+    const uint32_t T = 128, G = (b.count + T - 1) / T;
+    fors_pk_kernel<P><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.fors_roots, b.pk_fors);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fors(const Batch& b, cudaStream_t s) {
+    switch (b.pset) {
+    case 0: return launch_fors_t<P128f>(b, s);
+    case 1: return launch_fors_t<P192f>(b, s);
+    case 2: return launch_fors_t<P256f>(b, s);
+    case 3: return launch_fors_t<PToy>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fors_pk(const Batch& b, cudaStream_t s) {
+    switch (b.pset) {
+    case 0: return launch_fors_pk_t<P128f>(b, s);
+    case 1: return launch_fors_pk_t<P192f>(b, s);
+    case 2: return launch_fors_pk_t<P256f>(b, s);
+    case 3: return launch_fors_pk_t<PToy>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace hs

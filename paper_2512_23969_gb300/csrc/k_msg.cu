@@ -1,0 +1,291 @@
+// k_msg.cu -- per-key preparation, message offsets and the message stage.
+//
+// Message stage (the paper's hash_message + message_to_indices, Fig. 2):
+//   R      = Trunc_n(HMAC-SHA-x(SK.prf, PK.seed || M))          (PRF_msg)
+//   digest = MGF1-SHA-x(R || PK.seed || SHA-x(R || PK.seed || PK.root || M), m)
+//   digest = md || tree bytes || leaf bytes -> k FORS indices, idx_tree, idx_leaf
+// One thread per message; the work is serial in the message length (two
+// passes over M), which is the only length-dependent part of signing.
+#include <cuda_runtime.h>
+#include "hs_common.cuh"
+#include "hs_launch.h"
+#include "../../include/hs.h"
+
+namespace hs {
+
+// ------------------------------------------------------------- byte SHA-x
+// Streaming SHA-256 / SHA-512 over bytes and big-endian words.  Only the
+// message stage uses it (a few blocks per 32-byte message).
+template <bool BIG>
+struct ByteSha {
+    static constexpr int B = BIG ? 128 : 64;   // block bytes
+    static constexpr int BW = B / 4;
+    uint32_t st[BIG ? 16 : 8];
+    uint32_t blk[BW];
+    uint32_t fill;      // bytes in blk
+    uint64_t total;     // message bytes so far
+
+    __device__ void init() {
+        if constexpr (BIG) {
+            uint64_t s[8];
+            sha512_iv(s);
+            for (int i = 0; i < 8; i++) { st[2 * i] = (uint32_t)(s[i] >> 32); st[2 * i + 1] = (uint32_t)s[i]; }
+        } else {
+            sha256_iv(st);
+        }
+        for (int i = 0; i < BW; i++) blk[i] = 0;
+        fill = 0;
+        total = 0;
+    }
+    __device__ void compress() {
+        if constexpr (BIG) {
+            uint64_t s[8];
+            for (int i = 0; i < 8; i++) s[i] = ((uint64_t)st[2 * i] << 32) | st[2 * i + 1];
+            sha512_compress_w32(s, blk);
+            for (int i = 0; i < 8; i++) { st[2 * i] = (uint32_t)(s[i] >> 32); st[2 * i + 1] = (uint32_t)s[i]; }
+        } else {
+            uint32_t W[16];
+            for (int i = 0; i < 16; i++) W[i] = blk[i];
+            sha256_compress_rolled(st, W);
+        }
+        for (int i = 0; i < BW; i++) blk[i] = 0;
+        fill = 0;
+    }
+    __device__ void byte(uint32_t b) {
+        blk[fill >> 2] |= (b & 0xFFu) << (24 - 8 * (fill & 3));
+        fill++;
+        total++;
+        if (fill == B) compress();
+    }
+    // nbytes of a big-endian word array
+    __device__ void words(const uint32_t* w, int nbytes) {
+        for (int i = 0; i < nbytes; i++) byte(w[i >> 2] >> (24 - 8 * (i & 3)));
+    }
+    // raw bytes from global memory at any alignment
+    __device__ void mem(const uint8_t* p, uint64_t len) {
+        uint64_t i = 0;
+        while (i < len && (fill & 3)) { byte(p[i]); i++; }
+        while (i + 4 <= len) {
+            blk[fill >> 2] = ((uint32_t)p[i] << 24) | ((uint32_t)p[i + 1] << 16) |
+                             ((uint32_t)p[i + 2] << 8) | (uint32_t)p[i + 3];
+            fill += 4;
+            total += 4;
+            i += 4;
+            if (fill == B) compress();
+        }
+        while (i < len) { byte(p[i]); i++; }
+    }
+    // Pad (0x80, zeros, bit length) and return the digest words (8 or 16).
+    __device__ void finish(uint32_t* out) {
+        const uint64_t bits = total * 8;
+        blk[fill >> 2] |= 0x80u << (24 - 8 * (fill & 3));
+        fill++;
+        if (fill > (uint32_t)(B - (BIG ? 16 : 8))) compress();
+        blk[BW - 1] = (uint32_t)bits;
+        blk[BW - 2] = (uint32_t)(bits >> 32);
+        compress();
+        for (int i = 0; i < (BIG ? 16 : 8); i++) out[i] = st[i];
+    }
+};
+
+// ------------------------------------------------------------- keyprep
+// KeyBlock from a key buffer: sign keys are SK.seed||SK.prf||PK.seed||PK.root
+// (4n); verify keys are PK.seed||PK.root (2n).  The midstates are the SHA-2
+// state after the first block BlockPad(PK.seed).
+template <class P>
+__global__ void keyprep_kernel(const uint8_t* __restrict__ in, uint32_t num_keys, int from_pk,
+                               KeyBlock* __restrict__ out) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= num_keys) return;
+    KeyBlock kb;
+    for (int i = 0; i < 64; i++) reinterpret_cast<uint32_t*>(&kb)[i] = 0;
+    constexpr int NW = P::NW;
+    if (from_pk) {
+        const uint8_t* p = in + (size_t)k * 2 * P::N;
+        load_be_unaligned<NW>(p, kb.pk_seed);
+        load_be_unaligned<NW>(p + P::N, kb.pk_root);
+    } else {
+        const uint8_t* p = in + (size_t)k * 4 * P::N;
+        load_be_unaligned<NW>(p, kb.sk_seed);
+        load_be_unaligned<NW>(p + P::N, kb.sk_prf);
+        load_be_unaligned<NW>(p + 2 * P::N, kb.pk_seed);
+        load_be_unaligned<NW>(p + 3 * P::N, kb.pk_root);
+    }
+    {
+        uint32_t W[16];
+        for (int i = 0; i < 16; i++) W[i] = (i < NW) ? kb.pk_seed[i] : 0u;
+        sha256_iv(kb.ms256);
+        sha256_compress_rolled(kb.ms256, W);
+    }
+    if constexpr (P::BIG) {
+        uint32_t blk[32];
+        for (int i = 0; i < 32; i++) blk[i] = (i < NW) ? kb.pk_seed[i] : 0u;
+        uint64_t s[8];
+        sha512_iv(s);
+        sha512_compress_w32(s, blk);
+        for (int i = 0; i < 8; i++) { kb.ms512[2 * i] = (uint32_t)(s[i] >> 32); kb.ms512[2 * i + 1] = (uint32_t)s[i]; }
+    }
+    out[k] = kb;
+}
+
+// ------------------------------------------------------------- offsets
+// offsets[i] = lens[0] + ... + lens[i-1], i = 0..count (one CTA of 1024).
+__global__ void offsets_kernel(const uint64_t* __restrict__ lens, uint32_t count, uint64_t* __restrict__ off) {
+    __shared__ uint64_t part[1024];
+    const uint32_t t = threadIdx.x;
+    const uint32_t chunk = (count + 1023) / 1024;
+    const uint64_t lo = (uint64_t)t * chunk;
+    uint64_t s = 0;
+    for (uint64_t i = lo; i < lo + chunk && i < count; i++) s += lens[i];
+    part[t] = s;
+    __syncthreads();
+    for (uint32_t d = 1; d < 1024; d <<= 1) {       // inclusive Hillis-Steele scan
+        uint64_t v = (t >= d) ? part[t - d] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    uint64_t run = (t == 0) ? 0 : part[t - 1];
+    for (uint64_t i = lo; i < lo + chunk && i < count; i++) { off[i] = run; run += lens[i]; }
+    if (t == 1023) off[count] = part[1023];
+}
+
+// ------------------------------------------------------------- message stage
+template <class P>
+__device__ __forceinline__ uint32_t digest_byte(const uint32_t* dw, int i) {
+    return (dw[i >> 2] >> (24 - 8 * (i & 3))) & 0xFFu;
+}
+
+// verify = 0: compute R (PRF_msg) and write it to sig[0:n].
+// verify = 1: R is read from the signature.
+template <class P>
+__global__ void message_kernel(const KeyBlock* __restrict__ keys, uint32_t num_keys,
+                               const uint32_t* __restrict__ key_idx, const uint8_t* __restrict__ msgs,
+                               const uint64_t* __restrict__ off, uint32_t count, uint8_t* __restrict__ sigs,
+                               MsgInfo* __restrict__ infos, uint32_t* __restrict__ status, int verify) {
+    const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    constexpr int NW = P::NW;
+    constexpr int DW = P::BIG ? 16 : 8;            // digest words of SHA-x
+    uint8_t* sig = sigs + (size_t)m * P::SIG_BYTES;
+    MsgInfo info;
+    info.pad[0] = info.pad[1] = 0;
+    const uint32_t key = key_idx ? key_idx[m] : 0u;
+    if (key >= num_keys) {
+        atomicOr(status, 1u << HS_EKEY);
+        info.key = KEY_INVALID;
+        info.idx_tree = 0;
+        info.idx_leaf = 0;
+        for (int i = 0; i < 36; i++) info.fors_idx[i] = 0;
+        infos[m] = info;
+        if (!verify) {
+            uint4* s4 = reinterpret_cast<uint4*>(sig);
+            for (int i = 0; i < P::SIG_BYTES / 16; i++) s4[i] = make_uint4(0, 0, 0, 0);
+        }
+        return;
+    }
+    const KeyBlock& kb = keys[key];
+    const uint8_t* M = msgs + off[m];
+    const uint64_t mlen = off[m + 1] - off[m];
+
+    uint32_t R[8];
+    ByteSha<P::BIG> h;
+    if (!verify) {
+        // PRF_msg = HMAC-SHA-x(SK.prf, opt_rand || M), opt_rand = PK.seed
+        uint32_t kw[ByteSha<P::BIG>::BW];
+        for (int i = 0; i < ByteSha<P::BIG>::BW; i++) kw[i] = (i < NW) ? kb.sk_prf[i] : 0u;
+        uint32_t inner[DW];
+        h.init();
+        for (int i = 0; i < ByteSha<P::BIG>::BW; i++) {
+            uint32_t x = kw[i] ^ 0x36363636u;
+            h.words(&x, 4);
+        }
+        h.words(kb.pk_seed, P::N);
+        h.mem(M, mlen);
+        h.finish(inner);
+        h.init();
+        for (int i = 0; i < ByteSha<P::BIG>::BW; i++) {
+            uint32_t x = kw[i] ^ 0x5c5c5c5cu;
+            h.words(&x, 4);
+        }
+        h.words(inner, 4 * DW);
+        uint32_t mac[DW];
+        h.finish(mac);
+        for (int i = 0; i < NW; i++) R[i] = mac[i];
+        store_be<NW>(sig, R);
+    } else {
+        load_be<NW>(sig, R);
+    }
+    // H_msg
+    uint32_t inner[DW];
+    h.init();
+    h.words(R, P::N);
+    h.words(kb.pk_seed, P::N);
+    h.words(kb.pk_root, P::N);
+    h.mem(M, mlen);
+    h.finish(inner);
+    uint32_t dg[16];                     // >= m bytes (m <= 49)
+    int got = 0;
+    for (uint32_t c = 0; got < P::M; c++) {
+        h.init();
+        h.words(R, P::N);
+        h.words(kb.pk_seed, P::N);
+        h.words(inner, 4 * DW);
+        h.words(&c, 4);
+        uint32_t blockd[DW];
+        h.finish(blockd);
+        for (int i = 0; i < DW && got < P::M; i++, got += 4) dg[got >> 2] = blockd[i];
+    }
+    // md -> FORS indices: md read as a little-endian bit stream, index i from
+    // stream bits i*a .. i*a+a-1, first bit least significant.
+    for (int i = 0; i < P::K; i++) {
+        uint32_t v = 0;
+        for (int j = 0; j < P::A; j++) {
+            const int q = i * P::A + j;
+            v |= ((digest_byte<P>(dg, q >> 3) >> (q & 7)) & 1u) << j;
+        }
+        info.fors_idx[i] = (uint16_t)v;
+    }
+    for (int i = P::K; i < 36; i++) info.fors_idx[i] = 0;
+    uint64_t t = 0;
+    for (int b = 0; b < P::TREE_BYTES; b++) t = (t << 8) | digest_byte<P>(dg, P::MD_BYTES + b);
+    if (P::TREE_BITS < 64) t &= (1ull << (P::TREE_BITS & 63)) - 1ull;
+    uint32_t l = 0;
+    for (int b = 0; b < P::LEAF_BYTES; b++) l = (l << 8) | digest_byte<P>(dg, P::MD_BYTES + P::TREE_BYTES + b);
+    l &= (uint32_t)(P::LEAVES - 1);
+    info.idx_tree = t;
+    info.idx_leaf = l;
+    info.key = key;
+    infos[m] = info;
+}
+
+// ------------------------------------------------------------- launchers
+#define HS_DISPATCH(pset, CALL)                         \
+    switch (pset) {                                     \
+    case 0: { using P = P128f; CALL; } break;           \
+    case 1: { using P = P192f; CALL; } break;           \
+    case 2: { using P = P256f; CALL; } break;           \
+    case 3: { using P = PToy; CALL; } break;            \
+    default: return cudaErrorInvalidValue;              \
+    }
+
+cudaError_t launch_keyprep(const Batch& b, bool from_pk, cudaStream_t s) {
+    const uint32_t T = 128, G = (b.num_keys + T - 1) / T;
+    HS_DISPATCH(b.pset, (keyprep_kernel<P><<<G, T, 0, s>>>(b.keys_in, b.num_keys, from_pk ? 1 : 0, b.keys)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_offsets(const Batch& b, cudaStream_t s) {
+    offsets_kernel<<<1, 1024, 0, s>>>(b.lens, b.count, b.offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_message(const Batch& b, bool verify, cudaStream_t s) {
+    const uint32_t T = 64, G = (b.count + T - 1) / T;
+    HS_DISPATCH(b.pset, (message_kernel<P><<<G, T, 0, s>>>(b.keys, b.num_keys, b.key_idx, b.msgs, b.offsets,
+                                                             b.count, b.sigs, b.infos, b.status,
+                                                             verify ? 1 : 0)));
+    return cudaGetLastError();
+}
+
+}  // namespace hs

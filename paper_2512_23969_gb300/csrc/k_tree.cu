@@ -1,0 +1,215 @@
+// k_tree.cu -- TREE_Sign (paper Sec. III-A, III-C) and key generation.
+//
+// What it computes (Sec. II-A-1, II-A-3/4): for every layer j of the
+// hypertree, tree t_j = idx_tree >> (j h'), all 2^h' leaves.  A leaf is the
+// WOTS+ public key of keypair l: len chains, each PRF(WOTS_PRF) followed by
+// w-1 = 15 applications of F(WOTS_HASH), compressed by T_len(WOTS_PK)
+// (560 / 816 / 1072 SHA-256 calls per leaf).  Leaves are merged by H(TREE)
+// into the tree root; the h' auth nodes of the signing leaf go to the
+// signature and the root to scratch (it is what layer j+1 signs).
+//
+// GB300 mapping: one thread per leaf, the 2^h' leaves of a tree in an
+// aligned lane group of one warp, so the Merkle levels are merged with warp
+// shuffles (no shared memory, no barriers).  Each thread runs its len
+// chains back to back and streams every chain end straight into the T_len
+// hash, so only one chain value plus the running T_len state are live.  The
+// PRF and the 15 F steps of a chain share one call site of the fully
+// unrolled SHA-256 compression (all known-zero message words folded).
+// All d layers of all messages form one flat grid: the layers of a
+// signature are independent given the digest (paper Fig. 2).
+#include <cuda_runtime.h>
+#include "hs_common.cuh"
+#include "hs_launch.h"
+
+namespace hs {
+
+// Hypertree leaf = WOTS+ public key of keypair kp in tree (layer, tree).
+template <class P>
+__device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t* msT, const uint32_t* skseed,
+                                          uint32_t layer, uint64_t tree, uint32_t kp, uint32_t* out) {
+    constexpr int NW = P::NW;
+    TStream<P::BIG> ts;
+    ts.init(msT, make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0));
+    const Adrs aprf = make_adrs(layer, tree, T_WOTS_PRF, kp, 0, 0);
+    const Adrs ahash = make_adrs(layer, tree, T_WOTS_HASH, kp, 0, 0);
+#pragma unroll 1
+    for (uint32_t i = 0; i < (uint32_t)P::LEN; i++) {
+        uint32_t x[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) x[w] = skseed[w];
+        // step 0: PRF(WOTS_PRF(kp, chain i, hash 0)); steps 1..15: F(WOTS_HASH(kp, i, s-1))
+#pragma unroll 1
+        for (uint32_t s = 0; s < 16; s++) {
+            Adrs a = (s == 0) ? aprf : ahash;
+            a.w4 = i << 16;                 // chain i (< 2^16) | hash >> 16 (= 0)
+            a.half = (s == 0) ? 0u : s - 1u;  // low half of the hash address
+            hashF<P>(ms256, a, x, x);
+        }
+        ts.template push_n<NW>(x);
+    }
+    ts.template finish<NW>(P::LEN * P::N, out);
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) tree_kernel(const KeyBlock* __restrict__ keys,
+                                                   const MsgInfo* __restrict__ infos, uint32_t count,
+                                                   uint8_t* __restrict__ sigs, uint32_t* __restrict__ roots) {
+    constexpr int NW = P::NW, HP = P::HP, LV = P::LEAVES;
+    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t per_msg = (uint32_t)P::D * LV;
+    const uint32_t m = gid / per_msg;
+    const uint32_t r = gid % per_msg;
+    const uint32_t j = r / LV;                      // layer
+    const uint32_t l = r % LV;                      // leaf (keypair) in the tree
+    if (m >= count) return;                         // whole trees exit together
+    const MsgInfo& info = infos[m];
+    if (info.key == KEY_INVALID) return;
+    const unsigned gmask = ((LV == 32) ? 0xFFFFFFFFu : ((1u << LV) - 1u)) << (lane & ~(uint32_t)(LV - 1));
+
+    const KeyBlock& kb = keys[info.key];
+    uint32_t ms256[8], msT[P::BIG ? 16 : 8], skseed[NW];
+#pragma unroll
+    for (int w = 0; w < 8; w++) ms256[w] = kb.ms256[w];
+#pragma unroll
+    for (int w = 0; w < (P::BIG ? 16 : 8); w++) msT[w] = P::BIG ? kb.ms512[w] : kb.ms256[w];
+#pragma unroll
+    for (int w = 0; w < NW; w++) skseed[w] = kb.sk_seed[w];
+
+    const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
+    const uint32_t sl = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
+
+    uint32_t node[NW];
+    wots_leaf<P>(ms256, msT, skseed, j, tree, l, node);
+
+    uint8_t* auth = sigs + (size_t)m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES +
+                    (size_t)P::LEN * P::N;
+    if (l == (sl ^ 1u)) store_be<NW>(auth, node);
+#pragma unroll
+    for (int z = 1; z <= HP; z++) {
+        const int step = 1 << (z - 1);
+        uint32_t other[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) other[w] = __shfl_xor_sync(gmask, node[w], step);
+        if ((l & (2 * step - 1)) == 0) {
+            uint32_t lr[2 * NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) { lr[w] = node[w]; lr[NW + w] = other[w]; }
+            const uint32_t idx = l >> z;
+            hashH_ms<P>(ms256, msT, make_adrs(j, tree, T_TREE, 0, z, idx), lr, node);
+            if (z < HP && idx == ((sl >> z) ^ 1u)) store_be<NW>(auth + (size_t)z * P::N, node);
+        }
+    }
+    if (l == 0) {
+        uint32_t* rt = roots + ((size_t)m * P::D + j) * NW;
+#pragma unroll
+        for (int w = 0; w < NW; w++) rt[w] = node[w];
+    }
+}
+
+// Key generation: PK.root = root of tree 0 of the top layer d-1.  One lane
+// group per key; the midstates are derived from the seed in-thread.
+template <class P>
+__global__ void __launch_bounds__(128) keygen_kernel(const uint8_t* __restrict__ seeds, uint32_t count,
+                                                     uint8_t* __restrict__ pk, uint8_t* __restrict__ sk) {
+    constexpr int NW = P::NW, HP = P::HP, LV = P::LEAVES, N = P::N;
+    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t key = gid / LV;
+    const uint32_t l = gid % LV;
+    if (key >= count) return;
+    const unsigned gmask = ((LV == 32) ? 0xFFFFFFFFu : ((1u << LV) - 1u)) << (lane & ~(uint32_t)(LV - 1));
+    const uint8_t* sd = seeds + (size_t)key * 3 * N;
+    uint32_t skseed[NW], pkseed[NW];
+    load_be_unaligned<NW>(sd, skseed);
+    load_be_unaligned<NW>(sd + 2 * N, pkseed);
+    uint32_t ms256[8], msT[P::BIG ? 16 : 8];
+    {
+        uint32_t W[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) W[i] = (i < NW) ? pkseed[i] : 0u;
+        sha256_iv(ms256);
+        sha256_compress_rolled(ms256, W);
+    }
+    if constexpr (P::BIG) {
+        uint32_t blk[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) blk[i] = (i < NW) ? pkseed[i] : 0u;
+        uint64_t s[8];
+        sha512_iv(s);
+        sha512_compress_w32(s, blk);
+#pragma unroll
+        for (int i = 0; i < 8; i++) { msT[2 * i] = (uint32_t)(s[i] >> 32); msT[2 * i + 1] = (uint32_t)s[i]; }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; i++) msT[i] = ms256[i];
+    }
+    const uint32_t top = (uint32_t)P::D - 1;
+    uint32_t node[NW];
+    wots_leaf<P>(ms256, msT, skseed, top, 0ull, l, node);
+#pragma unroll
+    for (int z = 1; z <= HP; z++) {
+        const int step = 1 << (z - 1);
+        uint32_t other[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) other[w] = __shfl_xor_sync(gmask, node[w], step);
+        if ((l & (2 * step - 1)) == 0) {
+            uint32_t lr[2 * NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) { lr[w] = node[w]; lr[NW + w] = other[w]; }
+            hashH_ms<P>(ms256, msT, make_adrs(top, 0ull, T_TREE, 0, z, l >> z), lr, node);
+        }
+    }
+    if (l == 0) {
+        uint8_t* p = pk + (size_t)key * 2 * N;
+        uint8_t* s = sk + (size_t)key * 4 * N;
+        for (int b = 0; b < 3 * N; b++) s[b] = sd[b];
+        for (int b = 0; b < N; b++) {
+            const uint8_t v = (uint8_t)(node[b >> 2] >> (24 - 8 * (b & 3)));
+            s[3 * N + b] = v;
+            p[N + b] = v;
+            p[b] = sd[2 * N + b];
+        }
+    }
+}
+
+template <class P>
+static cudaError_t launch_tree_t(const Batch& b, cudaStream_t s) {
+    const uint64_t threads = (uint64_t)b.count * P::D * P::LEAVES;
+    const uint32_t T = 128;
+    const uint32_t G = (uint32_t)((threads + T - 1) / T);
+    tree_kernel<P><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots);
+    return cudaGetLastError();
+}
+
+template <class P>
+static cudaError_t launch_keygen_t(const uint8_t* seeds, uint32_t count, uint8_t* pk, uint8_t* sk, cudaStream_t s) {
+    const uint64_t threads = (uint64_t)count * P::LEAVES;
+    const uint32_t T = 128;
+    const uint32_t G = (uint32_t)((threads + T - 1) / T);
+    keygen_kernel<P><<<G, T, 0, s>>>(seeds, count, pk, sk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree(const Batch& b, cudaStream_t s) {
+    switch (b.pset) {
+    case 0: return launch_tree_t<P128f>(b, s);
+    case 1: return launch_tree_t<P192f>(b, s);
+    case 2: return launch_tree_t<P256f>(b, s);
+    case 3: return launch_tree_t<PToy>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_keygen(int pset, const uint8_t* seeds, uint32_t count, uint8_t* pk, uint8_t* sk,
+                          cudaStream_t s) {
+    switch (pset) {
+    case 0: return launch_keygen_t<P128f>(seeds, count, pk, sk, s);
+    case 1: return launch_keygen_t<P192f>(seeds, count, pk, sk, s);
+    case 2: return launch_keygen_t<P256f>(seeds, count, pk, sk, s);
+    case 3: return launch_keygen_t<PToy>(seeds, count, pk, sk, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace hs

@@ -1,0 +1,89 @@
+// k_wots.cu -- WOTS+_Sign (paper Sec. III, after FORS_Sign and TREE_Sign).
+//
+// What it computes (Sec. II-A-1): layer j signs the n-byte value
+// msg_j = PK_FORS (j = 0) or root_{j-1} (j >= 1).  Its base-16 digits (high
+// nibble first) are followed by the 3 digits of the checksum
+// sum(15 - d_i) << 4; chain i of the signing keypair is advanced from its
+// secret PRF(WOTS_PRF) by digit_i applications of F(WOTS_HASH).
+//
+// GB300 mapping: one thread per (message, layer, chain); each thread
+// recomputes the checksum from msg_j (2n nibble reads, negligible next to
+// its chain) so no cross-thread exchange is needed.
+#include <cuda_runtime.h>
+#include "hs_common.cuh"
+#include "hs_launch.h"
+
+namespace hs {
+
+template <class P>
+__global__ void __launch_bounds__(256) wots_kernel(const KeyBlock* __restrict__ keys,
+                                                   const MsgInfo* __restrict__ infos, uint32_t count,
+                                                   const uint32_t* __restrict__ pk_fors,
+                                                   const uint32_t* __restrict__ roots, uint8_t* __restrict__ sigs) {
+    constexpr int NW = P::NW, LEN = P::LEN;
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t per_msg = (uint32_t)P::D * LEN;
+    const uint64_t m = gid / per_msg;
+    const uint32_t r = (uint32_t)(gid % per_msg);
+    const uint32_t j = r / LEN;
+    const uint32_t i = r % LEN;
+    if (m >= count) return;
+    const MsgInfo& info = infos[m];
+    if (info.key == KEY_INVALID) return;
+    const KeyBlock& kb = keys[info.key];
+
+    const uint32_t* mj = (j == 0) ? pk_fors + m * NW : roots + (m * P::D + (j - 1)) * NW;
+    uint32_t msg[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) msg[w] = mj[w];
+    uint32_t csum = 0;
+#pragma unroll
+    for (int w = 0; w < NW; w++)
+#pragma unroll
+        for (int b = 0; b < 8; b++) csum += 15u - ((msg[w] >> (28 - 4 * b)) & 15u);
+    uint32_t digit;
+    if (i < (uint32_t)P::LEN1) {
+        digit = (msg[i >> 3] >> (28 - 4 * (i & 7))) & 15u;
+    } else {
+        const uint32_t c = csum << 4;                 // (8 - (len2 * 4) % 8) % 8 = 4
+        digit = (c >> (12 - 4 * (i - P::LEN1))) & 15u;
+    }
+
+    const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
+    const uint32_t kp = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
+    uint32_t ms256[8];
+#pragma unroll
+    for (int w = 0; w < 8; w++) ms256[w] = kb.ms256[w];
+    uint32_t x[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) x[w] = kb.sk_seed[w];
+    Adrs a = make_adrs(j, tree, T_WOTS_PRF, kp, i, 0);
+    const Adrs ahash = make_adrs(j, tree, T_WOTS_HASH, kp, i, 0);
+#pragma unroll 1
+    for (uint32_t s = 0; s <= digit; s++) {
+        if (s > 0) { a = ahash; a.half = s - 1u; }
+        hashF<P>(ms256, a, x, x);
+    }
+    store_be<NW>(sigs + m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES + (size_t)i * P::N, x);
+}
+
+template <class P>
+static cudaError_t launch_wots_t(const Batch& b, cudaStream_t s) {
+    const uint64_t threads = (uint64_t)b.count * P::D * P::LEN;
+    const uint32_t T = 256;
+    const uint32_t G = (uint32_t)((threads + T - 1) / T);
+    wots_kernel<P><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.pk_fors, b.roots, b.sigs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wots(const Batch& b, cudaStream_t s) {
+    switch (b.pset) {
+    case 0: return launch_wots_t<P128f>(b, s);
+    case 1: return launch_wots_t<P192f>(b, s);
+    case 2: return launch_wots_t<P256f>(b, s);
+    case 3: return launch_wots_t<PToy>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace hs

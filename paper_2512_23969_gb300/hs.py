@@ -1,0 +1,162 @@
+"""Thin Python binding of libhs.so (include/hs.h).
+
+Argument marshalling only: tensors (CUDA or CPU) and numpy arrays are passed
+to the C ABI as raw pointers with the current CUDA stream; every step of
+signing and verifying runs in the library's kernels.  There is no fallback:
+if ``libhs.so`` is missing or cannot be loaded, :func:`load` raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+PARAMS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3}
+N_BYTES = {"128f": 16, "192f": 24, "256f": 32, "toy": 16}
+STATUS = {0: "HS_OK", 1: "HS_EINVAL", 2: "HS_ENOMEM", 3: "HS_ECUDA", 4: "HS_ETIMEOUT", 5: "HS_EKEY"}
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libhs.so")
+
+_lib = None
+
+
+class HSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+def load():
+    """Load libhs.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libhs.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    vp, u32, u64p = C.c_void_p, C.c_uint32, C.c_void_p
+    for name in ("hs_sig_bytes", "hs_pk_bytes", "hs_sk_bytes", "hs_seed_bytes"):
+        getattr(L, name).argtypes = [C.c_int]
+        getattr(L, name).restype = C.c_size_t
+    L.hs_keygen.argtypes = [C.c_int, vp, u32, vp, vp, vp]
+    L.hs_sign_batch.argtypes = [C.c_int, vp, u32, vp, vp, u64p, u32, vp, vp]
+    L.hs_verify_batch.argtypes = [C.c_int, vp, u32, vp, vp, u64p, vp, u32, vp, vp]
+    L.hs_check_status.argtypes = [vp, C.POINTER(C.c_uint32)]
+    L.hs_last_error.restype = C.c_char_p
+    L.hs_profile_enable.argtypes = [C.c_int]
+    L.hs_profile_read.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_char_p), C.c_int]
+    L.hs_profile_read.restype = C.c_int
+    L.hs_sign_kernel_count.restype = C.c_int
+    for name in ("hs_keygen", "hs_sign_batch", "hs_verify_batch", "hs_check_status"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _pid(params):
+    return PARAMS[params] if isinstance(params, str) else int(params)
+
+
+def _check(rc):
+    if rc != 0:
+        raise HSError(rc, load().hs_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Raw address of a tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data if x.size else None
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr() if x.numel() else None
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+
+
+def _like(x, n, dtype_np, dtype_torch_name):
+    """Allocate an output on the same side (device / host) as x."""
+    if isinstance(x, np.ndarray):
+        return np.empty(n, dtype=dtype_np)
+    import torch
+    return torch.empty(n, dtype=getattr(torch, dtype_torch_name), device=x.device)
+
+
+def _nonempty(msgs, lens):
+    """A batch whose messages are all empty still passes a valid message
+    buffer (the C ABI accepts NULL only with host-side lengths)."""
+    if msgs is None or (msgs.size if isinstance(msgs, np.ndarray) else msgs.numel()) == 0:
+        return _like(lens, 16, np.uint8, "uint8")
+    return msgs
+
+
+def sig_bytes(params):
+    return int(load().hs_sig_bytes(_pid(params)))
+
+
+def hs_keygen(params, seeds, pk=None, sk=None, stream=None):
+    """(pk, sk) for each 3n-byte seed row of ``seeds`` (uint8 [count, 3n])."""
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    count = seeds.shape[0] if seeds.ndim == 2 else seeds.shape[0] // (3 * n)
+    pk = _like(seeds, count * 2 * n, np.uint8, "uint8") if pk is None else pk
+    sk = _like(seeds, count * 4 * n, np.uint8, "uint8") if sk is None else sk
+    _check(load().hs_keygen(_pid(params), _ptr(seeds), count, _ptr(pk), _ptr(sk), _stream(stream)))
+    return pk.reshape(count, 2 * n), sk.reshape(count, 4 * n)
+
+
+def hs_sign_batch(params, sk, msgs, lens, key_idx=None, sigs=None, num_keys=None, stream=None):
+    """Signatures (uint8 [count, SIG]) of the packed messages ``msgs`` with lengths ``lens``."""
+    count = int(lens.shape[0])
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    if num_keys is None:
+        num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
+    S = sig_bytes(params)
+    sigs = _like(lens, count * S, np.uint8, "uint8") if sigs is None else sigs
+    msgs = _nonempty(msgs, lens)
+    _check(load().hs_sign_batch(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), _ptr(msgs), _ptr(lens),
+                                count, _ptr(sigs), _stream(stream)))
+    return sigs.reshape(count, S)
+
+
+def hs_verify_batch(params, pk, msgs, lens, sigs, key_idx=None, ok=None, num_keys=None, stream=None):
+    """1/0 per signature (uint8 [count])."""
+    count = int(lens.shape[0])
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    if num_keys is None:
+        num_keys = (pk.shape[0] if pk.ndim == 2 else pk.shape[0] // (2 * n))
+    ok = _like(lens, count, np.uint8, "uint8") if ok is None else ok
+    msgs = _nonempty(msgs, lens)
+    _check(load().hs_verify_batch(_pid(params), _ptr(pk), int(num_keys), _ptr(key_idx), _ptr(msgs), _ptr(lens),
+                                  _ptr(sigs), count, _ptr(ok), _stream(stream)))
+    return ok
+
+
+def hs_check_status(stream=None):
+    """Synchronize the stream; return the device status flags (and clear them)."""
+    flags = C.c_uint32(0)
+    rc = load().hs_check_status(_stream(stream), C.byref(flags))
+    return rc, flags.value
+
+
+def hs_profile_enable(on=True):
+    load().hs_profile_enable(1 if on else 0)
+
+
+def hs_profile_read():
+    """{stage name: ms} of the most recent profiled hs_sign_batch call."""
+    ms = (C.c_float * 16)()
+    names = (C.c_char_p * 16)()
+    n = load().hs_profile_read(ms, names, 16)
+    if n < 0:
+        return {}
+    return {names[i].decode(): float(ms[i]) for i in range(n)}
+
+
+def hs_sign_kernel_count():
+    return int(load().hs_sign_kernel_count())

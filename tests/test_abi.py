@@ -1,0 +1,69 @@
+"""CPU-side checks of the C ABI library (no kernel is launched here).
+
+libhs.so must build for sm_103a, load, and export every function that
+include/hs.h declares; the size queries must agree with the oracle's
+parameter derivation; and the product package must not reach the oracle.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hs_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_23969_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert {"hs_keygen", "hs_sign_batch", "hs_verify_batch"} <= set(names)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_size_queries_match_oracle(lib, O):
+    for pid, ps in enumerate(("128f", "192f", "256f", "toy")):
+        P = O.params(ps)
+        for fn, want in (("hs_sig_bytes", P.sig_bytes), ("hs_pk_bytes", 2 * P.n),
+                         ("hs_sk_bytes", 4 * P.n), ("hs_seed_bytes", 3 * P.n)):
+            f = getattr(lib, fn)
+            f.argtypes = [C.c_int]
+            f.restype = C.c_size_t
+            assert f(pid) == want, (fn, ps)
+    lib.hs_sig_bytes.argtypes = [C.c_int]
+    lib.hs_sig_bytes.restype = C.c_size_t
+    assert lib.hs_sig_bytes(7) == 0
+    lib.hs_sign_kernel_count.restype = C.c_int
+    assert lib.hs_sign_kernel_count() == 7
+
+
+def test_count_zero_and_bad_enum_need_no_gpu(lib):
+    lib.hs_sign_batch.restype = C.c_int
+    lib.hs_sign_batch.argtypes = [C.c_int, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_uint32, C.c_void_p, C.c_void_p]
+    assert lib.hs_sign_batch(9, None, 1, None, None, None, 1, None, None) == 1      # HS_EINVAL
+    assert lib.hs_sign_batch(0, None, 1, None, None, None, 0, None, None) == 0      # count 0: no-op
+    lib.hs_last_error.restype = C.c_char_p
+    assert b"parameter set" in lib.hs_last_error()
+
+
+def test_product_never_imports_oracle():
+    pkg = os.path.join(ROOT, "paper_2512_23969_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
+                assert "spx_oracle" not in text, f
