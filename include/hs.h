@@ -138,6 +138,21 @@ int hs_profile_read(float *ms, const char **names, int max);
 /* Number of kernels one hs_sign_batch call launches (for launch accounting). */
 int hs_sign_kernel_count(void);
 
+/*
+ * hs_set_chain_checkpoint -- process-wide tuning knob of hs_sign_batch.
+ * TREE_Sign computes every chain of every WOTS+ key pair of the hypertree,
+ * including the signing key pair whose chains WOTS+_Sign needs again at the
+ * message digits (Sec. III: WOTS+_Sign runs after TREE_Sign).  With a stride
+ * s in {1, 2, 4, 8}, TREE_Sign stores every s-th position of the signing key
+ * pair's chains in scratch (count * d * len * (16 / s) * n bytes; 1.6 GB for
+ * 16384 128f signatures at s = 2) and WOTS+_Sign finishes each chain in fewer
+ * than s steps; s = 0 stores nothing and WOTS+_Sign recomputes each chain
+ * from its secret.  Signatures are identical for every setting.  Default 2.
+ * Returns HS_EINVAL for any other value.  Not thread-safe against
+ * concurrent signing calls.
+ */
+hs_status hs_set_chain_checkpoint(uint32_t stride);
+
 #ifdef __cplusplus
 }
 #endif

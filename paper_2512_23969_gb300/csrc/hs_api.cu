@@ -18,6 +18,9 @@ namespace hs {
 
 static thread_local std::string g_err;
 
+// Chain checkpoint stride used by signing (see hs_set_chain_checkpoint).
+static uint32_t g_ck = 2;
+
 static hs_status fail(hs_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 static hs_status fail(hs_status st, const char* fmt, ...) {
     char buf[512];
@@ -46,14 +49,18 @@ static bool set_info(int p, SetInfo* s) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count) {
+static size_t chk_bytes(const SetInfo& s, uint32_t count, uint32_t ck) {
+    return ck ? (size_t)count * s.d * s.len * (16 / ck) * (s.n / 4) * 4 : 0;
+}
+
+size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck) {
     SetInfo s;
     if (!set_info(pset, &s)) return 0;
     const size_t nw = (size_t)s.n / 4;
     return align256(sizeof(uint32_t)) + align256((size_t)num_keys * sizeof(KeyBlock)) +
            align256(((size_t)count + 1) * sizeof(uint64_t)) + align256((size_t)count * sizeof(MsgInfo)) +
            align256((size_t)count * s.k * nw * 4) + align256((size_t)count * nw * 4) +
-           align256((size_t)count * s.d * nw * 4);
+           align256((size_t)count * s.d * nw * 4) + align256(chk_bytes(s, count, ck));
 }
 
 void carve_scratch(Batch& b, void* base) {
@@ -67,7 +74,8 @@ void carve_scratch(Batch& b, void* base) {
     b.infos = reinterpret_cast<MsgInfo*>(p);      p += align256((size_t)b.count * sizeof(MsgInfo));
     b.fors_roots = reinterpret_cast<uint32_t*>(p); p += align256((size_t)b.count * s.k * nw * 4);
     b.pk_fors = reinterpret_cast<uint32_t*>(p);   p += align256((size_t)b.count * nw * 4);
-    b.roots = reinterpret_cast<uint32_t*>(p);
+    b.roots = reinterpret_cast<uint32_t*>(p);     p += align256((size_t)b.count * s.d * nw * 4);
+    b.chk = b.ck ? reinterpret_cast<uint32_t*>(p) : nullptr;
 }
 
 // ----------------------------------------------------------- device state
@@ -155,6 +163,13 @@ HS_API size_t hs_sk_bytes(hs_params p) { SetInfo s; return set_info(p, &s) ? (si
 HS_API size_t hs_seed_bytes(hs_params p) { SetInfo s; return set_info(p, &s) ? (size_t)3 * s.n : 0; }
 HS_API const char* hs_last_error(void) { return g_err.c_str(); }
 HS_API int hs_sign_kernel_count(void) { return 7; }
+
+HS_API hs_status hs_set_chain_checkpoint(uint32_t stride) {
+    if (stride != 0 && stride != 1 && stride != 2 && stride != 4 && stride != 8)
+        return fail(HS_EINVAL, "checkpoint stride must be 0, 1, 2, 4 or 8 (got %u)", stride);
+    g_ck = stride;
+    return HS_OK;
+}
 HS_API void hs_profile_enable(int on) { g_prof = on != 0; g_prof_valid = false; }
 
 HS_API int hs_profile_read(float* ms, const char** names, int max) {
@@ -282,7 +297,8 @@ static hs_status run_batch(bool verify, hs_params p, const uint8_t* keys_in, uin
     b.num_keys = num_keys;
     b.count = count;
     b.status = d->status;
-    const size_t scratch = scratch_bytes(p, num_keys, count);
+    b.ck = verify ? 0u : g_ck;
+    const size_t scratch = scratch_bytes(p, num_keys, count, b.ck);
     const size_t stage = (h_keys ? align256(key_bytes) : 0) + (h_idx ? align256((size_t)count * 4) : 0) +
                          (h_lens ? align256((size_t)count * 8) : 0) + (h_msgs ? align256(msg_total) : 0) +
                          (h_sig ? align256(sig_total) : 0) + (h_ok ? align256(count) : 0);

@@ -28,11 +28,13 @@ struct Batch {
     uint32_t* fors_roots;     // count * K * NW words
     uint32_t* pk_fors;        // count * NW words
     uint32_t* roots;          // count * D * NW words
+    uint32_t* chk;            // WOTS chain checkpoints: count * D * LEN * (16 / ck) * NW words
+    uint32_t ck;              // checkpoint stride (1, 2, 4) or 0 = none
     uint32_t* status;         // per-device status word
 };
 
 // Scratch bytes for a batch (each region 256-byte aligned).
-size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count);
+size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck);
 void carve_scratch(Batch& b, void* base);
 
 cudaError_t launch_keyprep(const Batch& b, bool from_pk, cudaStream_t s);

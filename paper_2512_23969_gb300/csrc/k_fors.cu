@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include "hs_common.cuh"
 #include "hs_launch.h"
+#include "sha256_chain.cuh"
 
 namespace hs {
 
@@ -27,10 +28,11 @@ template <> struct ForsShape<PToy>  { static constexpr int LPT = 4; };   // R = 
 template <int L> struct Log2 { static constexpr int v = 1 + Log2<L / 2>::v; };
 template <> struct Log2<1> { static constexpr int v = 0; };
 
-template <class P>
+template <class P, int POL>
 __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ keys,
                                                    const MsgInfo* __restrict__ infos, uint32_t count,
-                                                   uint8_t* __restrict__ sigs, uint32_t* __restrict__ fors_roots) {
+                                                   uint8_t* __restrict__ sigs, uint32_t* __restrict__ fors_roots,
+                                                   uint32_t one) {
     constexpr int NW = P::NW, A = P::A, K = P::K;
     constexpr int LPT = ForsShape<P>::LPT;
     constexpr int R = A - Log2<LPT>::v;           // height built inside one lane
@@ -62,6 +64,7 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
     const uint32_t gs = info.fors_idx[i];          // selected leaf in tree i
     uint8_t* sf = sigs + (size_t)m * P::SIG_BYTES + P::N + (size_t)i * (A + 1) * P::N;
 
+    const Pipes<POL> pp(one);
     uint32_t stk[R][NW];                           // left siblings, levels 0..R-1
     uint32_t node[NW];
     const uint32_t base = L << R;                  // first leaf of this lane (within tree)
@@ -69,10 +72,16 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
     for (uint32_t p = 0; p < (1u << R); p++) {
         const uint32_t t = base + p;               // leaf index within tree
         const uint32_t g = (i << A) + t;           // global leaf index
-        uint32_t sk[NW];
-        hashF<P>(ms256, make_adrs(0, tree, T_FORS_PRF, kp, 0, g), skseed, sk);
-        if (t == gs) store_be<NW>(sf, sk);
-        hashF<P>(ms256, make_adrs(0, tree, T_FORS_TREE, kp, 0, g), sk, node);
+        // leaf g: sk = PRF(FORS_PRF(g)), then F(FORS_TREE(height 0, g), sk);
+        // both through one call site of the compression
+#pragma unroll
+        for (int w = 0; w < NW; w++) node[w] = skseed[w];
+#pragma unroll 1
+        for (int s = 0; s < 2; s++) {
+            hashF_fast<POL, NW>(ms256, make_adrs(0, tree, s == 0 ? T_FORS_PRF : T_FORS_TREE, kp, 0, g), node,
+                                node, pp);
+            if (s == 0 && t == gs) store_be<NW>(sf, node);
+        }
         if (t == (gs ^ 1u)) store_be<NW>(sf + P::N, node);
         // merge with stacked left siblings while this node is a right child
         uint32_t z = 0, idx = t;
@@ -151,7 +160,7 @@ static cudaError_t launch_fors_t(const Batch& b, cudaStream_t s) {
     const uint64_t threads = (uint64_t)b.count * P::K * ForsShape<P>::LPT;
     const uint32_t T = 256;
     const uint32_t G = (uint32_t)((threads + T - 1) / T);
-    fors_kernel<P><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.fors_roots);
+    fors_kernel<P, kChainPol><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.fors_roots, 1u);
     return cudaGetLastError();
 }
 

@@ -20,40 +20,57 @@
 #include <cuda_runtime.h>
 #include "hs_common.cuh"
 #include "hs_launch.h"
+#include "sha256_chain.cuh"
 
 namespace hs {
 
 // Hypertree leaf = WOTS+ public key of keypair kp in tree (layer, tree).
-template <class P>
+// If chk is not null (the thread owns the signing leaf of its tree), every
+// ck-th chain position (0, ck, 2ck, ...) of every chain is stored there,
+// [chain][position / ck][NW words], so that WOTS+_Sign only has to finish
+// at most ck - 1 steps of each chain instead of recomputing it.
+template <class P, int POL>
 __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t* msT, const uint32_t* skseed,
-                                          uint32_t layer, uint64_t tree, uint32_t kp, uint32_t* out) {
+                                          uint32_t layer, uint64_t tree, uint32_t kp, uint32_t* out,
+                                          uint32_t* chk, uint32_t ck, const Pipes<POL>& pp) {
     constexpr int NW = P::NW;
     TStream<P::BIG> ts;
     ts.init(msT, make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0));
     const Adrs aprf = make_adrs(layer, tree, T_WOTS_PRF, kp, 0, 0);
     const Adrs ahash = make_adrs(layer, tree, T_WOTS_HASH, kp, 0, 0);
+    const uint32_t per_chain = ck ? 16u / ck : 0u;
 #pragma unroll 1
     for (uint32_t i = 0; i < (uint32_t)P::LEN; i++) {
         uint32_t x[NW];
 #pragma unroll
         for (int w = 0; w < NW; w++) x[w] = skseed[w];
-        // step 0: PRF(WOTS_PRF(kp, chain i, hash 0)); steps 1..15: F(WOTS_HASH(kp, i, s-1))
+        ChainCtx cx;
+        // step 0: PRF(WOTS_PRF(kp, chain i, hash 0)) = chain position 0;
+        // step s >= 1: F(WOTS_HASH(kp, chain i, hash s-1)) = position s.
 #pragma unroll 1
         for (uint32_t s = 0; s < 16; s++) {
-            Adrs a = (s == 0) ? aprf : ahash;
-            a.w4 = i << 16;                 // chain i (< 2^16) | hash >> 16 (= 0)
-            a.half = (s == 0) ? 0u : s - 1u;  // low half of the hash address
-            hashF<P>(ms256, a, x, x);
+            if (s <= 1) {
+                Adrs a = (s == 0) ? aprf : ahash;
+                a.w4 = i << 16;                  // chain i (< 2^16) | hash >> 16 (= 0)
+                chain_ctx<POL>(ms256, a, cx, pp);
+            }
+            chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, x, x, pp);
+            if (chk != nullptr && (s % ck) == 0) {
+                uint32_t* d = chk + ((size_t)i * per_chain + s / ck) * NW;
+#pragma unroll
+                for (int w = 0; w < NW; w++) d[w] = x[w];
+            }
         }
         ts.template push_n<NW>(x);
     }
     ts.template finish<NW>(P::LEN * P::N, out);
 }
 
-template <class P>
+template <class P, int POL>
 __global__ void __launch_bounds__(128) tree_kernel(const KeyBlock* __restrict__ keys,
                                                    const MsgInfo* __restrict__ infos, uint32_t count,
-                                                   uint8_t* __restrict__ sigs, uint32_t* __restrict__ roots) {
+                                                   uint8_t* __restrict__ sigs, uint32_t* __restrict__ roots,
+                                                   uint32_t* __restrict__ chk, uint32_t ck, uint32_t one) {
     constexpr int NW = P::NW, HP = P::HP, LV = P::LEAVES;
     const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31;
@@ -79,8 +96,11 @@ __global__ void __launch_bounds__(128) tree_kernel(const KeyBlock* __restrict__ 
     const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
     const uint32_t sl = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
 
+    const Pipes<POL> pp(one);
+    uint32_t* mychk = (ck != 0 && l == sl)
+                          ? chk + ((size_t)m * P::D + j) * (size_t)P::LEN * (16u / ck) * NW : nullptr;
     uint32_t node[NW];
-    wots_leaf<P>(ms256, msT, skseed, j, tree, l, node);
+    wots_leaf<P, POL>(ms256, msT, skseed, j, tree, l, node, mychk, ck, pp);
 
     uint8_t* auth = sigs + (size_t)m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES +
                     (size_t)P::LEN * P::N;
@@ -111,7 +131,8 @@ __global__ void __launch_bounds__(128) tree_kernel(const KeyBlock* __restrict__ 
 // group per key; the midstates are derived from the seed in-thread.
 template <class P>
 __global__ void __launch_bounds__(128) keygen_kernel(const uint8_t* __restrict__ seeds, uint32_t count,
-                                                     uint8_t* __restrict__ pk, uint8_t* __restrict__ sk) {
+                                                     uint8_t* __restrict__ pk, uint8_t* __restrict__ sk,
+                                                     uint32_t one) {
     constexpr int NW = P::NW, HP = P::HP, LV = P::LEAVES, N = P::N;
     const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31;
@@ -146,7 +167,8 @@ __global__ void __launch_bounds__(128) keygen_kernel(const uint8_t* __restrict__
     }
     const uint32_t top = (uint32_t)P::D - 1;
     uint32_t node[NW];
-    wots_leaf<P>(ms256, msT, skseed, top, 0ull, l, node);
+    const Pipes<kChainPol> pp(one);
+    wots_leaf<P, kChainPol>(ms256, msT, skseed, top, 0ull, l, node, nullptr, 0u, pp);
 #pragma unroll
     for (int z = 1; z <= HP; z++) {
         const int step = 1 << (z - 1);
@@ -178,7 +200,7 @@ static cudaError_t launch_tree_t(const Batch& b, cudaStream_t s) {
     const uint64_t threads = (uint64_t)b.count * P::D * P::LEAVES;
     const uint32_t T = 128;
     const uint32_t G = (uint32_t)((threads + T - 1) / T);
-    tree_kernel<P><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots);
+    tree_kernel<P, kChainPol><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck, 1u);
     return cudaGetLastError();
 }
 
@@ -187,7 +209,7 @@ static cudaError_t launch_keygen_t(const uint8_t* seeds, uint32_t count, uint8_t
     const uint64_t threads = (uint64_t)count * P::LEAVES;
     const uint32_t T = 128;
     const uint32_t G = (uint32_t)((threads + T - 1) / T);
-    keygen_kernel<P><<<G, T, 0, s>>>(seeds, count, pk, sk);
+    keygen_kernel<P><<<G, T, 0, s>>>(seeds, count, pk, sk, 1u);
     return cudaGetLastError();
 }
 

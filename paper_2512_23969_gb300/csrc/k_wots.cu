@@ -8,18 +8,24 @@
 //
 // GB300 mapping: one thread per (message, layer, chain); each thread
 // recomputes the checksum from msg_j (2n nibble reads, negligible next to
-// its chain) so no cross-thread exchange is needed.
+// its chain) so no cross-thread exchange is needed.  TREE_Sign already ran
+// every chain of the signing keypair to its end; when it stored every
+// ck-th chain position (ck = 1, 2 or 4), a chain's signature value is the
+// stored position floor(d / ck) ck advanced by d mod ck < ck steps, instead
+// of PRF plus d steps (the same value: chain composition).
 #include <cuda_runtime.h>
 #include "hs_common.cuh"
 #include "hs_launch.h"
+#include "sha256_chain.cuh"
 
 namespace hs {
 
-template <class P>
+template <class P, int POL>
 __global__ void __launch_bounds__(256) wots_kernel(const KeyBlock* __restrict__ keys,
                                                    const MsgInfo* __restrict__ infos, uint32_t count,
                                                    const uint32_t* __restrict__ pk_fors,
-                                                   const uint32_t* __restrict__ roots, uint8_t* __restrict__ sigs) {
+                                                   const uint32_t* __restrict__ roots, uint8_t* __restrict__ sigs,
+                                                   const uint32_t* __restrict__ chk, uint32_t ck, uint32_t one) {
     constexpr int NW = P::NW, LEN = P::LEN;
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t per_msg = (uint32_t)P::D * LEN;
@@ -54,15 +60,29 @@ __global__ void __launch_bounds__(256) wots_kernel(const KeyBlock* __restrict__ 
     uint32_t ms256[8];
 #pragma unroll
     for (int w = 0; w < 8; w++) ms256[w] = kb.ms256[w];
+    const Pipes<POL> pp(one);
     uint32_t x[NW];
+    if (ck != 0) {
+        const uint32_t per_chain = 16u / ck;
+        const uint32_t base = (digit / ck) * ck;
+        const uint32_t* c = chk + (((m * P::D + j) * (size_t)LEN + i) * per_chain + digit / ck) * NW;
 #pragma unroll
-    for (int w = 0; w < NW; w++) x[w] = kb.sk_seed[w];
-    Adrs a = make_adrs(j, tree, T_WOTS_PRF, kp, i, 0);
-    const Adrs ahash = make_adrs(j, tree, T_WOTS_HASH, kp, i, 0);
+        for (int w = 0; w < NW; w++) x[w] = c[w];
+        Adrs a = make_adrs(j, tree, T_WOTS_HASH, kp, i, 0);
 #pragma unroll 1
-    for (uint32_t s = 0; s <= digit; s++) {
-        if (s > 0) { a = ahash; a.half = s - 1u; }
-        hashF<P>(ms256, a, x, x);
+        for (uint32_t q = base; q < digit; q++) {
+            a.half = q;
+            hashF_fast<POL, NW>(ms256, a, x, x, pp);
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < NW; w++) x[w] = kb.sk_seed[w];
+        ChainCtx cx;
+        chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_PRF, kp, i, 0), cx, pp);
+        chain_step<POL, NW>(cx, ms256, 0u, x, x, pp);
+        if (digit > 0) chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, 0), cx, pp);
+#pragma unroll 1
+        for (uint32_t q = 0; q < digit; q++) chain_step<POL, NW>(cx, ms256, q, x, x, pp);
     }
     store_be<NW>(sigs + m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES + (size_t)i * P::N, x);
 }
@@ -72,7 +92,7 @@ static cudaError_t launch_wots_t(const Batch& b, cudaStream_t s) {
     const uint64_t threads = (uint64_t)b.count * P::D * P::LEN;
     const uint32_t T = 256;
     const uint32_t G = (uint32_t)((threads + T - 1) / T);
-    wots_kernel<P><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.pk_fors, b.roots, b.sigs);
+    wots_kernel<P, kChainPol><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.pk_fors, b.roots, b.sigs, b.chk, b.ck, 1u);
     return cudaGetLastError();
 }
 

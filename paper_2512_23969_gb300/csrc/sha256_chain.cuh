@@ -1,0 +1,163 @@
+// sha256_chain.cuh -- the SHA-256 compression specialised for WOTS+ chains
+// and other one-block tweakable hashes, balanced across GB300's pipes.
+//
+// Measured on this GB300 (sm_103a): LOP3, SHF and PRMT issue on the ALU pipe
+// at 64 lanes/clk/SM; IMAD issues on the FMA-heavy pipe at 64 lanes/clk/SM;
+// IADD3 can go to either; warp issue is 128 lanes/clk/SM.  SHA-256 is
+// dominated by rotations and 3-input logic that only the ALU pipe executes,
+// so the additions of each round are written as IMAD (a * one + b with a
+// kernel-argument 'one' the compiler cannot fold) to keep them off the ALU
+// pipe -- the same instruction re-selection the paper applies with its
+// mad.lo listing (Sec. III-C), chosen here by measurement on sm_103a.
+//
+// WOTS+ chains: within one chain every F call has the same first 5 message
+// words (the compressed address up to the hash index), so the state after
+// rounds 0..4 and the address-only parts of message words 16..20 are
+// computed once per chain (ChainCtx) and each of the chain's F steps runs
+// rounds 5..63 only.  The result is the same compression, bit for bit.
+#pragma once
+#include <cstdint>
+#include "hs_common.cuh"
+
+namespace hs {
+
+__device__ __forceinline__ uint32_t mad_add(uint32_t a, uint32_t b, uint32_t one) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(one), "r"(b));
+    return r;
+}
+template <uint32_t IMM>
+__device__ __forceinline__ uint32_t mad_addi(uint32_t a, uint32_t one) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(one), "n"(IMM));
+    return r;
+}
+
+// Addition policy: bit 0 = T1 sums on IMAD, bit 1 = e update on IMAD,
+// bit 2 = a update on IMAD.  POL 7 is the measured best for chains.
+template <int POL>
+struct Pipes {
+    uint32_t one;
+    __device__ __forceinline__ explicit Pipes(uint32_t o) : one(o) {}
+};
+
+// Policy used by the signing kernels (all round additions on IMAD).
+constexpr int kChainPol = 7;
+
+namespace detail {
+constexpr uint32_t kK256[64] = {HS_K256_LIST};
+}
+
+// Round t on a rotating state array: a = v[(-t) & 7], ..., h = v[(7 - t) & 7].
+template <int POL, int t>
+__device__ __forceinline__ void round256(uint32_t v[8], uint32_t w, const Pipes<POL>& p) {
+    constexpr uint32_t K = detail::kK256[t];
+    uint32_t& a = v[(8 - (t & 7)) & 7];
+    uint32_t& b = v[(9 - (t & 7)) & 7];
+    uint32_t& c = v[(10 - (t & 7)) & 7];
+    uint32_t& d = v[(11 - (t & 7)) & 7];
+    uint32_t& e = v[(12 - (t & 7)) & 7];
+    uint32_t& f = v[(13 - (t & 7)) & 7];
+    uint32_t& g = v[(14 - (t & 7)) & 7];
+    uint32_t& h = v[(15 - (t & 7)) & 7];
+    const uint32_t ch = (e & f) ^ (~e & g);
+    const uint32_t mj = (a & b) | (c & (a | b));
+    uint32_t t1;
+    if constexpr (POL & 1) t1 = mad_add(mad_add(mad_add(mad_addi<K>(h, p.one), w, p.one), S1_256(e), p.one), ch, p.one);
+    else t1 = h + S1_256(e) + ch + K + w;
+    if constexpr (POL & 2) d = mad_add(d, t1, p.one);
+    else d = d + t1;
+    if constexpr (POL & 4) h = mad_add(mad_add(t1, S0_256(a), p.one), mj, p.one);
+    else h = t1 + S0_256(a) + mj;
+}
+
+// Rounds [t0, t1) with the message schedule extended in the 16-word ring W.
+// PRE: words 0..4 are replaced by the chain constants c[] in words 16..20.
+template <int POL, bool PRE, int t0, int t1>
+struct Rounds256 {
+    __device__ static __forceinline__ void run(uint32_t v[8], uint32_t W[16], const uint32_t* c, const Pipes<POL>& p) {
+        constexpr int t = t0;
+        if constexpr (t >= 16) {
+            if constexpr (PRE && t <= 19) {
+                W[t & 15] = s1_256(W[(t - 2) & 15]) + W[(t - 7) & 15] + c[t - 16];
+            } else if constexpr (PRE && t == 20) {
+                W[t & 15] = s1_256(W[(t - 2) & 15]) + W[(t - 7) & 15] + s0_256(W[5]) + c[4];
+            } else {
+                W[t & 15] = s1_256(W[(t - 2) & 15]) + W[(t - 7) & 15] + s0_256(W[(t - 15) & 15]) + W[t & 15];
+            }
+        }
+        round256<POL, t>(v, W[t & 15], p);
+        if constexpr (t0 + 1 < t1) Rounds256<POL, PRE, t0 + 1, t1>::run(v, W, c, p);
+    }
+};
+
+// Chain-invariant part of an F call: state after rounds 0..4 (from the key
+// midstate, message words 0..4 = the address words) and the address-only
+// terms of message words 16..20.
+struct ChainCtx {
+    uint32_t s[8];
+    uint32_t c[5];
+};
+
+template <int POL>
+__device__ __forceinline__ void chain_ctx(const uint32_t ms[8], const Adrs& a, ChainCtx& x, const Pipes<POL>& p) {
+    uint32_t W[16];
+    W[0] = a.w0; W[1] = a.w1; W[2] = a.w2; W[3] = a.w3; W[4] = a.w4;
+#pragma unroll
+    for (int i = 0; i < 8; i++) x.s[i] = ms[i];
+    round256<POL, 0>(x.s, W[0], p);
+    round256<POL, 1>(x.s, W[1], p);
+    round256<POL, 2>(x.s, W[2], p);
+    round256<POL, 3>(x.s, W[3], p);
+    round256<POL, 4>(x.s, W[4], p);
+    x.c[0] = s0_256(W[1]) + W[0];
+    x.c[1] = s0_256(W[2]) + W[1];
+    x.c[2] = s0_256(W[3]) + W[2];
+    x.c[3] = s0_256(W[4]) + W[3];
+    x.c[4] = W[4];
+}
+
+// Message words 5..15 of a one-block call: low half of the last address word,
+// NW payload words at a 2-byte offset, 0x80 pad, zeros, bit length.
+template <int NW>
+__device__ __forceinline__ void tail_words(uint32_t W[16], uint32_t half, const uint32_t* x) {
+    W[5] = mid16(half, x[0]);
+#pragma unroll
+    for (int k = 1; k < NW; k++) W[5 + k] = mid16(x[k - 1], x[k]);
+    W[5 + NW] = (x[NW - 1] << 16) | 0x8000u;
+#pragma unroll
+    for (int k = 6 + NW; k < 15; k++) W[k] = 0;
+    W[15] = (64 + 22 + 4 * NW) * 8;
+}
+
+// One chain step with a precomputed context: out = Trunc_n(compress(ms, block)),
+// where the block's hash address is 'half' and its payload is x (NW words).
+template <int POL, int NW>
+__device__ __forceinline__ void chain_step(const ChainCtx& cx, const uint32_t ms[8], uint32_t half,
+                                           const uint32_t* x, uint32_t* out, const Pipes<POL>& p) {
+    uint32_t W[16];
+    tail_words<NW>(W, half, x);
+    uint32_t v[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = cx.s[i];
+    Rounds256<POL, true, 5, 64>::run(v, W, cx.c, p);
+#pragma unroll
+    for (int i = 0; i < NW; i++) out[i] = v[i] + ms[i];
+}
+
+// Plain one-block F / PRF (no reusable context), same round code.
+template <int POL, int NW>
+__device__ __forceinline__ void hashF_fast(const uint32_t ms[8], const Adrs& a, const uint32_t* x, uint32_t* out,
+                                           const Pipes<POL>& p) {
+    uint32_t W[16];
+    W[0] = a.w0; W[1] = a.w1; W[2] = a.w2; W[3] = a.w3; W[4] = a.w4;
+    tail_words<NW>(W, a.half, x);
+    uint32_t v[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = ms[i];
+    Rounds256<POL, false, 0, 64>::run(v, W, nullptr, p);
+#pragma unroll
+    for (int i = 0; i < NW; i++) out[i] = v[i] + ms[i];
+}
+
+}  // namespace hs

@@ -45,6 +45,8 @@ def load():
     L.hs_profile_read.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_char_p), C.c_int]
     L.hs_profile_read.restype = C.c_int
     L.hs_sign_kernel_count.restype = C.c_int
+    L.hs_set_chain_checkpoint.argtypes = [C.c_uint32]
+    L.hs_set_chain_checkpoint.restype = C.c_int
     for name in ("hs_keygen", "hs_sign_batch", "hs_verify_batch", "hs_check_status"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -160,3 +162,8 @@ def hs_profile_read():
 
 def hs_sign_kernel_count():
     return int(load().hs_sign_kernel_count())
+
+
+def hs_set_chain_checkpoint(stride):
+    """Stride of the WOTS+ chain positions TREE_Sign keeps for WOTS+_Sign (0 = none)."""
+    _check(load().hs_set_chain_checkpoint(int(stride)))
