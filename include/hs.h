@@ -153,6 +153,49 @@ int hs_sign_kernel_count(void);
  */
 hs_status hs_set_chain_checkpoint(uint32_t stride);
 
+/* Size of the fixed device buffer that hs_sign_batch_noalloc works in. */
+#define HS_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+
+/*
+ * hs_sign_batch_noalloc -- hs_sign_batch for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this entry point exists for
+ * users of the library.
+ *
+ * Who needs it: signing services that reserve all their device memory at
+ * start-up and must not allocate afterwards (an allocation at peak load can
+ * fail or fragment the heap), and host applications that embed this library
+ * and do not let it make device allocations of its own.  hs_sign_batch takes
+ * its scratch from a memory pool it creates, so those callers cannot use it.
+ *
+ * This variant allocates nothing: no cudaMalloc, cudaFree, pool or library
+ * allocation on any call.  Its scratch is one file-scope device array of
+ * HS_NOALLOC_SCRATCH_BYTES (8 MiB) that every GPU which loads this library
+ * holds until the process exits.  Arguments and outputs are those of
+ * hs_sign_batch, with these differences:
+ *  - every buffer (sk, key_idx, msgs, lens, sigs) must be device memory;
+ *    host pointers are rejected with HS_EINVAL (staging them would allocate);
+ *    msgs may not be NULL;
+ *  - a batch whose scratch does not fit the array is rejected with HS_EINVAL
+ *    and hs_last_error() states the bytes needed and available.  The need is
+ *    256 + 256 * num_keys + about 1.0 KB (128f), 1.4 KB (192f) or 1.8 KB
+ *    (256f) per message, so about 8000 / 5800 / 4600 messages fit;
+ *  - WOTS+_Sign recomputes its chains (no chain checkpoints are kept);
+ *  - a key_idx entry >= num_keys gives an all-zero signature for that
+ *    message; it is not reported through hs_check_status.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, and caches it; make that
+ * first call before any stream capture on the device.
+ * All calls on a device share the one array, and it keeps the previous
+ * call's contents (the call clears the words that must start at zero).
+ * Calls whose work overlaps on the GPU race on the array: issue them on one
+ * stream, or wait for one to finish before starting the next.
+ * Signatures are byte-identical to hs_sign_batch's.
+ */
+hs_status hs_sign_batch_noalloc(hs_params p, const uint8_t *sk, uint32_t num_keys,
+                                const uint32_t *key_idx, const uint8_t *msgs,
+                                const uint64_t *lens, uint32_t count, uint8_t *sigs,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,8 @@ static hs_status fail(hs_status st, const char* fmt, ...) {
     return st;
 }
 
+void set_last_error(const char* msg) { g_err = msg; }
+
 static hs_status cuda_fail(cudaError_t e, const char* what) {
     return fail(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }

@@ -33,6 +33,9 @@ struct Batch {
     uint32_t* status;         // per-device status word
 };
 
+// Record the text hs_last_error() returns on the calling thread.
+void set_last_error(const char* msg);
+
 // Scratch bytes for a batch (each region 256-byte aligned).
 size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck);
 void carve_scratch(Batch& b, void* base);

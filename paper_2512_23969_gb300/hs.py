@@ -45,6 +45,8 @@ def load():
     L.hs_profile_read.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_char_p), C.c_int]
     L.hs_profile_read.restype = C.c_int
     L.hs_sign_kernel_count.restype = C.c_int
+    L.hs_sign_batch_noalloc.argtypes = [C.c_int, vp, u32, vp, vp, u64p, u32, vp, vp]
+    L.hs_sign_batch_noalloc.restype = C.c_int
     L.hs_set_chain_checkpoint.argtypes = [C.c_uint32]
     L.hs_set_chain_checkpoint.restype = C.c_int
     for name in ("hs_keygen", "hs_sign_batch", "hs_verify_batch", "hs_check_status"):
@@ -167,3 +169,16 @@ def hs_sign_kernel_count():
 def hs_set_chain_checkpoint(stride):
     """Stride of the WOTS+ chain positions TREE_Sign keeps for WOTS+_Sign (0 = none)."""
     _check(load().hs_set_chain_checkpoint(int(stride)))
+
+
+def hs_sign_batch_noalloc(params, sk, msgs, lens, sigs, key_idx=None, num_keys=None, stream=None):
+    """Like hs_sign_batch, for callers that cannot allocate device memory:
+    all buffers (including the output ``sigs``) are caller-provided device
+    tensors, and the library works in its fixed 8 MiB device buffer."""
+    count = int(lens.shape[0])
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    if num_keys is None:
+        num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
+    _check(load().hs_sign_batch_noalloc(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), _ptr(msgs),
+                                        _ptr(lens), count, _ptr(sigs), _stream(stream)))
+    return sigs
