@@ -36,6 +36,14 @@ WORKLOAD = "SPHINCS+-SHA2-128f-simple, 16 keys, 16384 x 32 B messages, one batch
 # SHA-512 block on 32-bit lanes ~4000.
 OPS_C256 = 1384
 OPS_C512 = 4000
+# Of those, the work that only the ALU pipe (LOP3 / SHF / PRMT) can execute:
+# rotations, shifts and 3-input logic -- per SHA-256 round Sigma0, Sigma1 (3
+# rotations + 1 LOP3 each), Ch, Maj (1 LOP3 each) = 10, per schedule word
+# sigma0, sigma1 = 8 -> 64 x 10 + 48 x 8 = 1024; per SHA-512 compression on
+# 32-bit lanes (every 64-bit rotation or XOR is two 32-bit ops) 80 x 20 +
+# 64 x 16 = 2624.  Additions can run on the FMA pipe and are not counted.
+ALU_C256 = 1024
+ALU_C512 = 2624
 STAGE_WORK = {
     # set: {stage: (c256, c512)}
     "128f": {"tree": (22 * 8 * 35 * 16 + 22 * 8 * 10 + 22 * 7, 0),
@@ -53,6 +61,11 @@ STAGE_WORK = {
 def ops_per_sig(ps, stage):
     c256, c512 = STAGE_WORK[ps][stage]
     return c256 * OPS_C256 + c512 * OPS_C512
+
+
+def alu_ops_per_sig(ps, stage):
+    c256, c512 = STAGE_WORK[ps][stage]
+    return c256 * ALU_C256 + c512 * ALU_C512
 
 
 def int_peak_tops(sm_count, sm_mhz):
@@ -206,8 +219,9 @@ def run_own(args):
     torch.cuda.set_device(local)
     from paper_2512_23969_gb300 import build as hs_build
     hs_build.build()
-    from paper_2512_23969_gb300 import hs, inputs
+    from paper_2512_23969_gb300 import autotune, hs, inputs
     hs.load()
+    tuned = autotune.apply()
     props = torch.cuda.get_device_properties(local)
     sm_count = props.multi_processor_count
 
@@ -291,12 +305,19 @@ def run_own(args):
         if not torch.equal(sigs_h, sigs.cpu()):
             e2e["mismatch"] = True
 
-    # roofline of the dominant kernel (TREE_Sign), from its CUDA-event durations
+    # roofline of the dominant kernel (TREE_Sign), from its CUDA-event durations.
+    # Bound: the ALU pipe.  Peak = measured ALU-pipe lane-ops/clk/SM (LOP3 and
+    # SHF probes) x SMs x max SM clock; work = ALU-only ops of the algorithm.
+    pipes = hs.hs_probe_int_pipes()
+    alu_rate = min(pipes["lop3"], pipes["shf"])
     tree_ms = sum(stage_ms.get("tree", [0])) / max(1, len(stage_ms.get("tree", [1])))
     stage_avg = {k: round(sum(v) / len(v), 3) for k, v in stage_ms.items()}
     sm_mhz_peak = 2070.0
-    peak = int_peak_tops(sm_count, sm_mhz_peak)
-    achieved = ops_per_sig(ps, "tree") * count / (tree_ms / 1e3) / 1e12 if tree_ms > 0 else None
+    alu_peak = sm_count * alu_rate * sm_mhz_peak * 1e6 / 1e12
+    alu_work = alu_ops_per_sig(ps, "tree") * count
+    achieved = alu_work / (tree_ms / 1e3) / 1e12 if tree_ms > 0 else None
+    issue_peak = int_peak_tops(sm_count, sm_mhz_peak)
+    issue_achieved = ops_per_sig(ps, "tree") * count / (tree_ms / 1e3) / 1e12 if tree_ms > 0 else None
     traffic = None
     prof_file = os.path.join(ROOT, "profiles", "tree_%s_traffic.json" % ps)
     if os.path.exists(prof_file):
@@ -305,13 +326,20 @@ def run_own(args):
         except (OSError, ValueError):
             traffic = None
     roofline = {"bound": "alu", "kernel": "tree_kernel<%s> (TREE_Sign)" % ps,
-                "achieved": round(achieved, 3) if achieved else None, "peak": round(peak, 3),
-                "unit": "Tops/s", "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,
-                "peak_basis": "issue peak %d SMs x 128 int lanes/clk x %.0f MHz (max SM clock)" % (sm_count, sm_mhz_peak),
-                "ops_per_launch": ops_per_sig(ps, "tree") * count}
-    if clk.get("sm_mhz"):
-        roofline["frac_at_sampled_clock"] = round(achieved / int_peak_tops(sm_count, clk["sm_mhz"]), 4) \
-            if achieved else None
+                "achieved": round(achieved, 3) if achieved else None, "peak": round(alu_peak, 3),
+                "unit": "Tops/s", "frac": round(achieved / alu_peak, 4) if achieved else None, "traffic": traffic,
+                "peak_basis": "ALU pipe %.1f lane-ops/clk/SM (measured LOP3/SHF rate) x %d SMs x %.0f MHz"
+                              % (alu_rate, sm_count, sm_mhz_peak),
+                "work_basis": "%d ALU-pipe ops per SHA-256 compression, %d per SHA-512; %.4g per launch"
+                              % (ALU_C256, ALU_C512, alu_work),
+                "issue": {"achieved": round(issue_achieved, 3) if issue_achieved else None,
+                          "peak": round(issue_peak, 3),
+                          "frac": round(issue_achieved / issue_peak, 4) if issue_achieved else None,
+                          "basis": "%d int ops per SHA-256 compression vs %d SMs x 128 lanes/clk x %.0f MHz"
+                                   % (OPS_C256, sm_count, sm_mhz_peak)},
+                "measured_pipes_lane_ops_per_clk_per_sm": pipes}
+    if clk.get("sm_mhz") and achieved:
+        roofline["frac_at_sampled_clock"] = round(achieved / (sm_count * alu_rate * clk["sm_mhz"] * 1e6 / 1e12), 4)
 
     # CPU oracle baseline on a bounded sample
     cpu = None
@@ -341,6 +369,7 @@ def run_own(args):
         "verified": "%d/%d signatures accepted by GPU verify" % (n_ok, count),
         "wall_s": round(wall, 3),
         "device": props.name, "sm_count": sm_count,
+        "tuning": {k: autotune.get(ps, k) for k in autotune.KNOBS} | {"from_cache": bool(tuned)},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -135,6 +135,16 @@ const char *hs_last_error(void);
 void hs_profile_enable(int on);
 int hs_profile_read(float *ms, const char **names, int max);
 
+/*
+ * hs_probe_int_pipes -- measure the current GPU's integer issue rates for the
+ * roofline (the signer does not depend on it).  Writes up to 'max' rates in
+ * lane-operations per clock per SM, from SM cycle counters, for: 0 LOP3,
+ * 1 SHF (funnel shift), 2 IADD, 3 IMAD, 4 IMAD.HI, 5 PRMT, 6 LOP3+IMAD
+ * interleaved.  Synchronizes the device and allocates a few KB temporarily.
+ * Returns the number of rates written, or -1 on a CUDA error.
+ */
+int hs_probe_int_pipes(float *rates, int max);
+
 /* Number of kernels one hs_sign_batch call launches (for launch accounting). */
 int hs_sign_kernel_count(void);
 
@@ -152,6 +162,24 @@ int hs_sign_kernel_count(void);
  * concurrent signing calls.
  */
 hs_status hs_set_chain_checkpoint(uint32_t stride);
+
+/*
+ * Launch-shape tuning, per parameter set (process-wide).  Signatures are
+ * identical for every setting; only speed changes.  Knobs:
+ *   HS_TUNE_FORS_LANES      lanes of a warp that share one FORS tree
+ *                           (each lane builds a subtree of 2^a / lanes
+ *                           leaves, the rest merges by shuffles)
+ *   HS_TUNE_TREE_MIN_BLOCKS minimum resident 128-thread blocks per SM that
+ *                           TREE_Sign is compiled for (0 = compiler's choice)
+ * hs_tune_options lists the compiled values (returns their number, or -1);
+ * hs_tune_set returns HS_EINVAL for a value that is not compiled in;
+ * hs_tune_get returns the current value (-1 for bad arguments).  The
+ * package's autotuner measures these and stores the best per device.
+ */
+typedef enum { HS_TUNE_FORS_LANES = 0, HS_TUNE_TREE_MIN_BLOCKS = 1 } hs_tune_knob;
+int hs_tune_options(hs_params p, int knob, int32_t *values, int max);
+hs_status hs_tune_set(hs_params p, int knob, int32_t value);
+int32_t hs_tune_get(hs_params p, int knob);
 
 /* Size of the fixed device buffer that hs_sign_batch_noalloc works in. */
 #define HS_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)

@@ -1,0 +1,144 @@
+"""Measured launch-shape autotuner for the signer's kernels.
+
+The library compiles a few launch-shape variants per parameter set (lanes per
+FORS tree; minimum resident blocks of TREE_Sign) and exposes them through
+``hs_tune_options`` / ``hs_tune_set`` (include/hs.h).  This module times each
+variant on a seeded batch with the library's own per-stage CUDA events and
+keeps the fastest, in a JSON cache keyed by the device (name, SM count,
+compute capability, driver) so that a later process can apply it without
+re-measuring.  Signatures are identical for every setting, so the choice is
+purely about speed -- the same idea as the paper's offline tuning followed by
+profiling-based selection (Sec. III-B-2, III-C), with measurement on the
+target GPU in place of Alg. 1's analytic model.
+"""
+import ctypes as C
+import json
+import os
+
+import numpy as np
+
+from . import hs, inputs
+
+KNOBS = {"fors_lanes": 0, "tree_min_blocks": 1}
+STAGE_OF_KNOB = {"fors_lanes": "fors", "tree_min_blocks": "tree"}
+DEFAULT_COUNTS = {"128f": 16384, "192f": 8192, "256f": 8192, "toy": 4096}
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
+def options(params, knob):
+    L = hs.load()
+    L.hs_tune_options.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int32), C.c_int]
+    L.hs_tune_options.restype = C.c_int
+    vals = (C.c_int32 * 16)()
+    n = L.hs_tune_options(hs.PARAMS[params], KNOBS[knob], vals, 16)
+    return [int(v) for v in vals[:max(n, 0)]]
+
+
+def get(params, knob):
+    L = hs.load()
+    L.hs_tune_get.argtypes = [C.c_int, C.c_int]
+    L.hs_tune_get.restype = C.c_int32
+    return int(L.hs_tune_get(hs.PARAMS[params], KNOBS[knob]))
+
+
+def set(params, knob, value):   # noqa: A001 - mirrors hs_tune_set
+    L = hs.load()
+    L.hs_tune_set.argtypes = [C.c_int, C.c_int, C.c_int32]
+    L.hs_tune_set.restype = C.c_int
+    rc = L.hs_tune_set(hs.PARAMS[params], KNOBS[knob], int(value))
+    if rc != 0:
+        raise hs.HSError(rc, L.hs_last_error().decode())
+
+
+def device_key():
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    drv = C.c_int(0)
+    try:
+        C.CDLL("libcuda.so.1").cuDriverGetVersion(C.byref(drv))
+    except OSError:
+        pass
+    return "%s|sm%d%d|%dSM|drv%d" % (p.name, p.major, p.minor, p.multi_processor_count, drv.value)
+
+
+def _batch(params, count, seed=4242):
+    import torch
+    wl = inputs.make(params, count, 16, 32, seed)
+    pk, sk = hs.hs_keygen(params, torch.from_numpy(wl.seeds).cuda())
+    dev = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("msgs", "lens", "key_idx")}
+    sigs = torch.empty(count * hs.sig_bytes(params), dtype=torch.uint8, device="cuda")
+    return wl, sk, dev, sigs
+
+
+def _stage_ms(params, wl, sk, dev, sigs, stage, reps):
+    import torch
+    hs.hs_profile_enable(True)
+    best = float("inf")
+    for _ in range(reps + 1):                       # first call warms up
+        hs.hs_sign_batch(params, sk, dev["msgs"], dev["lens"], key_idx=dev["key_idx"], sigs=sigs,
+                         num_keys=wl.num_keys)
+        torch.cuda.synchronize()
+        best = min(best, hs.hs_profile_read()[stage])
+    hs.hs_profile_enable(False)
+    return best
+
+
+def tune(params_list=("128f", "192f", "256f"), counts=None, reps=3, verbose=True):
+    """Time every compiled variant of every knob; apply and return the best
+    ({params: {knob: {"best": v, "ms": {v: ms}}}})."""
+    import torch
+    result = {}
+    for ps in params_list:
+        count = (counts or {}).get(ps, DEFAULT_COUNTS[ps])
+        wl, sk, dev, sigs = _batch(ps, count)
+        ref = None
+        result[ps] = {}
+        for knob, stage in STAGE_OF_KNOB.items():
+            timings = {}
+            for v in options(ps, knob):
+                set(ps, knob, v)
+                timings[v] = _stage_ms(ps, wl, sk, dev, sigs, stage, reps)
+                cur = sigs.clone()
+                if ref is None:
+                    ref = cur
+                elif not torch.equal(ref, cur):
+                    raise RuntimeError("tuning %s=%d changed the signatures of %s" % (knob, v, ps))
+                if verbose:
+                    print("tune %s %s=%d: %s %.3f ms" % (ps, knob, v, stage, timings[v]), flush=True)
+            best = min(timings, key=timings.get)
+            set(ps, knob, best)
+            result[ps][knob] = {"best": best, "ms": {str(k): round(t, 4) for k, t in timings.items()},
+                                "count": count}
+    return result
+
+
+def save(result, path=CACHE):
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data[device_key()] = result
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+
+
+def apply(path=CACHE):
+    """Apply the cached choices for this device; return them (or {} if none)."""
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        data = json.load(f)
+    entry = data.get(device_key(), {})
+    for ps, knobs in entry.items():
+        for knob, rec in knobs.items():
+            if rec.get("best") in options(ps, knob):
+                set(ps, knob, rec["best"])
+    return entry
+
+
+if __name__ == "__main__":
+    import sys
+    sets = sys.argv[1:] or ["128f", "192f", "256f"]
+    res = tune(sets)
+    save(res)
+    print(json.dumps(res, indent=1))

@@ -1,0 +1,78 @@
+// dispatch.cu -- routes each launch to the parameter set's table with the
+// tuned launch shape (see hs_tune_set in include/hs.h).
+#include <atomic>
+#include "hs_launch.h"
+
+namespace hs {
+
+const SetOps* set_ops(int pset) {
+    switch (pset) {
+    case 0: return &kOps_128F;
+    case 1: return &kOps_192F;
+    case 2: return &kOps_256F;
+    case 3: return &kOps_Toy;
+    }
+    return nullptr;
+}
+
+namespace {
+// -1 = not set: use the table's default.
+std::atomic<int> g_tune[4][2] = {{{-1}, {-1}}, {{-1}, {-1}}, {{-1}, {-1}}, {{-1}, {-1}}};
+}
+
+int tune_get(int pset, int knob) {
+    const SetOps* o = set_ops(pset);
+    if (!o || knob < 0 || knob > 1) return -1;
+    const int v = g_tune[pset][knob].load();
+    if (v >= 0) return v;
+    return knob == 0 ? o->fors_lpt_default : o->tree_minb_default;
+}
+
+bool tune_set(int pset, int knob, int value) {
+    const SetOps* o = set_ops(pset);
+    if (!o || knob < 0 || knob > 1) return false;
+    const int* opts = knob == 0 ? o->fors_lpt : o->tree_minb;
+    const int n = knob == 0 ? o->n_fors_lpt : o->n_tree_minb;
+    for (int i = 0; i < n; i++)
+        if (opts[i] == value) {
+            g_tune[pset][knob].store(value);
+            return true;
+        }
+    return false;
+}
+
+cudaError_t launch_keyprep(const Batch& b, bool from_pk, cudaStream_t s) {
+    const SetOps* o = set_ops(b.pset);
+    return o ? o->keyprep(b, from_pk, s) : cudaErrorInvalidValue;
+}
+cudaError_t launch_message(const Batch& b, bool verify, cudaStream_t s) {
+    const SetOps* o = set_ops(b.pset);
+    return o ? o->message(b, verify, s) : cudaErrorInvalidValue;
+}
+cudaError_t launch_fors(const Batch& b, cudaStream_t s) {
+    const SetOps* o = set_ops(b.pset);
+    return o ? o->fors(b, tune_get(b.pset, 0), s) : cudaErrorInvalidValue;
+}
+cudaError_t launch_fors_pk(const Batch& b, cudaStream_t s) {
+    const SetOps* o = set_ops(b.pset);
+    return o ? o->fors_pk(b, s) : cudaErrorInvalidValue;
+}
+cudaError_t launch_tree(const Batch& b, cudaStream_t s) {
+    const SetOps* o = set_ops(b.pset);
+    return o ? o->tree(b, tune_get(b.pset, 1), s) : cudaErrorInvalidValue;
+}
+cudaError_t launch_wots(const Batch& b, cudaStream_t s) {
+    const SetOps* o = set_ops(b.pset);
+    return o ? o->wots(b, s) : cudaErrorInvalidValue;
+}
+cudaError_t launch_verify(const Batch& b, cudaStream_t s) {
+    const SetOps* o = set_ops(b.pset);
+    return o ? o->verify(b, s) : cudaErrorInvalidValue;
+}
+cudaError_t launch_keygen(int pset, const uint8_t* seeds, uint32_t count, uint8_t* pk, uint8_t* sk,
+                          cudaStream_t s) {
+    const SetOps* o = set_ops(pset);
+    return o ? o->keygen(seeds, count, pk, sk, s) : cudaErrorInvalidValue;
+}
+
+}  // namespace hs

@@ -166,6 +166,24 @@ HS_API size_t hs_seed_bytes(hs_params p) { SetInfo s; return set_info(p, &s) ? (
 HS_API const char* hs_last_error(void) { return g_err.c_str(); }
 HS_API int hs_sign_kernel_count(void) { return 7; }
 
+HS_API int hs_tune_options(hs_params p, int knob, int32_t* values, int max) {
+    const SetOps* o = set_ops(p);
+    if (!o || knob < 0 || knob > 1) return -1;
+    const int* opts = knob == 0 ? o->fors_lpt : o->tree_minb;
+    const int n = knob == 0 ? o->n_fors_lpt : o->n_tree_minb;
+    for (int i = 0; i < n && i < max; i++)
+        if (values) values[i] = opts[i];
+    return n;
+}
+
+HS_API hs_status hs_tune_set(hs_params p, int knob, int32_t value) {
+    if (!tune_set(p, knob, value))
+        return fail(HS_EINVAL, "tuning value %d is not available for set %d, knob %d", value, (int)p, knob);
+    return HS_OK;
+}
+
+HS_API int32_t hs_tune_get(hs_params p, int knob) { return tune_get(p, knob); }
+
 HS_API hs_status hs_set_chain_checkpoint(uint32_t stride) {
     if (stride != 0 && stride != 1 && stride != 2 && stride != 4 && stride != 8)
         return fail(HS_EINVAL, "checkpoint stride must be 0, 1, 2, 4 or 8 (got %u)", stride);

@@ -40,6 +40,33 @@ void set_last_error(const char* msg);
 size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck);
 void carve_scratch(Batch& b, void* base);
 
+// Per-parameter-set kernel launchers (one table per set_<name>.cu).  The
+// FORS and TREE launchers take the tuned launch shape: lanes per FORS tree
+// and the minimum resident blocks per SM of TREE_Sign (0 = compiler choice);
+// the arrays list the compiled variants, the *_default fields the defaults.
+struct SetOps {
+    cudaError_t (*keyprep)(const Batch&, bool, cudaStream_t);
+    cudaError_t (*message)(const Batch&, bool, cudaStream_t);
+    cudaError_t (*fors)(const Batch&, int, cudaStream_t);
+    cudaError_t (*fors_pk)(const Batch&, cudaStream_t);
+    cudaError_t (*tree)(const Batch&, int, cudaStream_t);
+    cudaError_t (*wots)(const Batch&, cudaStream_t);
+    cudaError_t (*verify)(const Batch&, cudaStream_t);
+    cudaError_t (*keygen)(const uint8_t*, uint32_t, uint8_t*, uint8_t*, cudaStream_t);
+    const int* fors_lpt;
+    int n_fors_lpt;
+    int fors_lpt_default;
+    const int* tree_minb;
+    int n_tree_minb;
+    int tree_minb_default;
+};
+extern const SetOps kOps_128F, kOps_192F, kOps_256F, kOps_Toy;
+const SetOps* set_ops(int pset);
+
+// Tuned launch shape per set (knob 0 = FORS lanes per tree, 1 = TREE min blocks).
+int tune_get(int pset, int knob);
+bool tune_set(int pset, int knob, int value);
+
 cudaError_t launch_keyprep(const Batch& b, bool from_pk, cudaStream_t s);
 cudaError_t launch_offsets(const Batch& b, cudaStream_t s);
 cudaError_t launch_message(const Batch& b, bool verify, cudaStream_t s);

@@ -1,4 +1,4 @@
-// k_fors.cu -- FORS_Sign (paper Sec. III-B) and the FORS public key.
+// kern_fors.cuh -- FORS_Sign (paper Sec. III-B) and the FORS public key.
 //
 // What it computes (Sec. II-A-2): for each of the k trees of height a, the
 // leaves F(FORS_TREE(0, g), PRF(FORS_PRF(g))) with g = i 2^a + j, the
@@ -12,6 +12,7 @@
 // stack), then the top log2(LPT) levels are merged across the group with
 // warp shuffles.  No shared memory and no block barriers; the grid is flat
 // over (message, tree, lane), so every message's k trees run in parallel.
+#pragma once
 #include <cuda_runtime.h>
 #include "hs_common.cuh"
 #include "hs_launch.h"
@@ -19,24 +20,17 @@
 
 namespace hs {
 
-template <class P> struct ForsShape;
-template <> struct ForsShape<P128f> { static constexpr int LPT = 8; };   // R = 3
-template <> struct ForsShape<P192f> { static constexpr int LPT = 32; };  // R = 3
-template <> struct ForsShape<P256f> { static constexpr int LPT = 32; };  // R = 4
-template <> struct ForsShape<PToy>  { static constexpr int LPT = 4; };   // R = 1
-
 template <int L> struct Log2 { static constexpr int v = 1 + Log2<L / 2>::v; };
 template <> struct Log2<1> { static constexpr int v = 0; };
 
-template <class P, int POL>
+template <class P, int POL, int LPT>
 __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ keys,
                                                    const MsgInfo* __restrict__ infos, uint32_t count,
                                                    uint8_t* __restrict__ sigs, uint32_t* __restrict__ fors_roots,
                                                    uint32_t one) {
     constexpr int NW = P::NW, A = P::A, K = P::K;
-    constexpr int LPT = ForsShape<P>::LPT;
     constexpr int R = A - Log2<LPT>::v;           // height built inside one lane
-    static_assert(R >= 1 && R <= 4, "lane subtree height");
+    static_assert(R >= 1 && R <= 7, "lane subtree height");
     const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t L = gid % LPT;                  // lane within the tree group
@@ -153,42 +147,6 @@ __global__ void fors_pk_kernel(const KeyBlock* __restrict__ keys, const MsgInfo*
     ts.template finish<NW>(P::K * P::N, out);
 #pragma unroll
     for (int w = 0; w < NW; w++) pk_fors[(size_t)m * NW + w] = out[w];
-}
-
-template <class P>
-static cudaError_t launch_fors_t(const Batch& b, cudaStream_t s) {
-    const uint64_t threads = (uint64_t)b.count * P::K * ForsShape<P>::LPT;
-    const uint32_t T = 256;
-    const uint32_t G = (uint32_t)((threads + T - 1) / T);
-    fors_kernel<P, kChainPol><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.fors_roots, 1u);
-    return cudaGetLastError();
-}
-
-template <class P>
-static cudaError_t launch_fors_pk_t(const Batch& b, cudaStream_t s) {
-    const uint32_t T = 128, G = (b.count + T - 1) / T;
-    fors_pk_kernel<P><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.fors_roots, b.pk_fors);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fors(const Batch& b, cudaStream_t s) {
-    switch (b.pset) {
-    case 0: return launch_fors_t<P128f>(b, s);
-    case 1: return launch_fors_t<P192f>(b, s);
-    case 2: return launch_fors_t<P256f>(b, s);
-    case 3: return launch_fors_t<PToy>(b, s);
-    }
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_fors_pk(const Batch& b, cudaStream_t s) {
-    switch (b.pset) {
-    case 0: return launch_fors_pk_t<P128f>(b, s);
-    case 1: return launch_fors_pk_t<P192f>(b, s);
-    case 2: return launch_fors_pk_t<P256f>(b, s);
-    case 3: return launch_fors_pk_t<PToy>(b, s);
-    }
-    return cudaErrorInvalidValue;
 }
 
 }  // namespace hs

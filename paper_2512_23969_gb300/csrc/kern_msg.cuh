@@ -1,4 +1,4 @@
-// k_msg.cu -- per-key preparation, message offsets and the message stage.
+// kern_msg.cuh -- per-key preparation and the message stage (kernel templates).
 //
 // Message stage (the paper's hash_message + message_to_indices, Fig. 2):
 //   R      = Trunc_n(HMAC-SHA-x(SK.prf, PK.seed || M))          (PRF_msg)
@@ -6,6 +6,7 @@
 //   digest = md || tree bytes || leaf bytes -> k FORS indices, idx_tree, idx_leaf
 // One thread per message; the work is serial in the message length (two
 // passes over M), which is the only length-dependent part of signing.
+#pragma once
 #include <cuda_runtime.h>
 #include "hs_common.cuh"
 #include "hs_launch.h"
@@ -128,28 +129,6 @@ __global__ void keyprep_kernel(const uint8_t* __restrict__ in, uint32_t num_keys
     out[k] = kb;
 }
 
-// ------------------------------------------------------------- offsets
-// offsets[i] = lens[0] + ... + lens[i-1], i = 0..count (one CTA of 1024).
-__global__ void offsets_kernel(const uint64_t* __restrict__ lens, uint32_t count, uint64_t* __restrict__ off) {
-    __shared__ uint64_t part[1024];
-    const uint32_t t = threadIdx.x;
-    const uint32_t chunk = (count + 1023) / 1024;
-    const uint64_t lo = (uint64_t)t * chunk;
-    uint64_t s = 0;
-    for (uint64_t i = lo; i < lo + chunk && i < count; i++) s += lens[i];
-    part[t] = s;
-    __syncthreads();
-    for (uint32_t d = 1; d < 1024; d <<= 1) {       // inclusive Hillis-Steele scan
-        uint64_t v = (t >= d) ? part[t - d] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    uint64_t run = (t == 0) ? 0 : part[t - 1];
-    for (uint64_t i = lo; i < lo + chunk && i < count; i++) { off[i] = run; run += lens[i]; }
-    if (t == 1023) off[count] = part[1023];
-}
-
 // ------------------------------------------------------------- message stage
 template <class P>
 __device__ __forceinline__ uint32_t digest_byte(const uint32_t* dw, int i) {
@@ -257,35 +236,6 @@ __global__ void message_kernel(const KeyBlock* __restrict__ keys, uint32_t num_k
     info.idx_leaf = l;
     info.key = key;
     infos[m] = info;
-}
-
-// ------------------------------------------------------------- launchers
-#define HS_DISPATCH(pset, CALL)                         \
-    switch (pset) {                                     \
-    case 0: { using P = P128f; CALL; } break;           \
-    case 1: { using P = P192f; CALL; } break;           \
-    case 2: { using P = P256f; CALL; } break;           \
-    case 3: { using P = PToy; CALL; } break;            \
-    default: return cudaErrorInvalidValue;              \
-    }
-
-cudaError_t launch_keyprep(const Batch& b, bool from_pk, cudaStream_t s) {
-    const uint32_t T = 128, G = (b.num_keys + T - 1) / T;
-    HS_DISPATCH(b.pset, (keyprep_kernel<P><<<G, T, 0, s>>>(b.keys_in, b.num_keys, from_pk ? 1 : 0, b.keys)));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_offsets(const Batch& b, cudaStream_t s) {
-    offsets_kernel<<<1, 1024, 0, s>>>(b.lens, b.count, b.offsets);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_message(const Batch& b, bool verify, cudaStream_t s) {
-    const uint32_t T = 64, G = (b.count + T - 1) / T;
-    HS_DISPATCH(b.pset, (message_kernel<P><<<G, T, 0, s>>>(b.keys, b.num_keys, b.key_idx, b.msgs, b.offsets,
-                                                             b.count, b.sigs, b.infos, b.status,
-                                                             verify ? 1 : 0)));
-    return cudaGetLastError();
 }
 
 }  // namespace hs

@@ -1,4 +1,4 @@
-// k_tree.cu -- TREE_Sign (paper Sec. III-A, III-C) and key generation.
+// kern_tree.cuh -- TREE_Sign (paper Sec. III-A, III-C) and key generation.
 //
 // What it computes (Sec. II-A-1, II-A-3/4): for every layer j of the
 // hypertree, tree t_j = idx_tree >> (j h'), all 2^h' leaves.  A leaf is the
@@ -17,6 +17,7 @@
 // unrolled SHA-256 compression (all known-zero message words folded).
 // All d layers of all messages form one flat grid: the layers of a
 // signature are independent given the digest (paper Fig. 2).
+#pragma once
 #include <cuda_runtime.h>
 #include "hs_common.cuh"
 #include "hs_launch.h"
@@ -66,8 +67,8 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
     ts.template finish<NW>(P::LEN * P::N, out);
 }
 
-template <class P, int POL>
-__global__ void __launch_bounds__(128) tree_kernel(const KeyBlock* __restrict__ keys,
+template <class P, int POL, int MINB>
+__global__ void __launch_bounds__(128, MINB) tree_kernel(const KeyBlock* __restrict__ keys,
                                                    const MsgInfo* __restrict__ infos, uint32_t count,
                                                    uint8_t* __restrict__ sigs, uint32_t* __restrict__ roots,
                                                    uint32_t* __restrict__ chk, uint32_t ck, uint32_t one) {
@@ -193,45 +194,6 @@ __global__ void __launch_bounds__(128) keygen_kernel(const uint8_t* __restrict__
             p[b] = sd[2 * N + b];
         }
     }
-}
-
-template <class P>
-static cudaError_t launch_tree_t(const Batch& b, cudaStream_t s) {
-    const uint64_t threads = (uint64_t)b.count * P::D * P::LEAVES;
-    const uint32_t T = 128;
-    const uint32_t G = (uint32_t)((threads + T - 1) / T);
-    tree_kernel<P, kChainPol><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck, 1u);
-    return cudaGetLastError();
-}
-
-template <class P>
-static cudaError_t launch_keygen_t(const uint8_t* seeds, uint32_t count, uint8_t* pk, uint8_t* sk, cudaStream_t s) {
-    const uint64_t threads = (uint64_t)count * P::LEAVES;
-    const uint32_t T = 128;
-    const uint32_t G = (uint32_t)((threads + T - 1) / T);
-    keygen_kernel<P><<<G, T, 0, s>>>(seeds, count, pk, sk, 1u);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tree(const Batch& b, cudaStream_t s) {
-    switch (b.pset) {
-    case 0: return launch_tree_t<P128f>(b, s);
-    case 1: return launch_tree_t<P192f>(b, s);
-    case 2: return launch_tree_t<P256f>(b, s);
-    case 3: return launch_tree_t<PToy>(b, s);
-    }
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_keygen(int pset, const uint8_t* seeds, uint32_t count, uint8_t* pk, uint8_t* sk,
-                          cudaStream_t s) {
-    switch (pset) {
-    case 0: return launch_keygen_t<P128f>(seeds, count, pk, sk, s);
-    case 1: return launch_keygen_t<P192f>(seeds, count, pk, sk, s);
-    case 2: return launch_keygen_t<P256f>(seeds, count, pk, sk, s);
-    case 3: return launch_keygen_t<PToy>(seeds, count, pk, sk, s);
-    }
-    return cudaErrorInvalidValue;
 }
 
 }  // namespace hs

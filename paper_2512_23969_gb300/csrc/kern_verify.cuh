@@ -1,4 +1,4 @@
-// k_verify.cu -- batched signature verification on the GPU.
+// kern_verify.cuh -- batched signature verification on the GPU.
 //
 // The scheme's verification (the paper signs only; this is the definition's
 // inverse of Fig. 2): PK_FORS from the FORS signature (leaf from the
@@ -11,6 +11,7 @@
 // len chains of a layer; lane 0 runs the short serial parts (T_k, T_len and
 // the climbs) from a per-warp shared-memory slice.  The layers are serial
 // by definition, so a warp walks them in order.
+#pragma once
 #include <cuda_runtime.h>
 #include "hs_common.cuh"
 #include "hs_launch.h"
@@ -131,23 +132,6 @@ __global__ void __launch_bounds__(128) verify_kernel(const KeyBlock* __restrict_
         for (int w = 0; w < NW; w++) diff |= bmsg[w] ^ kb.pk_root[w];
         ok[m] = diff == 0 ? 1 : 0;
     }
-}
-
-template <class P>
-static cudaError_t launch_verify_t(const Batch& b, cudaStream_t s) {
-    const uint32_t G = (b.count + 3) / 4;
-    verify_kernel<P><<<G, 128, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.ok);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_verify(const Batch& b, cudaStream_t s) {
-    switch (b.pset) {
-    case 0: return launch_verify_t<P128f>(b, s);
-    case 1: return launch_verify_t<P192f>(b, s);
-    case 2: return launch_verify_t<P256f>(b, s);
-    case 3: return launch_verify_t<PToy>(b, s);
-    }
-    return cudaErrorInvalidValue;
 }
 
 }  // namespace hs

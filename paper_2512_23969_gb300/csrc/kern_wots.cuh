@@ -1,4 +1,4 @@
-// k_wots.cu -- WOTS+_Sign (paper Sec. III, after FORS_Sign and TREE_Sign).
+// kern_wots.cuh -- WOTS+_Sign (paper Sec. III, after FORS_Sign and TREE_Sign).
 //
 // What it computes (Sec. II-A-1): layer j signs the n-byte value
 // msg_j = PK_FORS (j = 0) or root_{j-1} (j >= 1).  Its base-16 digits (high
@@ -13,6 +13,7 @@
 // ck-th chain position (ck = 1, 2 or 4), a chain's signature value is the
 // stored position floor(d / ck) ck advanced by d mod ck < ck steps, instead
 // of PRF plus d steps (the same value: chain composition).
+#pragma once
 #include <cuda_runtime.h>
 #include "hs_common.cuh"
 #include "hs_launch.h"
@@ -85,25 +86,6 @@ __global__ void __launch_bounds__(256) wots_kernel(const KeyBlock* __restrict__ 
         for (uint32_t q = 0; q < digit; q++) chain_step<POL, NW>(cx, ms256, q, x, x, pp);
     }
     store_be<NW>(sigs + m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES + (size_t)i * P::N, x);
-}
-
-template <class P>
-static cudaError_t launch_wots_t(const Batch& b, cudaStream_t s) {
-    const uint64_t threads = (uint64_t)b.count * P::D * P::LEN;
-    const uint32_t T = 256;
-    const uint32_t G = (uint32_t)((threads + T - 1) / T);
-    wots_kernel<P, kChainPol><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.pk_fors, b.roots, b.sigs, b.chk, b.ck, 1u);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_wots(const Batch& b, cudaStream_t s) {
-    switch (b.pset) {
-    case 0: return launch_wots_t<P128f>(b, s);
-    case 1: return launch_wots_t<P192f>(b, s);
-    case 2: return launch_wots_t<P256f>(b, s);
-    case 3: return launch_wots_t<PToy>(b, s);
-    }
-    return cudaErrorInvalidValue;
 }
 
 }  // namespace hs

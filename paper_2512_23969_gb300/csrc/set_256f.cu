@@ -1,0 +1,34 @@
+// set_256f.cu -- every kernel instantiated for SPHINCS+-SHA2-256f,
+// with the launch-shape variants the tuner may pick from.
+#include "set_impl.cuh"
+
+namespace hs {
+namespace {
+using P = P256f;
+const int kForsLpt[] = {4, 8, 16};
+const int kTreeMinb[] = {0, 4};
+
+cudaError_t fors_variant(const Batch& b, int lpt, cudaStream_t s) {
+    switch (lpt) {
+    case 4: return SetImpl<P>::fors<4>(b, s);
+    case 8: return SetImpl<P>::fors<8>(b, s);
+    case 16: return SetImpl<P>::fors<16>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tree_variant(const Batch& b, int minb, cudaStream_t s) {
+    switch (minb) {
+    case 0: return SetImpl<P>::tree<1>(b, s);
+    case 4: return SetImpl<P>::tree<4>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
+extern const SetOps kOps_256F = {
+    SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk, tree_variant,
+    SetImpl<P>::wots,    SetImpl<P>::verify,  SetImpl<P>::keygen,
+    kForsLpt, 3, 4, kTreeMinb, 2, 0};
+
+}  // namespace hs

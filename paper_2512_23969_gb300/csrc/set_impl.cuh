@@ -1,0 +1,71 @@
+// set_impl.cuh -- host launchers of every kernel for one parameter set P.
+// Each set_<name>.cu instantiates SetImpl<P> and the launch-shape variants
+// the tuner may choose from, and exports them as one SetOps table.
+#pragma once
+#include <cuda_runtime.h>
+#include "hs_launch.h"
+#include "kern_msg.cuh"
+#include "kern_fors.cuh"
+#include "kern_tree.cuh"
+#include "kern_wots.cuh"
+#include "kern_verify.cuh"
+
+namespace hs {
+
+template <class P>
+struct SetImpl {
+    static cudaError_t keyprep(const Batch& b, bool from_pk, cudaStream_t s) {
+        const uint32_t T = 128, G = (b.num_keys + T - 1) / T;
+        keyprep_kernel<P><<<G, T, 0, s>>>(b.keys_in, b.num_keys, from_pk ? 1 : 0, b.keys);
+        return cudaGetLastError();
+    }
+    static cudaError_t message(const Batch& b, bool verify, cudaStream_t s) {
+        const uint32_t T = 64, G = (b.count + T - 1) / T;
+        message_kernel<P><<<G, T, 0, s>>>(b.keys, b.num_keys, b.key_idx, b.msgs, b.offsets, b.count, b.sigs,
+                                          b.infos, b.status, verify ? 1 : 0);
+        return cudaGetLastError();
+    }
+    template <int LPT>
+    static cudaError_t fors(const Batch& b, cudaStream_t s) {
+        const uint64_t threads = (uint64_t)b.count * P::K * LPT;
+        const uint32_t T = 256;
+        const uint32_t G = (uint32_t)((threads + T - 1) / T);
+        fors_kernel<P, kChainPol, LPT><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.fors_roots, 1u);
+        return cudaGetLastError();
+    }
+    static cudaError_t fors_pk(const Batch& b, cudaStream_t s) {
+        const uint32_t T = 128, G = (b.count + T - 1) / T;
+        fors_pk_kernel<P><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.fors_roots, b.pk_fors);
+        return cudaGetLastError();
+    }
+    template <int MINB>
+    static cudaError_t tree(const Batch& b, cudaStream_t s) {
+        const uint64_t threads = (uint64_t)b.count * P::D * P::LEAVES;
+        const uint32_t T = 128;
+        const uint32_t G = (uint32_t)((threads + T - 1) / T);
+        tree_kernel<P, kChainPol, MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck, 1u);
+        return cudaGetLastError();
+    }
+    static cudaError_t wots(const Batch& b, cudaStream_t s) {
+        const uint64_t threads = (uint64_t)b.count * P::D * P::LEN;
+        const uint32_t T = 256;
+        const uint32_t G = (uint32_t)((threads + T - 1) / T);
+        wots_kernel<P, kChainPol><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.pk_fors, b.roots, b.sigs, b.chk,
+                                                   b.ck, 1u);
+        return cudaGetLastError();
+    }
+    static cudaError_t verify(const Batch& b, cudaStream_t s) {
+        const uint32_t G = (b.count + 3) / 4;
+        verify_kernel<P><<<G, 128, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.ok);
+        return cudaGetLastError();
+    }
+    static cudaError_t keygen(const uint8_t* seeds, uint32_t count, uint8_t* pk, uint8_t* sk, cudaStream_t s) {
+        const uint64_t threads = (uint64_t)count * P::LEAVES;
+        const uint32_t T = 128;
+        const uint32_t G = (uint32_t)((threads + T - 1) / T);
+        keygen_kernel<P><<<G, T, 0, s>>>(seeds, count, pk, sk, 1u);
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace hs

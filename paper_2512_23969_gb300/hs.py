@@ -47,6 +47,8 @@ def load():
     L.hs_sign_kernel_count.restype = C.c_int
     L.hs_sign_batch_noalloc.argtypes = [C.c_int, vp, u32, vp, vp, u64p, u32, vp, vp]
     L.hs_sign_batch_noalloc.restype = C.c_int
+    L.hs_probe_int_pipes.argtypes = [C.POINTER(C.c_float), C.c_int]
+    L.hs_probe_int_pipes.restype = C.c_int
     L.hs_set_chain_checkpoint.argtypes = [C.c_uint32]
     L.hs_set_chain_checkpoint.restype = C.c_int
     for name in ("hs_keygen", "hs_sign_batch", "hs_verify_batch", "hs_check_status"):
@@ -182,3 +184,15 @@ def hs_sign_batch_noalloc(params, sk, msgs, lens, sigs, key_idx=None, num_keys=N
     _check(load().hs_sign_batch_noalloc(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), _ptr(msgs),
                                         _ptr(lens), count, _ptr(sigs), _stream(stream)))
     return sigs
+
+
+PIPE_FORMS = ("lop3", "shf", "iadd", "imad", "imad_hi", "prmt", "lop3+imad")
+
+
+def hs_probe_int_pipes():
+    """{instruction form: measured lane-ops per clock per SM} on the current GPU."""
+    r = (C.c_float * 8)()
+    n = load().hs_probe_int_pipes(r, 8)
+    if n < 0:
+        raise HSError(3, "hs_probe_int_pipes failed")
+    return {PIPE_FORMS[i]: round(float(r[i]), 2) for i in range(n)}
