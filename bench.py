@@ -209,6 +209,78 @@ def run_reference(args):
     return 0
 
 
+def _time_steps(fn, stream, flush, steps, warmup):
+    """CUDA-event time of fn() per step (L2 flushed between steps, outside)."""
+    import torch
+    for i in range(warmup):
+        flush.fill_(i & 0xFF)
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(steps):
+        flush.fill_((k + 3) & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def measure_other_configs(hs, inputs, args, stream, flush):
+    import torch
+    res = {}
+    dev = lambda x: torch.from_numpy(x).cuda()
+    steps, warmup = max(2, args.steps // 2), 3
+    for ps in ("192f", "256f"):
+        wl = inputs.config(2, ps)
+        pk, sk = hs.hs_keygen(ps, dev(wl.seeds))
+        m, l, k = dev(wl.msgs), dev(wl.lens), dev(wl.key_idx)
+        sig = torch.empty(wl.count * hs.sig_bytes(ps), dtype=torch.uint8, device="cuda")
+        hs.hs_profile_enable(True)
+        ms = _time_steps(lambda: hs.hs_sign_batch(ps, sk, m, l, key_idx=k, sigs=sig, num_keys=wl.num_keys,
+                                                   stream=stream), stream, flush, steps, warmup)
+        prof = hs.hs_profile_read()
+        hs.hs_profile_enable(False)
+        ok = hs.hs_verify_batch(ps, pk, m, l, sig.view(wl.count, -1), key_idx=k, num_keys=wl.num_keys)
+        res[ps] = {"workload": wl.name, "value": round(wl.count * len(ms) / (sum(ms) / 1e3), 1),
+                   "unit": "signatures/s", "ms_per_step": round(sum(ms) / len(ms), 3),
+                   "stage_ms": {a: round(b, 3) for a, b in prof.items()},
+                   "verified": int(ok.sum().item()) == wl.count}
+    # mixed-parameter batch (32768 messages 50/30/20, log-uniform 16 B - 64 KB, 64 keys)
+    wls = inputs.mixed()
+    jobs = []
+    for wl in wls:
+        pk, sk = hs.hs_keygen(wl.params, dev(wl.seeds))
+        jobs.append({"params": wl.params, "sk": sk, "pk": pk, "msgs": dev(wl.msgs), "lens": dev(wl.lens),
+                     "key_idx": dev(wl.key_idx), "num_keys": wl.num_keys,
+                     "sigs": torch.empty(wl.count * hs.sig_bytes(wl.params), dtype=torch.uint8, device="cuda")})
+    total = sum(wl.count for wl in wls)
+
+    def plain():
+        for j in jobs:
+            hs.hs_sign_batch(j["params"], j["sk"], j["msgs"], j["lens"], key_idx=j["key_idx"], sigs=j["sigs"],
+                             num_keys=j["num_keys"], stream=stream)
+
+    out = {"workload": "mixed 32768 msgs 50/30/20 128f/192f/256f, log-U[16 B, 64 KB], 64 keys (32/19/13)",
+           "messages": total, "msg_bytes": int(sum(int(wl.lens.sum()) for wl in wls))}
+    for name, fn in (("plain_per_set_calls", plain),
+                     ("one_graph_launch", lambda: hs.hs_sign_mixed(jobs, use_graph=True, stream=stream)),
+                     ("streams_no_graph", lambda: hs.hs_sign_mixed(jobs, use_graph=False, stream=stream))):
+        ms = _time_steps(fn, stream, flush, steps, warmup)
+        out[name] = {"value": round(total * len(ms) / (sum(ms) / 1e3), 1), "unit": "signatures/s",
+                     "ms_per_step": round(sum(ms) / len(ms), 3), "max_ms": round(max(ms), 3)}
+    n_ok = 0
+    for j, wl in zip(jobs, wls):
+        ok = hs.hs_verify_batch(wl.params, j["pk"], j["msgs"], j["lens"], j["sigs"].view(wl.count, -1),
+                                key_idx=j["key_idx"], num_keys=wl.num_keys)
+        n_ok += int(ok.sum().item())
+    out["verified"] = "%d/%d" % (n_ok, total)
+    res["mixed"] = out
+    return res
+
+
 def run_own(args):
     import numpy as np
     import torch
@@ -341,6 +413,16 @@ def run_own(args):
     if clk.get("sm_mhz") and achieved:
         roofline["frac_at_sampled_clock"] = round(achieved / (sm_count * alu_rate * clk["sm_mhz"] * 1e6 / 1e12), 4)
 
+    # the other workloads of the signer's specification, measured with the
+    # same events: 192f / 256f batches, and the mixed-parameter batch in one
+    # graph launch against one hs_sign_batch call per set
+    others = {}
+    if args.other_configs:
+        try:
+            others = measure_other_configs(hs, inputs, args, stream, flush)
+        except Exception as exc:      # keep the main line; report what failed
+            others = {"error": repr(exc)[:300]}
+
     # CPU oracle baseline on a bounded sample
     cpu = None
     if rank == 0 and args.cpu_seconds > 0:
@@ -367,6 +449,7 @@ def run_own(args):
         "stage_ms": stage_avg,
         "batch_latency_ms": {"p50": round(ms_sorted[len(ms_sorted) // 2], 3), "max": round(ms_sorted[-1], 3)},
         "verified": "%d/%d signatures accepted by GPU verify" % (n_ok, count),
+        "other_configs": others,
         "wall_s": round(wall, 3),
         "device": props.name, "sm_count": sm_count,
         "tuning": {k: autotune.get(ps, k) for k in autotune.KNOBS} | {"from_cache": bool(tuned)},
@@ -389,6 +472,8 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=10.0)
     ap.add_argument("--params", choices=["128f", "192f", "256f"], default="128f",
                     help="parameter set (the default workload is 128f)")
+    ap.add_argument("--no-other-configs", dest="other_configs", action="store_false",
+                    help="skip the 192f / 256f / mixed-parameter measurements")
     ap.add_argument("--count", type=int, default=16384,
                     help="messages per step (smaller counts are for profiler captures)")
     args = ap.parse_args()

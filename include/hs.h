@@ -98,6 +98,32 @@ hs_status hs_sign_batch(hs_params p, const uint8_t *sk, uint32_t num_keys,
                         void *stream);
 
 /*
+ * hs_sign_mixed -- several signing jobs, possibly under different parameter
+ * sets, in one call (the paper's batched form, Sec. III-F: per batch a DAG
+ * of {FORS_Sign || TREE_Sign} -> WOTS+_Sign; here every job's DAG runs on
+ * its own pair of streams, all forked from and joined into 'stream').
+ *   jobs[j] : one hs_sign_batch worth of arguments; device buffers only
+ *   njobs   : 0..16 (jobs with count 0 are skipped)
+ *   use_graph: 1 = the whole fork/join sequence is captured into one CUDA
+ *             graph and launched once; 0 = the same launches go out directly
+ * Asynchronous on 'stream'; signatures are identical to hs_sign_batch's.
+ * Errors: HS_EINVAL (bad set, NULL or host buffer, more than 16 jobs),
+ * HS_ENOMEM, HS_ECUDA.  Key-index errors go to the status word.
+ * Calls must not be issued concurrently from several host threads.
+ */
+typedef struct {
+    hs_params params;
+    const uint8_t *sk;
+    uint32_t num_keys;
+    const uint32_t *key_idx;
+    const uint8_t *msgs;
+    const uint64_t *lens;
+    uint32_t count;
+    uint8_t *sigs;
+} hs_sign_job;
+hs_status hs_sign_mixed(const hs_sign_job *jobs, uint32_t njobs, int use_graph, void *stream);
+
+/*
  * hs_verify_batch -- verify 'count' signatures (the scheme's verification:
  * FORS public key from the FORS signature, then d WOTS+ public keys from
  * their signatures and auth-path climbs, compared with PK.root).

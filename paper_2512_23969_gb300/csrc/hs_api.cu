@@ -118,6 +118,19 @@ static hs_status dev_state(DevState** out) {
     return HS_OK;
 }
 
+uint32_t* device_status_word() {
+    DevState* d;
+    return dev_state(&d) == HS_OK ? d->status : nullptr;
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+    DevState* d;
+    if (dev_state(&d) != HS_OK) return cudaErrorUnknown;
+    return cudaMallocFromPoolAsync(p, bytes, d->pool, s);
+}
+
+uint32_t chain_checkpoint_stride() { return g_ck; }
+
 // 1 if p is host memory (pageable or pinned), 0 if device or managed.
 static int is_host_ptr(const void* p) {
     if (!p) return 0;

@@ -36,6 +36,13 @@ struct Batch {
 // Record the text hs_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 
+// Library state shared by the entry points: the current device's status
+// word (nullptr if the device state could not be set up), a stream-ordered
+// allocation from the library's pool, and the chain checkpoint stride.
+uint32_t* device_status_word();
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+uint32_t chain_checkpoint_stride();
+
 // Scratch bytes for a batch (each region 256-byte aligned).
 size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck);
 void carve_scratch(Batch& b, void* base);

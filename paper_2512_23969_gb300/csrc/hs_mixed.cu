@@ -1,0 +1,181 @@
+// hs_mixed.cu -- hs_sign_mixed: one call signing several batches, possibly
+// under different parameter sets, as one CUDA graph launch.
+//
+// Per job the stage DAG of the paper (Sec. III-F: FORS_Sign and TREE_Sign
+// are independent given the digest; WOTS+_Sign needs both) is laid out on
+// two forked streams:
+//   A: keyprep -> offsets -> message -> [fork] -> TREE_Sign -> [join] -> WOTS+_Sign
+//   B:                                   [fork] -> FORS_Sign -> FORS pk -> [join]
+// and all jobs fork from, and join back into, the caller's stream.  With
+// use_graph the whole fork/join sequence is stream-captured into one graph
+// and launched once; without it the same launches go out directly (the
+// "plain" per-stage form that the graph form is measured against).
+#include <cuda_runtime.h>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+#include "hs_launch.h"
+#include "../../include/hs.h"
+
+#define HS_API extern "C" __attribute__((visibility("default")))
+
+namespace hs {
+namespace {
+
+constexpr int kMaxJobs = 16;
+
+struct MixedDev {
+    bool init = false;
+    cudaStream_t capture;               // graphs are captured here, launched on the caller's stream
+    cudaStream_t side[2 * kMaxJobs];
+    cudaEvent_t fork, msg[kMaxJobs], fors[kMaxJobs], done[kMaxJobs];
+};
+std::mutex g_mx_mu;
+MixedDev g_mx[64];
+
+hs_status mx_fail(hs_status st, const char* msg) {
+    set_last_error(msg);
+    return st;
+}
+
+hs_status mixed_dev(MixedDev** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return mx_fail(HS_ECUDA, "hs_sign_mixed: no usable current device");
+    }
+    std::lock_guard<std::mutex> lk(g_mx_mu);
+    MixedDev& d = g_mx[dev];
+    if (!d.init) {
+        bool ok = cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 2 * kMaxJobs && ok; i++)
+            ok = cudaStreamCreateWithFlags(&d.side[i], cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < kMaxJobs && ok; i++)
+            ok = cudaEventCreateWithFlags(&d.msg[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&d.fors[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&d.done[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return mx_fail(HS_ECUDA, "hs_sign_mixed: stream/event creation failed");
+        }
+        d.init = true;
+    }
+    *out = &d;
+    return HS_OK;
+}
+
+bool is_dev(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Enqueue every job's stage DAG (fork from / join into 'origin').
+cudaError_t enqueue_jobs(MixedDev& d, std::vector<Batch>& bs, cudaStream_t origin) {
+    cudaError_t e = cudaEventRecord(d.fork, origin);
+    for (size_t j = 0; j < bs.size() && e == cudaSuccess; j++) {
+        const Batch& b = bs[j];
+        cudaStream_t A = d.side[2 * j], B = d.side[2 * j + 1];
+        e = cudaStreamWaitEvent(A, d.fork, 0);
+        if (e == cudaSuccess) e = launch_keyprep(b, false, A);
+        if (e == cudaSuccess) e = launch_offsets(b, A);
+        if (e == cudaSuccess) e = launch_message(b, false, A);
+        if (e == cudaSuccess) e = cudaEventRecord(d.msg[j], A);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(B, d.msg[j], 0);
+        if (e == cudaSuccess) e = launch_fors(b, B);
+        if (e == cudaSuccess) e = launch_fors_pk(b, B);
+        if (e == cudaSuccess) e = cudaEventRecord(d.fors[j], B);
+        if (e == cudaSuccess) e = launch_tree(b, A);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(A, d.fors[j], 0);
+        if (e == cudaSuccess) e = launch_wots(b, A);
+        if (e == cudaSuccess) e = cudaEventRecord(d.done[j], A);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, d.done[j], 0);
+    }
+    return e;
+}
+
+}  // namespace
+}  // namespace hs
+
+using namespace hs;
+
+HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_graph, void* stream) {
+    if (njobs == 0) return HS_OK;
+    if (!jobs) return mx_fail(HS_EINVAL, "hs_sign_mixed: NULL job array");
+    if (njobs > (uint32_t)kMaxJobs) return mx_fail(HS_EINVAL, "hs_sign_mixed: at most 16 jobs per call");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<Batch> bs;
+    std::vector<size_t> off;
+    size_t total = 0;
+    for (uint32_t j = 0; j < njobs; j++) {
+        const hs_sign_job& jb = jobs[j];
+        if ((int)jb.params < 0 || (int)jb.params > 3) return mx_fail(HS_EINVAL, "hs_sign_mixed: invalid parameter set");
+        if (jb.count == 0) continue;
+        if (!jb.sk || !jb.msgs || !jb.lens || !jb.sigs || jb.num_keys == 0)
+            return mx_fail(HS_EINVAL, "hs_sign_mixed: NULL buffer or num_keys == 0");
+        if (!is_dev(jb.sk) || !is_dev(jb.msgs) || !is_dev(jb.lens) || !is_dev(jb.sigs) ||
+            (jb.key_idx && !is_dev(jb.key_idx)))
+            return mx_fail(HS_EINVAL, "hs_sign_mixed: every buffer must be device memory");
+        Batch b{};
+        b.pset = jb.params;
+        b.keys_in = jb.sk;
+        b.num_keys = jb.num_keys;
+        b.key_idx = jb.key_idx;
+        b.msgs = jb.msgs;
+        b.lens = jb.lens;
+        b.count = jb.count;
+        b.sigs = jb.sigs;
+        b.ck = chain_checkpoint_stride();
+        bs.push_back(b);
+        off.push_back(total);
+        total += scratch_bytes(b.pset, b.num_keys, b.count, b.ck);
+    }
+    if (bs.empty()) return HS_OK;
+    MixedDev* d = nullptr;
+    hs_status st = mixed_dev(&d);
+    if (st != HS_OK) return st;
+    uint32_t* status = device_status_word();
+    if (!status) return mx_fail(HS_ECUDA, "hs_sign_mixed: device state unavailable");
+    void* base = nullptr;
+    cudaError_t e = pool_alloc(&base, total, s);
+    if (e != cudaSuccess) {
+        char buf[200];
+        snprintf(buf, sizeof(buf), "hs_sign_mixed: scratch of %zu bytes: %s", total, cudaGetErrorString(e));
+        return mx_fail(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA, buf);
+    }
+    for (size_t j = 0; j < bs.size(); j++) {
+        bs[j].status = status;
+        carve_scratch(bs[j], static_cast<char*>(base) + off[j]);
+    }
+    if (use_graph) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        // Capture on a library stream (the caller's may be the legacy default
+        // stream, which cannot be captured); the graph is launched on 'stream'.
+        e = cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = enqueue_jobs(*d, bs, d->capture);
+            e = cudaStreamEndCapture(d->capture, &g);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, s);
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+    } else {
+        e = enqueue_jobs(*d, bs, s);
+    }
+    cudaError_t ef = cudaFreeAsync(base, s);
+    if (e == cudaSuccess) e = ef;
+    if (e != cudaSuccess) {
+        char buf[200];
+        snprintf(buf, sizeof(buf), "hs_sign_mixed: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        return mx_fail(HS_ECUDA, buf);
+    }
+    return HS_OK;
+}

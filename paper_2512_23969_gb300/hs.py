@@ -49,6 +49,8 @@ def load():
     L.hs_sign_batch_noalloc.restype = C.c_int
     L.hs_probe_int_pipes.argtypes = [C.POINTER(C.c_float), C.c_int]
     L.hs_probe_int_pipes.restype = C.c_int
+    L.hs_sign_mixed.argtypes = [C.c_void_p, C.c_uint32, C.c_int, C.c_void_p]
+    L.hs_sign_mixed.restype = C.c_int
     L.hs_set_chain_checkpoint.argtypes = [C.c_uint32]
     L.hs_set_chain_checkpoint.restype = C.c_int
     for name in ("hs_keygen", "hs_sign_batch", "hs_verify_batch", "hs_check_status"):
@@ -196,3 +198,26 @@ def hs_probe_int_pipes():
     if n < 0:
         raise HSError(3, "hs_probe_int_pipes failed")
     return {PIPE_FORMS[i]: round(float(r[i]), 2) for i in range(n)}
+
+
+class SignJob(C.Structure):
+    """hs_sign_job of include/hs.h."""
+    _fields_ = [("params", C.c_int), ("sk", C.c_void_p), ("num_keys", C.c_uint32), ("key_idx", C.c_void_p),
+                ("msgs", C.c_void_p), ("lens", C.c_void_p), ("count", C.c_uint32), ("sigs", C.c_void_p)]
+
+
+def hs_sign_mixed(jobs, use_graph=True, stream=None):
+    """Sign several batches (possibly different parameter sets) in one call.
+    ``jobs``: sequence of dicts with params, sk, msgs, lens, sigs and
+    optionally key_idx, num_keys (device tensors).  Returns the sigs tensors."""
+    arr = (SignJob * len(jobs))()
+    for j, jb in enumerate(jobs):
+        ps = jb["params"]
+        n = N_BYTES[ps] if isinstance(ps, str) else [16, 24, 32, 16][ps]
+        sk = jb["sk"]
+        nk = jb.get("num_keys") or (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
+        msgs = _nonempty(jb["msgs"], jb["lens"])
+        arr[j] = SignJob(_pid(ps), _ptr(sk), int(nk), _ptr(jb.get("key_idx")), _ptr(msgs), _ptr(jb["lens"]),
+                         int(jb["lens"].shape[0]), _ptr(jb["sigs"]))
+    _check(load().hs_sign_mixed(C.cast(arr, C.c_void_p), len(jobs), 1 if use_graph else 0, _stream(stream)))
+    return [jb["sigs"] for jb in jobs]

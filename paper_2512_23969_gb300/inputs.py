@@ -85,6 +85,26 @@ def make(params, count, num_keys=1, lengths=32, seed=BASE_SEED, name="custom",
     return Workload(name, params, seeds, msgs, lens, key_idx, sub)
 
 
+def mixed(count=32768, mix=(0.5, 0.3, 0.2), keys=(32, 19, 13), lengths=("loguniform", 16, 65536),
+          seed=BASE_SEED + 3, name="mixed"):
+    """Mixed-parameter batch: each message draws its set from ``mix`` over
+    (128f, 192f, 256f); per set, its own seeded keys and key indices drawn
+    uniformly; message lengths log-uniform.  Returns one Workload per set
+    (messages in draw order), with the global message index of each row in
+    ``Workload.subset``."""
+    rng = np.random.default_rng(seed)
+    sets = ("128f", "192f", "256f")
+    which = rng.choice(3, size=count, p=np.asarray(mix) / np.sum(mix))
+    out = []
+    for si, ps in enumerate(sets):
+        idx = np.nonzero(which == si)[0]
+        sub_seed = int(rng.integers(0, 2 ** 31))
+        wl = make(ps, int(idx.size), keys[si], lengths, sub_seed, "%s-%s" % (name, ps), key_mode="random")
+        wl.subset = idx
+        out.append(wl)
+    return out
+
+
 def config(index, params=None):
     """The five workload recipes (sizes of the configurations the signer is
     specified on); ``params`` picks the set for the two-set / mixed recipes.

@@ -1,0 +1,49 @@
+"""hs_sign_mixed: several parameter sets in one call (graph or plain launches)
+give byte-identical signatures to one hs_sign_batch call per set, and to the
+oracle on sampled messages."""
+import numpy as np
+import pytest
+
+from paper_2512_23969_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_mixed_equals_per_set(hs, O, use_graph):
+    import torch
+    jobs, refs, wls = [], [], []
+    for k, (ps, count) in enumerate((("128f", 33), ("192f", 12), ("256f", 7), ("toy", 40), ("128f", 5))):
+        wl = inputs.make(ps, count, num_keys=2 + k % 3, lengths=("loguniform", 16, 4096), seed=810 + k,
+                         key_mode="random")
+        pk, sk = hs.hs_keygen(ps, _dev(wl.seeds))
+        d = {"params": ps, "sk": sk, "msgs": _dev(wl.msgs), "lens": _dev(wl.lens), "key_idx": _dev(wl.key_idx),
+             "num_keys": wl.num_keys}
+        refs.append(hs.hs_sign_batch(ps, sk, d["msgs"], d["lens"], key_idx=d["key_idx"], num_keys=wl.num_keys))
+        d["sigs"] = torch.full((count * hs.sig_bytes(ps),), 0x5A, dtype=torch.uint8, device="cuda")
+        jobs.append(d)
+        wls.append(wl)
+    hs.hs_sign_mixed(jobs, use_graph=use_graph)
+    torch.cuda.synchronize()
+    for d, ref, wl in zip(jobs, refs, wls):
+        assert torch.equal(d["sigs"].view(wl.count, -1), ref), d["params"]
+    # one message per job against the oracle
+    for d, wl in zip(jobs, wls):
+        i = wl.count - 1
+        osk = O.keygen(wl.params, bytes(wl.seeds[wl.key_idx[i]]))[1]
+        assert d["sigs"].view(wl.count, -1)[i].cpu().numpy().tobytes() == O.sign(wl.params, osk, wl.message(i))
+    rc, flags = hs.hs_check_status()
+    assert rc == 0 and flags == 0
+
+
+def test_mixed_rejects_host_buffers(hs):
+    wl = inputs.make("toy", 2, seed=3)
+    pk, sk = hs.hs_keygen("toy", wl.seeds)
+    with pytest.raises(hs.HSError):
+        hs.hs_sign_mixed([{"params": "toy", "sk": sk, "msgs": wl.msgs, "lens": wl.lens,
+                           "sigs": np.zeros(2 * 1456, np.uint8)}])
