@@ -281,6 +281,54 @@ def measure_other_configs(hs, inputs, args, stream, flush):
     return res
 
 
+def measure_serving(hs, inputs, seconds, rhos, burst=60000):
+    """Config-5 style serving run: 1024 resident keys (614/256/154), mix
+    60/25/15 of 128f/192f/256f, log-uniform 16 B - 4 KB messages, an 8 GiB
+    device-memory admission budget.  First a saturating burst (all requests
+    at t = 0) measures the peak rate of this mix; then Poisson arrivals at
+    rho x peak for 'seconds' each, reporting achieved rate and p50/p99
+    latency from arrival to host-observed completion."""
+    import numpy as np
+    import torch
+    budget, max_batch, inflight = 8 << 30, 2048, 4
+    base = inputs.serving_trace(rate=1.0, seconds=1.0)          # keys and pool only
+    keys = {}
+    for ps in ("128f", "192f", "256f"):
+        keys[ps] = hs.hs_keygen(ps, torch.from_numpy(base["seeds"][ps]).cuda())[1]
+    out = {"workload": "serving: 1024 keys (614/256/154), mix 60/25/15 128f/192f/256f, log-U[16 B, 4 KB]",
+           "mem_budget_bytes": budget, "max_batch": max_batch, "max_inflight": inflight}
+    with hs.Server(keys, max_inflight=inflight, max_batch=max_batch, mem_budget=budget) as srv:
+        tr = inputs.serving_trace(rate=1e6, seconds=burst / 1e6, seed=inputs.BASE_SEED + 40)
+        tr["arrival_ns"][:] = 0
+        n = len(tr["params"])
+        t0 = time.perf_counter()
+        lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
+                            tr["arrival_ns"])
+        wall = time.perf_counter() - t0
+        peak = n / wall
+        out["burst"] = {"requests": n, "value": round(peak, 1), "unit": "signatures/s",
+                        "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
+                        "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3)}
+        for rho in rhos:
+            tr = inputs.serving_trace(rate=rho * peak, seconds=seconds, seed=inputs.BASE_SEED + 41 + int(rho * 100))
+            n = len(tr["params"])
+            lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
+                                tr["arrival_ns"])
+            finish = (tr["arrival_ns"].astype(np.float64) + lat.astype(np.float64)).max() / 1e9
+            st = srv.stats()
+            out["rho_%.2f" % rho] = {"offered": round(rho * peak, 1), "requests": n,
+                                     "value": round(n / finish, 1), "unit": "signatures/s",
+                                     "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
+                                     "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3),
+                                     "max_ms": round(float(lat.max()) / 1e6, 3)}
+        st = srv.stats()
+        out["batches"] = st["batches"]
+        out["mean_batch"] = round(st["batched_requests"] / max(1, st["batches"]), 1)
+        out["max_inflight_batches"] = st["max_inflight_batches"]
+        out["max_device_bytes_in_use"] = st["max_device_bytes_in_use"]
+    return out
+
+
 def run_own(args):
     import numpy as np
     import torch
@@ -423,6 +471,13 @@ def run_own(args):
         except Exception as exc:      # keep the main line; report what failed
             others = {"error": repr(exc)[:300]}
 
+    serving = None
+    if args.serving_seconds > 0:
+        try:
+            serving = measure_serving(hs, inputs, args.serving_seconds, (0.5, 0.75, 1.0))
+        except Exception as exc:
+            serving = {"error": repr(exc)[:300]}
+
     # CPU oracle baseline on a bounded sample
     cpu = None
     if rank == 0 and args.cpu_seconds > 0:
@@ -450,6 +505,7 @@ def run_own(args):
         "batch_latency_ms": {"p50": round(ms_sorted[len(ms_sorted) // 2], 3), "max": round(ms_sorted[-1], 3)},
         "verified": "%d/%d signatures accepted by GPU verify" % (n_ok, count),
         "other_configs": others,
+        "serving": serving,
         "wall_s": round(wall, 3),
         "device": props.name, "sm_count": sm_count,
         "tuning": {k: autotune.get(ps, k) for k in autotune.KNOBS} | {"from_cache": bool(tuned)},
@@ -474,6 +530,8 @@ def main():
                     help="parameter set (the default workload is 128f)")
     ap.add_argument("--no-other-configs", dest="other_configs", action="store_false",
                     help="skip the 192f / 256f / mixed-parameter measurements")
+    ap.add_argument("--serving-seconds", type=float, default=3.0,
+                    help="seconds of Poisson load per rate in the serving measurement (0 = skip)")
     ap.add_argument("--count", type=int, default=16384,
                     help="messages per step (smaller counts are for profiler captures)")
     args = ap.parse_args()

@@ -207,6 +207,63 @@ int hs_tune_options(hs_params p, int knob, int32_t *values, int max);
 hs_status hs_tune_set(hs_params p, int knob, int32_t value);
 int32_t hs_tune_get(hs_params p, int knob);
 
+/*
+ * Continuous-batching signing server.  Requests (parameter set, key index,
+ * message) are submitted at any time; a scheduler thread keeps up to
+ * max_inflight batches on the GPU, each on its own stream, and launches the
+ * next batch -- the oldest pending requests of one parameter set, at most
+ * max_batch of them -- as soon as a slot and memory are free, so newly
+ * arrived requests overlap with running ones.  Device memory for messages,
+ * signatures and scratch comes from one arena of mem_budget_bytes reserved
+ * at creation (admission control: a batch that does not fit waits); host
+ * staging uses a pinned arena of pinned_bytes (0 = half the budget).  Keys
+ * and their SHA-2 midstates are resident on the device from creation.
+ * Signatures equal hs_sign_batch's for the same key and message.
+ *
+ * hs_server_create: sks[p] = nkeys[p] keys of set p (4n bytes each, host or
+ *   device; nkeys[p] = 0 disables set p).  The current device is used.
+ * hs_server_submit: copies the message; the signature is written to sig_out
+ *   (host memory, hs_sig_bytes(p) bytes, valid until completion; NULL =
+ *   compute and discard, for load tests).  HS_EKEY for a key index >= nkeys.
+ * hs_server_wait: blocks up to timeout_ms; HS_ETIMEOUT if still pending.
+ * hs_server_poll: hands out each completed request once (id and latency
+ *   from arrival to host-observed completion, in ns) and forgets it.
+ * hs_server_replay: open-loop load generator: submits request i (set
+ *   params[i], key keys[i], message pool entry pool_idx[i] of the packed pool
+ *   pool_msgs / pool_lens) at arrival_ns[i] after the call starts, waits for
+ *   all, and reports each latency from its scheduled arrival.  Signatures go
+ *   to sigs + sig_offsets[i], or are discarded if sigs is NULL.
+ *   HS_ETIMEOUT after timeout_ms.
+ * hs_server_destroy: stops the scheduler, waits for running batches, frees
+ *   everything; requests never launched are dropped.
+ */
+typedef struct hs_server hs_server;
+typedef struct {
+    uint32_t max_inflight;      /* batches on the GPU at once (1..16) */
+    uint32_t max_batch;         /* requests per batch */
+    uint64_t mem_budget_bytes;  /* device arena for in-flight work (>= 1 MiB) */
+    uint64_t pinned_bytes;      /* pinned host staging arena (0 = budget / 2) */
+} hs_server_config;
+typedef struct {
+    uint64_t completed, batches, batched_requests, pending;
+    uint64_t max_device_bytes_in_use;
+    uint32_t max_inflight_batches;
+} hs_server_stats;
+hs_status hs_server_create(const hs_server_config *cfg, const uint8_t *const sks[4],
+                           const uint32_t nkeys[4], hs_server **out);
+hs_status hs_server_submit(hs_server *s, hs_params p, uint32_t key, const uint8_t *msg,
+                           uint64_t len, uint8_t *sig_out, uint64_t *id);
+hs_status hs_server_wait(hs_server *s, uint64_t id, uint32_t timeout_ms);
+int hs_server_poll(hs_server *s, uint64_t *ids, uint64_t *latency_ns, int max);
+hs_status hs_server_get_stats(hs_server *s, hs_server_stats *st);
+hs_status hs_server_replay(hs_server *s, uint32_t count, const uint8_t *params,
+                           const uint32_t *keys, const uint32_t *pool_idx,
+                           const uint8_t *pool_msgs, const uint64_t *pool_lens,
+                           uint32_t pool_count, const uint64_t *arrival_ns, uint8_t *sigs,
+                           const uint64_t *sig_offsets, uint64_t *latency_ns,
+                           uint32_t timeout_ms);
+hs_status hs_server_destroy(hs_server *s);
+
 /* Size of the fixed device buffer that hs_sign_batch_noalloc works in. */
 #define HS_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 

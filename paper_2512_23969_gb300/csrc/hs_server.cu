@@ -1,0 +1,543 @@
+// hs_server.cu -- continuous-batching signing server (include/hs.h, hs_server_*).
+//
+// Requests (parameter set, key index, message) arrive at any time through
+// hs_server_submit.  A scheduler thread keeps up to 'max_inflight' batches
+// on the GPU, each on its own stream: whenever a slot frees up and memory
+// is available, it takes the oldest pending requests of one parameter set
+// (up to 'max_batch') as the next batch, stages them through pinned host
+// memory, launches message stage -> FORS_Sign || TREE_Sign -> WOTS+_Sign,
+// and copies the signatures back.  Batches of different sets and different
+// arrival times therefore overlap on the device, and a request that arrives
+// while others are running is admitted as soon as a slot and memory free
+// up -- not after the running batches drain.
+//
+// Admission is bounded by a device-memory budget: one device arena of
+// 'mem_budget_bytes' is reserved at creation and every batch's messages,
+// signatures and scratch are carved from it (first-fit, coalescing); a batch
+// that does not fit waits for running batches to return memory.  Keys and
+// their SHA-2 midstates are made resident once, at creation.
+// Completion is signalled by a host callback on the batch stream; no thread
+// spins on the GPU, and every host wait takes a timeout.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+#include "hs_launch.h"
+#include "../../include/hs.h"
+
+#define HS_API extern "C" __attribute__((visibility("default")))
+
+namespace hs {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+inline uint64_t now_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
+}
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// First-fit allocator over [0, cap) with coalescing of freed ranges.
+class Arena {
+public:
+    explicit Arena(size_t cap = 0) { reset(cap); }
+    void reset(size_t cap) {
+        free_.clear();
+        cap_ = cap;
+        used_ = 0;
+        if (cap) free_[0] = cap;
+    }
+    // returns offset or SIZE_MAX
+    size_t alloc(size_t n) {
+        n = al256(n ? n : 1);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                const size_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > n) free_[off + n] = len - n;
+                used_ += n;
+                return off;
+            }
+        }
+        return SIZE_MAX;
+    }
+    void release(size_t off, size_t n) {
+        n = al256(n ? n : 1);
+        used_ -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+    size_t cap() const { return cap_; }
+
+private:
+    std::map<size_t, size_t> free_;
+    size_t cap_ = 0, used_ = 0;
+};
+
+struct Request {
+    int pset;
+    uint32_t key;
+    std::vector<uint8_t> msg;
+    uint8_t* out;          // caller's signature buffer (host)
+    uint64_t t_arrive;     // ns (submit time, or scheduled arrival in replay)
+    uint64_t t_done = 0;
+    int status = -1;       // -1 pending, else hs_status
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    bool busy = false;
+    std::atomic<bool> finished{false};
+    int pset = 0;
+    std::vector<uint64_t> ids;
+    size_t dev_off = 0, dev_len = 0, host_off = 0, host_len = 0;
+    size_t sig_host = 0;   // offset of the signatures inside the host region
+    void* server = nullptr;
+};
+
+}  // namespace
+
+struct ServerImpl {
+    hs_server_config cfg;
+    int device = 0;
+    // per set: resident keys and midstates
+    uint8_t* sk_dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    KeyBlock* kb_dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t nkeys[4] = {0, 0, 0, 0};
+    // arenas
+    uint8_t* dev_base = nullptr;
+    uint8_t* host_base = nullptr;
+    Arena dev_arena, host_arena;
+    std::vector<Slot> slots;
+    // requests
+    std::mutex mu;
+    std::condition_variable cv_sched, cv_done;
+    std::unordered_map<uint64_t, Request> reqs;
+    std::deque<uint64_t> pending[4];
+    std::deque<uint64_t> completed;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread th;
+    // stats
+    uint64_t n_done = 0, n_batches = 0, n_batched_reqs = 0, max_dev_used = 0;
+    uint32_t max_inflight_seen = 0;
+    hs_status fatal = HS_OK;
+};
+
+namespace {
+
+int sig_bytes_of(int p) {
+    switch (p) {
+    case 0: return P128f::SIG_BYTES;
+    case 1: return P192f::SIG_BYTES;
+    case 2: return P256f::SIG_BYTES;
+    case 3: return PToy::SIG_BYTES;
+    }
+    return 0;
+}
+int n_of(int p) { return p == 1 ? 24 : (p == 2 ? 32 : 16); }
+
+void CUDART_CB on_batch_done(void* arg) {
+    Slot* s = static_cast<Slot*>(arg);
+    ServerImpl* sv = static_cast<ServerImpl*>(s->server);
+    s->finished.store(true);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);   // no CUDA calls in a host callback
+    }
+    sv->cv_sched.notify_one();
+}
+
+// Bytes a batch needs from each arena.
+struct Need { size_t dev, host; };
+Need batch_need(int pset, size_t count, size_t msg_bytes, uint32_t ck) {
+    const size_t sig = (size_t)count * sig_bytes_of(pset);
+    Need n;
+    n.host = al256(msg_bytes) + al256(count * 8) + al256(count * 4) + al256(sig);
+    n.dev = n.host + al256(scratch_bytes(pset, 0, (uint32_t)count, ck));
+    return n;
+}
+
+// Retire finished batches (lock held).
+void retire(ServerImpl& sv) {
+    for (auto& s : sv.slots) {
+        if (!s.busy || !s.finished.load()) continue;
+        const int S = sig_bytes_of(s.pset);
+        const uint64_t t = now_ns();
+        const cudaError_t e = cudaStreamQuery(s.stream);   // callback ran after the D2H copy
+        for (size_t i = 0; i < s.ids.size(); i++) {
+            auto it = sv.reqs.find(s.ids[i]);
+            if (it == sv.reqs.end()) continue;
+            Request& r = it->second;
+            if (e == cudaSuccess || e == cudaErrorNotReady) {
+                if (r.out) memcpy(r.out, sv.host_base + s.host_off + s.sig_host + (size_t)i * S, S);
+                r.status = HS_OK;
+            } else {
+                r.status = HS_ECUDA;
+            }
+            r.t_done = t;
+            sv.completed.push_back(s.ids[i]);
+            sv.n_done++;
+        }
+        sv.dev_arena.release(s.dev_off, s.dev_len);
+        sv.host_arena.release(s.host_off, s.host_len);
+        s.ids.clear();
+        s.busy = false;
+        s.finished.store(false);
+        sv.cv_done.notify_all();
+    }
+}
+
+// Form and launch one batch on a free slot (lock held).  Returns false if
+// nothing could be launched (no pending request, or no memory for even one).
+bool admit(ServerImpl& sv, Slot& slot) {
+    int best = -1;
+    uint64_t oldest = UINT64_MAX;
+    for (int p = 0; p < 4; p++)
+        if (!sv.pending[p].empty()) {
+            const uint64_t t = sv.reqs[sv.pending[p].front()].t_arrive;
+            if (t < oldest) { oldest = t; best = p; }
+        }
+    if (best < 0) return false;
+    const int p = best;
+    const uint32_t ck = chain_checkpoint_stride();
+    // take requests while the cumulative need fits what the arenas could give
+    size_t count = 0, msg_bytes = 0;
+    const size_t limit = std::min<size_t>(sv.cfg.max_batch, sv.pending[p].size());
+    const size_t dev_free = sv.dev_arena.cap() - sv.dev_arena.used();
+    const size_t host_free = sv.host_arena.cap() - sv.host_arena.used();
+    while (count < limit) {
+        const Request& r = sv.reqs[sv.pending[p][count]];
+        const Need n = batch_need(p, count + 1, msg_bytes + r.msg.size(), ck);
+        if (n.dev > dev_free || n.host > host_free) break;
+        msg_bytes += r.msg.size();
+        count++;
+    }
+    if (count == 0) return false;
+    Need need = batch_need(p, count, msg_bytes, ck);
+    size_t doff = sv.dev_arena.alloc(need.dev);
+    size_t hoff = doff == SIZE_MAX ? SIZE_MAX : sv.host_arena.alloc(need.host);
+    while ((doff == SIZE_MAX || hoff == SIZE_MAX) && count > 1) {   // fragmentation: shrink
+        if (doff != SIZE_MAX) sv.dev_arena.release(doff, need.dev);
+        count = (count + 1) / 2;
+        msg_bytes = 0;
+        for (size_t i = 0; i < count; i++) msg_bytes += sv.reqs[sv.pending[p][i]].msg.size();
+        need = batch_need(p, count, msg_bytes, ck);
+        doff = sv.dev_arena.alloc(need.dev);
+        hoff = doff == SIZE_MAX ? SIZE_MAX : sv.host_arena.alloc(need.host);
+    }
+    if (doff == SIZE_MAX || hoff == SIZE_MAX) {
+        if (doff != SIZE_MAX) sv.dev_arena.release(doff, need.dev);
+        return false;
+    }
+    // host staging layout: msgs | lens | key_idx | sigs  (device: same, then scratch)
+    uint8_t* h = sv.host_base + hoff;
+    uint8_t* d = sv.dev_base + doff;
+    const size_t o_lens = al256(msg_bytes), o_kidx = o_lens + al256(count * 8),
+                 o_sigs = o_kidx + al256(count * 4), o_scr = o_sigs + al256(count * (size_t)sig_bytes_of(p));
+    slot.ids.clear();
+    size_t mo = 0;
+    for (size_t i = 0; i < count; i++) {
+        const uint64_t id = sv.pending[p].front();
+        sv.pending[p].pop_front();
+        const Request& r = sv.reqs[id];
+        if (!r.msg.empty()) memcpy(h + mo, r.msg.data(), r.msg.size());
+        mo += r.msg.size();
+        reinterpret_cast<uint64_t*>(h + o_lens)[i] = r.msg.size();
+        reinterpret_cast<uint32_t*>(h + o_kidx)[i] = r.key;
+        slot.ids.push_back(id);
+    }
+    Batch b{};
+    b.pset = p;
+    b.keys_in = sv.sk_dev[p];
+    b.num_keys = 0;                               // scratch holds no key blocks (see below)
+    b.key_idx = reinterpret_cast<const uint32_t*>(d + o_kidx);
+    b.msgs = msg_bytes ? d : d + o_lens;          // never read when all lengths are 0
+    b.lens = reinterpret_cast<const uint64_t*>(d + o_lens);
+    b.count = (uint32_t)count;
+    b.sigs = d + o_sigs;
+    b.ck = ck;
+    b.status = device_status_word();
+    carve_scratch(b, d + o_scr);
+    b.keys = sv.kb_dev[p];                        // resident midstates, not scratch
+    b.num_keys = sv.nkeys[p];
+    cudaStream_t s = slot.stream;
+    cudaError_t e = cudaMemcpyAsync(d, h, o_sigs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_offsets(b, s);
+    if (e == cudaSuccess) e = launch_message(b, false, s);
+    if (e == cudaSuccess) e = launch_fors(b, s);
+    if (e == cudaSuccess) e = launch_fors_pk(b, s);
+    if (e == cudaSuccess) e = launch_tree(b, s);
+    if (e == cudaSuccess) e = launch_wots(b, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + o_sigs, d + o_sigs, count * (size_t)sig_bytes_of(p), cudaMemcpyDeviceToHost, s);
+    slot.pset = p;
+    slot.dev_off = doff;
+    slot.dev_len = need.dev;
+    slot.host_off = hoff;
+    slot.host_len = need.host;
+    slot.sig_host = o_sigs;
+    slot.busy = true;
+    slot.finished.store(false);
+    if (e == cudaSuccess) e = cudaLaunchHostFunc(s, on_batch_done, &slot);
+    if (e != cudaSuccess) {
+        sv.fatal = HS_ECUDA;
+        slot.finished.store(true);      // retire() marks the requests failed
+        cudaGetLastError();
+    }
+    sv.n_batches++;
+    sv.n_batched_reqs += count;
+    sv.max_dev_used = std::max<uint64_t>(sv.max_dev_used, sv.dev_arena.used());
+    return true;
+}
+
+void scheduler(ServerImpl* sv) {
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (!sv->stop) {
+        retire(*sv);
+        bool launched = true;
+        while (launched) {
+            launched = false;
+            for (auto& s : sv->slots)
+                if (!s.busy && admit(*sv, s)) { launched = true; break; }
+        }
+        uint32_t busy = 0;
+        for (auto& s : sv->slots) busy += s.busy ? 1 : 0;
+        sv->max_inflight_seen = std::max(sv->max_inflight_seen, busy);
+        // sleep until a submit, a batch completion, or a short timeout
+        sv->cv_sched.wait_for(lk, std::chrono::milliseconds(busy ? 2 : 50));
+    }
+    retire(*sv);
+}
+
+}  // namespace
+}  // namespace hs
+
+using namespace hs;
+
+struct hs_server { ServerImpl impl; };
+
+static hs_status sv_fail(hs_status st, const char* msg) {
+    set_last_error(msg);
+    return st;
+}
+
+HS_API hs_status hs_server_create(const hs_server_config* cfg, const uint8_t* const sks[4],
+                                  const uint32_t nkeys[4], hs_server** out) {
+    if (!cfg || !sks || !nkeys || !out) return sv_fail(HS_EINVAL, "hs_server_create: NULL argument");
+    if (cfg->max_inflight < 1 || cfg->max_inflight > 16 || cfg->max_batch < 1 || cfg->mem_budget_bytes < (1u << 20))
+        return sv_fail(HS_EINVAL, "hs_server_create: max_inflight 1..16, max_batch >= 1, budget >= 1 MiB");
+    hs_server* s = new hs_server();
+    ServerImpl& sv = s->impl;
+    sv.cfg = *cfg;
+    cudaGetDevice(&sv.device);
+    bool ok = true;
+    for (int p = 0; p < 4 && ok; p++) {
+        sv.nkeys[p] = nkeys[p];
+        if (!nkeys[p]) continue;
+        if (!sks[p]) { ok = false; break; }
+        const size_t kb = (size_t)nkeys[p] * 4 * n_of(p);
+        ok = cudaMalloc(&sv.sk_dev[p], kb) == cudaSuccess &&
+             cudaMalloc(&sv.kb_dev[p], (size_t)nkeys[p] * sizeof(KeyBlock)) == cudaSuccess &&
+             cudaMemcpy(sv.sk_dev[p], sks[p], kb, cudaMemcpyDefault) == cudaSuccess;
+        if (ok) {
+            Batch b{};
+            b.pset = p;
+            b.keys_in = sv.sk_dev[p];
+            b.num_keys = nkeys[p];
+            b.keys = sv.kb_dev[p];
+            ok = launch_keyprep(b, false, 0) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+        }
+    }
+    const size_t host_bytes = cfg->pinned_bytes ? cfg->pinned_bytes : cfg->mem_budget_bytes / 2;
+    ok = ok && cudaMalloc(&sv.dev_base, cfg->mem_budget_bytes) == cudaSuccess &&
+         cudaHostAlloc(&sv.host_base, host_bytes, cudaHostAllocDefault) == cudaSuccess;
+    if (ok) {
+        sv.dev_arena.reset(cfg->mem_budget_bytes);
+        sv.host_arena.reset(host_bytes);
+        sv.slots = std::vector<Slot>(cfg->max_inflight);
+        for (auto& sl : sv.slots) {
+            sl.server = &sv;
+            ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess;
+        }
+    }
+    if (!ok || !device_status_word()) {
+        cudaGetLastError();
+        hs_server_destroy(s);
+        return sv_fail(HS_ENOMEM, "hs_server_create: could not reserve keys, arenas or streams");
+    }
+    sv.th = std::thread(scheduler, &sv);
+    *out = s;
+    return HS_OK;
+}
+
+static hs_status submit_at(hs_server* s, hs_params p, uint32_t key, const uint8_t* msg, uint64_t len,
+                           uint8_t* sig_out, uint64_t* id, uint64_t t_arrive) {
+    if (!s || (int)p < 0 || (int)p > 3 || (len && !msg))
+        return sv_fail(HS_EINVAL, "hs_server_submit: bad argument");
+    ServerImpl& sv = s->impl;
+    if (key >= sv.nkeys[p]) return sv_fail(HS_EKEY, "hs_server_submit: key index out of range");
+    Request r;
+    r.pset = p;
+    r.key = key;
+    r.msg.assign(msg, msg + len);
+    r.out = sig_out;
+    r.t_arrive = t_arrive;
+    const Need one = batch_need(p, 1, len, chain_checkpoint_stride());
+    if (one.dev > sv.dev_arena.cap() || one.host > sv.host_arena.cap())
+        return sv_fail(HS_EINVAL, "hs_server_submit: request larger than the memory budget");
+    uint64_t rid;
+    {
+        std::lock_guard<std::mutex> lk(sv.mu);
+        rid = sv.next_id++;
+        sv.reqs.emplace(rid, std::move(r));
+        sv.pending[p].push_back(rid);
+    }
+    sv.cv_sched.notify_one();
+    if (id) *id = rid;
+    return HS_OK;
+}
+
+HS_API hs_status hs_server_submit(hs_server* s, hs_params p, uint32_t key, const uint8_t* msg, uint64_t len,
+                                  uint8_t* sig_out, uint64_t* id) {
+    return submit_at(s, p, key, msg, len, sig_out, id, now_ns());
+}
+
+HS_API hs_status hs_server_wait(hs_server* s, uint64_t id, uint32_t timeout_ms) {
+    if (!s) return sv_fail(HS_EINVAL, "hs_server_wait: NULL server");
+    ServerImpl& sv = s->impl;
+    std::unique_lock<std::mutex> lk(sv.mu);
+    auto it = sv.reqs.find(id);
+    if (it == sv.reqs.end()) return sv_fail(HS_EINVAL, "hs_server_wait: unknown request id");
+    const bool done = sv.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+        auto f = sv.reqs.find(id);
+        return f == sv.reqs.end() || f->second.status >= 0;
+    });
+    if (!done) return sv_fail(HS_ETIMEOUT, "hs_server_wait: timed out");
+    auto f = sv.reqs.find(id);
+    return f == sv.reqs.end() ? HS_OK : (hs_status)f->second.status;   // collected by a poll: it completed
+}
+
+HS_API int hs_server_poll(hs_server* s, uint64_t* ids, uint64_t* latency_ns, int max) {
+    if (!s || max < 0) return -1;
+    ServerImpl& sv = s->impl;
+    std::lock_guard<std::mutex> lk(sv.mu);
+    int n = 0;
+    while (n < max && !sv.completed.empty()) {
+        const uint64_t id = sv.completed.front();
+        sv.completed.pop_front();
+        auto it = sv.reqs.find(id);
+        if (it == sv.reqs.end()) continue;
+        if (ids) ids[n] = id;
+        if (latency_ns) latency_ns[n] = it->second.t_done - it->second.t_arrive;
+        sv.reqs.erase(it);
+        n++;
+    }
+    return n;
+}
+
+HS_API hs_status hs_server_get_stats(hs_server* s, hs_server_stats* st) {
+    if (!s || !st) return sv_fail(HS_EINVAL, "hs_server_get_stats: NULL argument");
+    ServerImpl& sv = s->impl;
+    std::lock_guard<std::mutex> lk(sv.mu);
+    st->completed = sv.n_done;
+    st->batches = sv.n_batches;
+    st->batched_requests = sv.n_batched_reqs;
+    st->max_device_bytes_in_use = sv.max_dev_used;
+    st->max_inflight_batches = sv.max_inflight_seen;
+    uint64_t pend = 0;
+    for (int p = 0; p < 4; p++) pend += sv.pending[p].size();
+    st->pending = pend;
+    return sv.fatal;
+}
+
+HS_API hs_status hs_server_replay(hs_server* s, uint32_t count, const uint8_t* params, const uint32_t* keys,
+                                  const uint32_t* pool_idx, const uint8_t* pool_msgs, const uint64_t* pool_lens,
+                                  uint32_t pool_count, const uint64_t* arrival_ns, uint8_t* sigs,
+                                  const uint64_t* sig_offsets, uint64_t* latency_ns, uint32_t timeout_ms) {
+    if (!s || (count && (!params || !keys || !pool_idx || !pool_lens || !pool_count || !arrival_ns || !latency_ns)) ||
+        (sigs && !sig_offsets))
+        return sv_fail(HS_EINVAL, "hs_server_replay: NULL argument");
+    ServerImpl& sv = s->impl;
+    std::vector<uint64_t> pool_off(pool_count + 1, 0);
+    for (uint32_t i = 0; i < pool_count; i++) pool_off[i + 1] = pool_off[i] + pool_lens[i];
+    for (uint32_t i = 0; i < count; i++)
+        if (pool_idx[i] >= pool_count) return sv_fail(HS_EINVAL, "hs_server_replay: pool index out of range");
+    std::vector<uint64_t> ids(count);
+    std::unordered_map<uint64_t, uint32_t> index;
+    index.reserve(count * 2 + 16);
+    const uint64_t t0 = now_ns();
+    for (uint32_t i = 0; i < count; i++) {
+        const uint64_t due = t0 + arrival_ns[i];
+        for (uint64_t t = now_ns(); t < due; t = now_ns()) {
+            if (due - t > 200000) std::this_thread::sleep_for(std::chrono::nanoseconds(due - t - 100000));
+        }
+        const uint32_t q = pool_idx[i];
+        // latency is measured from the scheduled arrival, not from the submit
+        hs_status st = submit_at(s, (hs_params)params[i], keys[i], pool_msgs ? pool_msgs + pool_off[q] : nullptr,
+                                 pool_lens[q], sigs ? sigs + sig_offsets[i] : nullptr, &ids[i], due);
+        if (st != HS_OK) return st;
+        index[ids[i]] = i;
+    }
+    uint32_t got = 0;
+    std::vector<uint64_t> cid(4096), lat(4096);
+    const uint64_t deadline = now_ns() + (uint64_t)timeout_ms * 1000000ull;
+    while (got < count) {
+        const int n = hs_server_poll(s, cid.data(), lat.data(), (int)cid.size());
+        for (int k = 0; k < n; k++) {
+            auto it = index.find(cid[k]);
+            if (it != index.end()) { latency_ns[it->second] = lat[k]; got++; }
+        }
+        if (got >= count) break;
+        if (now_ns() > deadline) return sv_fail(HS_ETIMEOUT, "hs_server_replay: requests still pending at the timeout");
+        std::unique_lock<std::mutex> lk(sv.mu);
+        sv.cv_done.wait_for(lk, std::chrono::milliseconds(5));
+    }
+    return sv.fatal;
+}
+
+HS_API hs_status hs_server_destroy(hs_server* s) {
+    if (!s) return HS_OK;
+    ServerImpl& sv = s->impl;
+    if (sv.th.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(sv.mu);
+            sv.stop = true;
+        }
+        sv.cv_sched.notify_all();
+        sv.th.join();
+    }
+    for (auto& sl : sv.slots)
+        if (sl.stream) {
+            cudaStreamSynchronize(sl.stream);
+            cudaStreamDestroy(sl.stream);
+        }
+    for (int p = 0; p < 4; p++) {
+        if (sv.sk_dev[p]) cudaFree(sv.sk_dev[p]);
+        if (sv.kb_dev[p]) cudaFree(sv.kb_dev[p]);
+    }
+    if (sv.dev_base) cudaFree(sv.dev_base);
+    if (sv.host_base) cudaFreeHost(sv.host_base);
+    delete s;
+    return HS_OK;
+}

@@ -51,6 +51,20 @@ def load():
     L.hs_probe_int_pipes.restype = C.c_int
     L.hs_sign_mixed.argtypes = [C.c_void_p, C.c_uint32, C.c_int, C.c_void_p]
     L.hs_sign_mixed.restype = C.c_int
+    L.hs_server_create.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]
+    L.hs_server_submit.argtypes = [C.c_void_p, C.c_int, C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p,
+                                   C.POINTER(C.c_uint64)]
+    L.hs_server_wait.argtypes = [C.c_void_p, C.c_uint64, C.c_uint32]
+    L.hs_server_poll.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    L.hs_server_poll.restype = C.c_int
+    L.hs_server_get_stats.argtypes = [C.c_void_p, C.c_void_p]
+    L.hs_server_replay.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_uint32]
+    L.hs_server_destroy.argtypes = [C.c_void_p]
+    for name in ("hs_server_create", "hs_server_submit", "hs_server_wait", "hs_server_get_stats",
+                 "hs_server_replay", "hs_server_destroy"):
+        getattr(L, name).restype = C.c_int
     L.hs_set_chain_checkpoint.argtypes = [C.c_uint32]
     L.hs_set_chain_checkpoint.restype = C.c_int
     for name in ("hs_keygen", "hs_sign_batch", "hs_verify_batch", "hs_check_status"):
@@ -221,3 +235,110 @@ def hs_sign_mixed(jobs, use_graph=True, stream=None):
                          int(jb["lens"].shape[0]), _ptr(jb["sigs"]))
     _check(load().hs_sign_mixed(C.cast(arr, C.c_void_p), len(jobs), 1 if use_graph else 0, _stream(stream)))
     return [jb["sigs"] for jb in jobs]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_inflight", C.c_uint32), ("max_batch", C.c_uint32), ("mem_budget_bytes", C.c_uint64),
+                ("pinned_bytes", C.c_uint64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_uint64), ("batches", C.c_uint64), ("batched_requests", C.c_uint64),
+                ("pending", C.c_uint64), ("max_device_bytes_in_use", C.c_uint64),
+                ("max_inflight_batches", C.c_uint32)]
+
+
+class Server:
+    """Continuous-batching signing server (hs_server_* of include/hs.h).
+
+    ``keys``: {params: sk array/tensor [num_keys, 4n]} for the sets it serves.
+    """
+
+    def __init__(self, keys, max_inflight=4, max_batch=1024, mem_budget=8 << 30, pinned=0):
+        L = load()
+        self._keepalive = []
+        sks = (C.c_void_p * 4)()
+        nk = (C.c_uint32 * 4)()
+        for ps, sk in keys.items():
+            pid = PARAMS[ps]
+            self._keepalive.append(sk)
+            sks[pid] = _ptr(sk)
+            nk[pid] = int(sk.shape[0])
+        cfg = ServerConfig(int(max_inflight), int(max_batch), int(mem_budget), int(pinned))
+        h = C.c_void_p()
+        _check(L.hs_server_create(C.byref(cfg), sks, nk, C.byref(h)))
+        self._h = h
+        self.budget = int(mem_budget)
+
+    def submit(self, params, key, msg, out=None):
+        """Queue one request; returns (id, out) where out receives the signature."""
+        msg = bytes(msg)
+        if out is None:
+            out = np.empty(sig_bytes(params), dtype=np.uint8)
+        rid = C.c_uint64()
+        buf = C.create_string_buffer(msg, len(msg)) if msg else None
+        _check(load().hs_server_submit(self._h, _pid(params), int(key), buf, len(msg), _ptr(out), C.byref(rid)))
+        return rid.value, out
+
+    def wait(self, rid, timeout_ms=60000):
+        _check(load().hs_server_wait(self._h, int(rid), int(timeout_ms)))
+
+    def poll(self, max_n=4096):
+        ids = np.empty(max_n, dtype=np.uint64)
+        lat = np.empty(max_n, dtype=np.uint64)
+        n = load().hs_server_poll(self._h, _ptr(ids), _ptr(lat), max_n)
+        return list(zip(ids[:n].tolist(), lat[:n].tolist()))
+
+    def stats(self):
+        st = ServerStats()
+        rc = load().hs_server_get_stats(self._h, C.byref(st))
+        d = {f: getattr(st, f) for f, _ in ServerStats._fields_}
+        d["status"] = rc
+        return d
+
+    def replay(self, params, keys, pool_idx, pool_msgs, pool_lens, arrival_ns, keep_signatures=False,
+               timeout_ms=600000):
+        """Open-loop load: request i arrives arrival_ns[i] after the start.
+        Returns (latency_ns array, signatures list or None)."""
+        params = np.ascontiguousarray(params, dtype=np.uint8)
+        keys = np.ascontiguousarray(keys, dtype=np.uint32)
+        pool_idx = np.ascontiguousarray(pool_idx, dtype=np.uint32)
+        pool_lens = np.ascontiguousarray(pool_lens, dtype=np.uint64)
+        arrival_ns = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+        n = int(params.shape[0])
+        lat = np.zeros(n, dtype=np.uint64)
+        sigs = offs = None
+        if keep_signatures:
+            sizes = np.array([SIG_BY_ID[int(p)] for p in params], dtype=np.uint64)
+            offs = np.zeros(n, dtype=np.uint64)
+            if n > 1:
+                np.cumsum(sizes[:-1], out=offs[1:])
+            sigs = np.zeros(int(sizes.sum()), dtype=np.uint8)
+        msgs = pool_msgs if pool_msgs is not None and pool_msgs.size else np.zeros(16, np.uint8)
+        _check(load().hs_server_replay(self._h, n, _ptr(params), _ptr(keys), _ptr(pool_idx), _ptr(msgs),
+                                       _ptr(pool_lens), int(pool_lens.shape[0]), _ptr(arrival_ns), _ptr(sigs),
+                                       _ptr(offs), _ptr(lat), int(timeout_ms)))
+        out = None
+        if keep_signatures:
+            out = [sigs[int(o):int(o) + SIG_BY_ID[int(p)]].tobytes() for o, p in zip(offs, params)]
+        return lat, out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hs_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+SIG_BY_ID = {0: 17088, 1: 35664, 2: 49856, 3: 1456}

@@ -105,6 +105,34 @@ def mixed(count=32768, mix=(0.5, 0.3, 0.2), keys=(32, 19, 13), lengths=("logunif
     return out
 
 
+def serving_trace(rate, seconds, mix=(0.6, 0.25, 0.15), keys=(614, 256, 154), lengths=(16, 4096),
+                  pool=65536, seed=BASE_SEED + 4):
+    """Open-loop serving load: Poisson arrivals at ``rate`` requests/s for
+    ``seconds``; each request draws its set from ``mix`` over (128f, 192f,
+    256f), a key uniformly among that set's keys, and a message from a pool
+    of ``pool`` seeded messages with log-uniform lengths.  Returns a dict of
+    arrays (params ids, key indices, pool indices, arrival times in ns) plus
+    the pool and one seed row per key and set."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.poisson(rate * seconds))
+    gaps = rng.exponential(1.0 / rate, size=n)
+    arrival = np.cumsum(gaps)
+    arrival_ns = (arrival * 1e9).astype(np.uint64)
+    which = rng.choice(3, size=n, p=np.asarray(mix) / np.sum(mix)).astype(np.uint8)
+    kidx = np.zeros(n, dtype=np.uint32)
+    for si in range(3):
+        sel = which == si
+        kidx[sel] = rng.integers(0, keys[si], size=int(sel.sum()))
+    pool_lens = log_uniform_lengths(rng, pool, lengths[0], lengths[1])
+    pool_msgs = np.frombuffer(rng.bytes(int(pool_lens.sum())), dtype=np.uint8).copy()
+    pool_idx = rng.integers(0, pool, size=n).astype(np.uint32)
+    seeds = {}
+    for si, ps in enumerate(("128f", "192f", "256f")):
+        seeds[ps] = np.frombuffer(rng.bytes(3 * N_BYTES[ps] * keys[si]), dtype=np.uint8).reshape(keys[si], -1).copy()
+    return {"params": which, "keys": kidx, "pool_idx": pool_idx, "arrival_ns": arrival_ns,
+            "pool_msgs": pool_msgs, "pool_lens": pool_lens, "seeds": seeds, "rate": rate, "seconds": seconds}
+
+
 def config(index, params=None):
     """The five workload recipes (sizes of the configurations the signer is
     specified on); ``params`` picks the set for the two-set / mixed recipes.
