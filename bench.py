@@ -332,10 +332,8 @@ def measure_serving(hs, inputs, seconds, rhos, burst=60000):
 def run_own(args):
     import numpy as np
     import torch
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
+    from paper_2512_23969_gb300 import replicas
+    ws, rank, local = replicas.init_from_env()
     torch.cuda.set_device(local)
     from paper_2512_23969_gb300 import build as hs_build
     hs_build.build()
@@ -369,8 +367,7 @@ def run_own(args):
         flush.fill_(i & 0xFF)
         step()
     torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -391,12 +388,10 @@ def run_own(args):
     for a, b in evs:
         step_ms.append(a.elapsed_time(b))
     hs.hs_profile_enable(False)
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * count * args.steps / (total_ms / 1e3)
+    torch.cuda.synchronize()
+    replicas.barrier()
+    total_ms = replicas.max_over_ranks(sum(step_ms))
+    value = replicas.job_rate(ws, count, args.steps, total_ms)
 
     # correctness guard on the timed output: GPU verify of every signature
     ok = hs.hs_verify_batch(ps, pk, msgs, lens, sigs.view(count, S), key_idx=kidx, num_keys=wl.num_keys)
@@ -404,7 +399,7 @@ def run_own(args):
 
     # end to end through the C ABI with pinned host buffers (copies inside the call)
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and rank == 0:
         sk_h = sk.cpu().pin_memory()
         msgs_h = torch.from_numpy(wl.msgs).pin_memory()
         lens_h = torch.from_numpy(wl.lens).pin_memory()
@@ -465,14 +460,14 @@ def run_own(args):
     # same events: 192f / 256f batches, and the mixed-parameter batch in one
     # graph launch against one hs_sign_batch call per set
     others = {}
-    if args.other_configs:
+    if args.other_configs and rank == 0:
         try:
             others = measure_other_configs(hs, inputs, args, stream, flush)
         except Exception as exc:      # keep the main line; report what failed
             others = {"error": repr(exc)[:300]}
 
     serving = None
-    if args.serving_seconds > 0:
+    if args.serving_seconds > 0 and rank == 0:
         try:
             serving = measure_serving(hs, inputs, args.serving_seconds, (0.5, 0.75, 1.0))
         except Exception as exc:
@@ -512,6 +507,7 @@ def run_own(args):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    replicas.barrier()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
