@@ -74,6 +74,31 @@ def lib():
     return _lib
 
 
+class library:
+    """Context manager that points every call of this module at another build
+    of the oracle source (the tests use it to check that the pins catch
+    deliberately planted mistakes), restoring the regular build on exit."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = lib()
+        _lib = None
+        real_build = _build.build
+        _build.build = lambda force=False, _p=self.path: _p
+        try:
+            lib()
+        finally:
+            _build.build = real_build
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+
+
 def _pid(ps):
     return PARAM_IDS[ps] if isinstance(ps, str) else int(ps)
 
