@@ -16,7 +16,8 @@ namespace hs {
 
 // ------------------------------------------------------------- byte SHA-x
 // Streaming SHA-256 / SHA-512 over bytes and big-endian words.  Only the
-// message stage uses it (a few blocks per 32-byte message).
+// message stage uses it: key and prefix bytes go through the byte path,
+// message bodies a whole block at a time (block_from).
 template <bool BIG>
 struct ByteSha {
     static constexpr int B = BIG ? 128 : 64;   // block bytes
@@ -62,18 +63,47 @@ struct ByteSha {
     __device__ void words(const uint32_t* w, int nbytes) {
         for (int i = 0; i < nbytes; i++) byte(w[i >> 2] >> (24 - 8 * (i & 3)));
     }
+    // One whole block straight from memory at any alignment: aligned 32-bit
+    // loads, and one prmt per big-endian word picks its 4 bytes across two
+    // loaded words.  Every word loaded holds at least one byte of the block,
+    // so nothing outside the message is touched.
+    __device__ void block_from(const uint8_t* q) {
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(q);
+        const uint32_t* a = reinterpret_cast<const uint32_t*>(addr & ~(uintptr_t)3);
+        const uint32_t sh = (uint32_t)(addr & 3);
+        uint32_t w[BW];
+        if (sh == 0) {
+#pragma unroll
+            for (int k = 0; k < BW; k++) w[k] = bswap32(__ldg(a + k));
+        } else {
+            const uint32_t sel = (sh << 12) | ((sh + 1) << 8) | ((sh + 2) << 4) | (sh + 3);
+            uint32_t w0 = __ldg(a);
+#pragma unroll
+            for (int k = 0; k < BW; k++) {
+                const uint32_t w1 = __ldg(a + k + 1);
+                w[k] = __byte_perm(w0, w1, sel);
+                w0 = w1;
+            }
+        }
+        if constexpr (BIG) {
+            uint64_t s[8], W[16];
+#pragma unroll
+            for (int i = 0; i < 8; i++) s[i] = ((uint64_t)st[2 * i] << 32) | st[2 * i + 1];
+#pragma unroll
+            for (int i = 0; i < 16; i++) W[i] = ((uint64_t)w[2 * i] << 32) | w[2 * i + 1];
+            sha512_compress(s, W);
+#pragma unroll
+            for (int i = 0; i < 8; i++) { st[2 * i] = (uint32_t)(s[i] >> 32); st[2 * i + 1] = (uint32_t)s[i]; }
+        } else {
+            sha256_compress_full(st, w);
+        }
+        total += B;
+    }
     // raw bytes from global memory at any alignment
     __device__ void mem(const uint8_t* p, uint64_t len) {
         uint64_t i = 0;
-        while (i < len && (fill & 3)) { byte(p[i]); i++; }
-        while (i + 4 <= len) {
-            blk[fill >> 2] = ((uint32_t)p[i] << 24) | ((uint32_t)p[i + 1] << 16) |
-                             ((uint32_t)p[i + 2] << 8) | (uint32_t)p[i + 3];
-            fill += 4;
-            total += 4;
-            i += 4;
-            if (fill == B) compress();
-        }
+        while (i < len && fill != 0) { byte(p[i]); i++; }   // finish the open block
+        for (; len - i >= (uint64_t)B; i += B) block_from(p + i);
         while (i < len) { byte(p[i]); i++; }
     }
     // Pad (0x80, zeros, bit length) and return the digest words (8 or 16).
