@@ -209,6 +209,14 @@ def run_reference(args):
     return 0
 
 
+def log(msg):
+    """Progress line on stderr (the JSON line alone goes to stdout)."""
+    print("[bench %.1fs] %s" % (time.perf_counter() - T_START, msg), file=sys.stderr, flush=True)
+
+
+T_START = time.perf_counter()
+
+
 def _time_steps(fn, stream, flush, steps, warmup):
     """CUDA-event time of fn() per step (L2 flushed between steps, outside)."""
     import torch
@@ -234,6 +242,7 @@ def measure_other_configs(hs, inputs, args, stream, flush):
     dev = lambda x: torch.from_numpy(x).cuda()
     steps, warmup = max(2, args.steps // 2), 3
     for ps in ("192f", "256f"):
+        log("config 2 %s" % ps)
         wl = inputs.config(2, ps)
         pk, sk = hs.hs_keygen(ps, dev(wl.seeds))
         m, l, k = dev(wl.msgs), dev(wl.lens), dev(wl.key_idx)
@@ -301,9 +310,14 @@ def measure_serving(hs, inputs, seconds, rhos, burst=60000):
         tr = inputs.serving_trace(rate=1e6, seconds=burst / 1e6, seed=inputs.BASE_SEED + 40)
         tr["arrival_ns"][:] = 0
         n = len(tr["params"])
+        log("serving: burst of %d requests" % n)
         t0 = time.perf_counter()
-        lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
-                            tr["arrival_ns"])
+        try:
+            lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
+                                tr["arrival_ns"], timeout_ms=120000)
+        except hs.HSError:
+            log("serving: burst timed out; server stats %s" % srv.stats())
+            raise
         wall = time.perf_counter() - t0
         peak = n / wall
         out["burst"] = {"requests": n, "value": round(peak, 1), "unit": "signatures/s",
@@ -312,8 +326,13 @@ def measure_serving(hs, inputs, seconds, rhos, burst=60000):
         for rho in rhos:
             tr = inputs.serving_trace(rate=rho * peak, seconds=seconds, seed=inputs.BASE_SEED + 41 + int(rho * 100))
             n = len(tr["params"])
-            lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
-                                tr["arrival_ns"])
+            log("serving: rho %.2f, %d requests" % (rho, n))
+            try:
+                lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
+                                    tr["arrival_ns"], timeout_ms=int(seconds * 1000) + 60000)
+            except hs.HSError:
+                log("serving: replay timed out; server stats %s" % srv.stats())
+                raise
             finish = (tr["arrival_ns"].astype(np.float64) + lat.astype(np.float64)).max() / 1e9
             st = srv.stats()
             out["rho_%.2f" % rho] = {"offered": round(rho * peak, 1), "requests": n,
@@ -362,6 +381,7 @@ def run_own(args):
     def step():
         hs.hs_sign_batch(ps, sk, msgs, lens, key_idx=kidx, sigs=sigs, num_keys=wl.num_keys, stream=stream)
 
+    log("main workload: %d x %s" % (count, ps))
     hs.hs_profile_enable(True)
     for i in range(args.warmup):
         flush.fill_(i & 0xFF)
@@ -514,6 +534,9 @@ def run_own(args):
 
 
 def main():
+    import faulthandler
+    faulthandler.enable()
+    faulthandler.dump_traceback_later(300, repeat=True)     # stacks on stderr if a stage stalls
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)

@@ -197,12 +197,18 @@ hs_status hs_set_chain_checkpoint(uint32_t stride);
  *                           leaves, the rest merges by shuffles)
  *   HS_TUNE_TREE_MIN_BLOCKS minimum resident 128-thread blocks per SM that
  *                           TREE_Sign is compiled for (0 = compiler's choice)
+ *   HS_TUNE_TREE_SPLIT_BELOW batches of fewer messages than this run
+ *                           TREE_Sign chain-parallel (a thread per WOTS+
+ *                           chain, then a thread per leaf for T_len and the
+ *                           Merkle levels); 0 = never.  Any value >= 0 is
+ *                           accepted; hs_tune_options lists suggestions.
+ *                           Extra scratch: len * n bytes per hypertree leaf.
  * hs_tune_options lists the compiled values (returns their number, or -1);
  * hs_tune_set returns HS_EINVAL for a value that is not compiled in;
  * hs_tune_get returns the current value (-1 for bad arguments).  The
  * package's autotuner measures these and stores the best per device.
  */
-typedef enum { HS_TUNE_FORS_LANES = 0, HS_TUNE_TREE_MIN_BLOCKS = 1 } hs_tune_knob;
+typedef enum { HS_TUNE_FORS_LANES = 0, HS_TUNE_TREE_MIN_BLOCKS = 1, HS_TUNE_TREE_SPLIT_BELOW = 2 } hs_tune_knob;
 int hs_tune_options(hs_params p, int knob, int32_t *values, int max);
 hs_status hs_tune_set(hs_params p, int knob, int32_t value);
 int32_t hs_tune_get(hs_params p, int knob);

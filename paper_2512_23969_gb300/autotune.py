@@ -19,7 +19,7 @@ import numpy as np
 
 from . import hs, inputs
 
-KNOBS = {"fors_lanes": 0, "tree_min_blocks": 1}
+KNOBS = {"fors_lanes": 0, "tree_min_blocks": 1, "tree_split_below": 2}
 STAGE_OF_KNOB = {"fors_lanes": "fors", "tree_min_blocks": "tree"}
 DEFAULT_COUNTS = {"128f": 16384, "192f": 8192, "256f": 8192, "toy": 4096}
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
@@ -83,6 +83,27 @@ def _stage_ms(params, wl, sk, dev, sigs, stage, reps):
     return best
 
 
+def tune_split(ps, counts=(64, 256, 1024, 2048, 4096, 8192), reps=3, verbose=True):
+    """Batch size below which the chain-parallel TREE_Sign is faster: time
+    the TREE stage in both forms at growing batch sizes."""
+    rows = {}
+    below = 0
+    for count in counts:
+        wl, sk, dev, sigs = _batch(ps, count)
+        ms = {}
+        for form, thr in (("split", 1 << 30), ("leaf", 0)):
+            set(ps, "tree_split_below", thr)
+            ms[form] = _stage_ms(ps, wl, sk, dev, sigs, "tree", reps)
+        rows[str(count)] = {k: round(v, 4) for k, v in ms.items()}
+        if verbose:
+            print("tune %s tree form at %d: split %.3f ms, per-leaf %.3f ms" % (ps, count, ms["split"], ms["leaf"]),
+                  flush=True)
+        if ms["split"] < ms["leaf"]:
+            below = count * 2 if count == counts[-1] else counts[counts.index(count) + 1]
+    set(ps, "tree_split_below", below)
+    return {"best": below, "ms": rows}
+
+
 def tune(params_list=("128f", "192f", "256f"), counts=None, reps=3, verbose=True):
     """Time every compiled variant of every knob; apply and return the best
     ({params: {knob: {"best": v, "ms": {v: ms}}}})."""
@@ -93,6 +114,7 @@ def tune(params_list=("128f", "192f", "256f"), counts=None, reps=3, verbose=True
         wl, sk, dev, sigs = _batch(ps, count)
         ref = None
         result[ps] = {}
+        result[ps]["tree_split_below"] = tune_split(ps, reps=reps, verbose=verbose)
         for knob, stage in STAGE_OF_KNOB.items():
             timings = {}
             for v in options(ps, knob):
@@ -131,7 +153,7 @@ def apply(path=CACHE):
     entry = data.get(device_key(), {})
     for ps, knobs in entry.items():
         for knob, rec in knobs.items():
-            if rec.get("best") in options(ps, knob):
+            if knob == "tree_split_below" or rec.get("best") in options(ps, knob):
                 set(ps, knob, rec["best"])
     return entry
 

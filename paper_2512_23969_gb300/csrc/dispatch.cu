@@ -17,20 +17,32 @@ const SetOps* set_ops(int pset) {
 
 namespace {
 // -1 = not set: use the table's default.
-std::atomic<int> g_tune[4][2] = {{{-1}, {-1}}, {{-1}, {-1}}, {{-1}, {-1}}, {{-1}, {-1}}};
+std::atomic<int> g_tune[4][3] = {{{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}};
+// Default batch size below which TREE_Sign runs chain-parallel, per set.
+constexpr int kSplitDefault[4] = {8192, 2048, 4096, 0};
 }
 
 int tune_get(int pset, int knob) {
     const SetOps* o = set_ops(pset);
-    if (!o || knob < 0 || knob > 1) return -1;
+    if (!o || knob < 0 || knob > 2) return -1;
     const int v = g_tune[pset][knob].load();
     if (v >= 0) return v;
-    return knob == 0 ? o->fors_lpt_default : o->tree_minb_default;
+    return knob == 0 ? o->fors_lpt_default : (knob == 1 ? o->tree_minb_default : kSplitDefault[pset]);
+}
+
+bool tree_split(int pset, uint32_t count) {
+    const int below = tune_get(pset, 2);
+    return below > 0 && count < (uint32_t)below;
 }
 
 bool tune_set(int pset, int knob, int value) {
     const SetOps* o = set_ops(pset);
-    if (!o || knob < 0 || knob > 1) return false;
+    if (!o || knob < 0 || knob > 2) return false;
+    if (knob == 2) {                      // any batch-size threshold
+        if (value < 0) return false;
+        g_tune[pset][2].store(value);
+        return true;
+    }
     const int* opts = knob == 0 ? o->fors_lpt : o->tree_minb;
     const int n = knob == 0 ? o->n_fors_lpt : o->n_tree_minb;
     for (int i = 0; i < n; i++)
@@ -59,7 +71,8 @@ cudaError_t launch_fors_pk(const Batch& b, cudaStream_t s) {
 }
 cudaError_t launch_tree(const Batch& b, cudaStream_t s) {
     const SetOps* o = set_ops(b.pset);
-    return o ? o->tree(b, tune_get(b.pset, 1), s) : cudaErrorInvalidValue;
+    if (!o) return cudaErrorInvalidValue;
+    return b.split ? o->tree_split(b, s) : o->tree(b, tune_get(b.pset, 1), s);
 }
 cudaError_t launch_wots(const Batch& b, cudaStream_t s) {
     const SetOps* o = set_ops(b.pset);

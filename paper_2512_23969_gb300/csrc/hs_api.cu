@@ -38,13 +38,13 @@ static hs_status cuda_fail(cudaError_t e, const char* what) {
     return fail(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-struct SetInfo { int n, d, k, len, sig; };
+struct SetInfo { int n, d, k, len, sig, leaves; };
 static bool set_info(int p, SetInfo* s) {
     switch (p) {
-    case 0: *s = {P128f::N, P128f::D, P128f::K, P128f::LEN, P128f::SIG_BYTES}; return true;
-    case 1: *s = {P192f::N, P192f::D, P192f::K, P192f::LEN, P192f::SIG_BYTES}; return true;
-    case 2: *s = {P256f::N, P256f::D, P256f::K, P256f::LEN, P256f::SIG_BYTES}; return true;
-    case 3: *s = {PToy::N, PToy::D, PToy::K, PToy::LEN, PToy::SIG_BYTES}; return true;
+    case 0: *s = {P128f::N, P128f::D, P128f::K, P128f::LEN, P128f::SIG_BYTES, P128f::LEAVES}; return true;
+    case 1: *s = {P192f::N, P192f::D, P192f::K, P192f::LEN, P192f::SIG_BYTES, P192f::LEAVES}; return true;
+    case 2: *s = {P256f::N, P256f::D, P256f::K, P256f::LEN, P256f::SIG_BYTES, P256f::LEAVES}; return true;
+    case 3: *s = {PToy::N, PToy::D, PToy::K, PToy::LEN, PToy::SIG_BYTES, PToy::LEAVES}; return true;
     }
     return false;
 }
@@ -55,14 +55,19 @@ static size_t chk_bytes(const SetInfo& s, uint32_t count, uint32_t ck) {
     return ck ? (size_t)count * s.d * s.len * (16 / ck) * (s.n / 4) * 4 : 0;
 }
 
-size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck) {
+static size_t ends_bytes(const SetInfo& s, uint32_t count, bool split) {
+    return split ? (size_t)count * s.d * s.leaves * s.len * (s.n / 4) * 4 : 0;
+}
+
+size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck, bool split) {
     SetInfo s;
     if (!set_info(pset, &s)) return 0;
     const size_t nw = (size_t)s.n / 4;
     return align256(sizeof(uint32_t)) + align256((size_t)num_keys * sizeof(KeyBlock)) +
            align256(((size_t)count + 1) * sizeof(uint64_t)) + align256((size_t)count * sizeof(MsgInfo)) +
            align256((size_t)count * s.k * nw * 4) + align256((size_t)count * nw * 4) +
-           align256((size_t)count * s.d * nw * 4) + align256(chk_bytes(s, count, ck));
+           align256((size_t)count * s.d * nw * 4) + align256(chk_bytes(s, count, ck)) +
+           align256(ends_bytes(s, count, split));
 }
 
 void carve_scratch(Batch& b, void* base) {
@@ -78,6 +83,8 @@ void carve_scratch(Batch& b, void* base) {
     b.pk_fors = reinterpret_cast<uint32_t*>(p);   p += align256((size_t)b.count * nw * 4);
     b.roots = reinterpret_cast<uint32_t*>(p);     p += align256((size_t)b.count * s.d * nw * 4);
     b.chk = b.ck ? reinterpret_cast<uint32_t*>(p) : nullptr;
+    p += align256(chk_bytes(s, b.count, b.ck));
+    b.ends = b.split ? reinterpret_cast<uint32_t*>(p) : nullptr;
 }
 
 // ----------------------------------------------------------- device state
@@ -181,7 +188,14 @@ HS_API int hs_sign_kernel_count(void) { return 7; }
 
 HS_API int hs_tune_options(hs_params p, int knob, int32_t* values, int max) {
     const SetOps* o = set_ops(p);
-    if (!o || knob < 0 || knob > 1) return -1;
+    if (!o || knob < 0 || knob > 2) return -1;
+    if (knob == 2) {                 // any threshold is valid; these are the suggested ones
+        static const int kSplit[] = {0, 256, 512, 1024, 2048, 4096, 8192};
+        const int n = 7;
+        for (int i = 0; i < n && i < max; i++)
+            if (values) values[i] = kSplit[i];
+        return n;
+    }
     const int* opts = knob == 0 ? o->fors_lpt : o->tree_minb;
     const int n = knob == 0 ? o->n_fors_lpt : o->n_tree_minb;
     for (int i = 0; i < n && i < max; i++)
@@ -331,7 +345,8 @@ static hs_status run_batch(bool verify, hs_params p, const uint8_t* keys_in, uin
     b.count = count;
     b.status = d->status;
     b.ck = verify ? 0u : g_ck;
-    const size_t scratch = scratch_bytes(p, num_keys, count, b.ck);
+    b.split = !verify && tree_split(p, count);
+    const size_t scratch = scratch_bytes(p, num_keys, count, b.ck, b.split);
     const size_t stage = (h_keys ? align256(key_bytes) : 0) + (h_idx ? align256((size_t)count * 4) : 0) +
                          (h_lens ? align256((size_t)count * 8) : 0) + (h_msgs ? align256(msg_total) : 0) +
                          (h_sig ? align256(sig_total) : 0) + (h_ok ? align256(count) : 0);

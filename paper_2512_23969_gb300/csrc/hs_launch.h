@@ -30,6 +30,8 @@ struct Batch {
     uint32_t* roots;          // count * D * NW words
     uint32_t* chk;            // WOTS chain checkpoints: count * D * LEN * (16 / ck) * NW words
     uint32_t ck;              // checkpoint stride (1, 2, 4) or 0 = none
+    bool split;               // TREE_Sign in its chain-parallel form (small batches)
+    uint32_t* ends;           // chain ends of the split form: count * D * 2^h' * LEN * NW words
     uint32_t* status;         // per-device status word
 };
 
@@ -44,7 +46,7 @@ cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
 uint32_t chain_checkpoint_stride();
 
 // Scratch bytes for a batch (each region 256-byte aligned).
-size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck);
+size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck, bool split = false);
 void carve_scratch(Batch& b, void* base);
 
 // Per-parameter-set kernel launchers (one table per set_<name>.cu).  The
@@ -57,6 +59,7 @@ struct SetOps {
     cudaError_t (*fors)(const Batch&, int, cudaStream_t);
     cudaError_t (*fors_pk)(const Batch&, cudaStream_t);
     cudaError_t (*tree)(const Batch&, int, cudaStream_t);
+    cudaError_t (*tree_split)(const Batch&, cudaStream_t);
     cudaError_t (*wots)(const Batch&, cudaStream_t);
     cudaError_t (*verify)(const Batch&, cudaStream_t);
     cudaError_t (*keygen)(const uint8_t*, uint32_t, uint8_t*, uint8_t*, cudaStream_t);
@@ -70,9 +73,11 @@ struct SetOps {
 extern const SetOps kOps_128F, kOps_192F, kOps_256F, kOps_Toy;
 const SetOps* set_ops(int pset);
 
-// Tuned launch shape per set (knob 0 = FORS lanes per tree, 1 = TREE min blocks).
+// Tuned launch shape per set (knob 0 = FORS lanes per tree, 1 = TREE min
+// blocks, 2 = batch size below which TREE_Sign runs chain-parallel).
 int tune_get(int pset, int knob);
 bool tune_set(int pset, int knob, int value);
+bool tree_split(int pset, uint32_t count);
 
 cudaError_t launch_keyprep(const Batch& b, bool from_pk, cudaStream_t s);
 cudaError_t launch_offsets(const Batch& b, cudaStream_t s);

@@ -130,9 +130,10 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
         b.count = jb.count;
         b.sigs = jb.sigs;
         b.ck = chain_checkpoint_stride();
+        b.split = tree_split(b.pset, b.count);
         bs.push_back(b);
         off.push_back(total);
-        total += scratch_bytes(b.pset, b.num_keys, b.count, b.ck);
+        total += scratch_bytes(b.pset, b.num_keys, b.count, b.ck, b.split);
     }
     if (bs.empty()) return HS_OK;
     MixedDev* d = nullptr;

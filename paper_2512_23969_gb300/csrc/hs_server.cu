@@ -16,11 +16,13 @@
 // signatures and scratch are carved from it (first-fit, coalescing); a batch
 // that does not fit waits for running batches to return memory.  Keys and
 // their SHA-2 midstates are made resident once, at creation.
-// Completion is signalled by a host callback on the batch stream; no thread
-// spins on the GPU, and every host wait takes a timeout.
+// Completion: each batch records an event after its signature copy; the
+// scheduler polls the events (cudaEventQuery) between bounded sleeps.  No
+// CUDA host function is used: a host function that waited for the
+// scheduler's mutex while the scheduler, holding it, made CUDA calls could
+// deadlock the two.  No thread spins on the GPU, and every wait is bounded.
 #include <cuda_runtime.h>
 #include <algorithm>
-#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -106,13 +108,13 @@ struct Request {
 
 struct Slot {
     cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
     bool busy = false;
-    std::atomic<bool> finished{false};
+    bool failed = false;
     int pset = 0;
     std::vector<uint64_t> ids;
     size_t dev_off = 0, dev_len = 0, host_off = 0, host_len = 0;
     size_t sig_host = 0;   // offset of the signatures inside the host region
-    void* server = nullptr;
 };
 
 }  // namespace
@@ -157,38 +159,32 @@ int sig_bytes_of(int p) {
 }
 int n_of(int p) { return p == 1 ? 24 : (p == 2 ? 32 : 16); }
 
-void CUDART_CB on_batch_done(void* arg) {
-    Slot* s = static_cast<Slot*>(arg);
-    ServerImpl* sv = static_cast<ServerImpl*>(s->server);
-    s->finished.store(true);
-    {
-        std::lock_guard<std::mutex> lk(sv->mu);   // no CUDA calls in a host callback
-    }
-    sv->cv_sched.notify_one();
-}
-
 // Bytes a batch needs from each arena.
 struct Need { size_t dev, host; };
 Need batch_need(int pset, size_t count, size_t msg_bytes, uint32_t ck) {
     const size_t sig = (size_t)count * sig_bytes_of(pset);
     Need n;
     n.host = al256(msg_bytes) + al256(count * 8) + al256(count * 4) + al256(sig);
-    n.dev = n.host + al256(scratch_bytes(pset, 0, (uint32_t)count, ck));
+    n.dev = n.host + al256(scratch_bytes(pset, 0, (uint32_t)count, ck, tree_split(pset, (uint32_t)count)));
     return n;
 }
 
 // Retire finished batches (lock held).
 void retire(ServerImpl& sv) {
     for (auto& s : sv.slots) {
-        if (!s.busy || !s.finished.load()) continue;
+        if (!s.busy) continue;
+        cudaError_t e = cudaSuccess;
+        if (!s.failed) {
+            e = cudaEventQuery(s.done);            // recorded after the signature copy
+            if (e == cudaErrorNotReady) continue;
+        }
         const int S = sig_bytes_of(s.pset);
         const uint64_t t = now_ns();
-        const cudaError_t e = cudaStreamQuery(s.stream);   // callback ran after the D2H copy
         for (size_t i = 0; i < s.ids.size(); i++) {
             auto it = sv.reqs.find(s.ids[i]);
             if (it == sv.reqs.end()) continue;
             Request& r = it->second;
-            if (e == cudaSuccess || e == cudaErrorNotReady) {
+            if (!s.failed && e == cudaSuccess) {
                 if (r.out) memcpy(r.out, sv.host_base + s.host_off + s.sig_host + (size_t)i * S, S);
                 r.status = HS_OK;
             } else {
@@ -202,7 +198,8 @@ void retire(ServerImpl& sv) {
         sv.host_arena.release(s.host_off, s.host_len);
         s.ids.clear();
         s.busy = false;
-        s.finished.store(false);
+        s.failed = false;
+        if (e != cudaSuccess) cudaGetLastError();
         sv.cv_done.notify_all();
     }
 }
@@ -276,6 +273,7 @@ bool admit(ServerImpl& sv, Slot& slot) {
     b.count = (uint32_t)count;
     b.sigs = d + o_sigs;
     b.ck = ck;
+    b.split = tree_split(p, (uint32_t)count);
     b.status = device_status_word();
     carve_scratch(b, d + o_scr);
     b.keys = sv.kb_dev[p];                        // resident midstates, not scratch
@@ -297,11 +295,11 @@ bool admit(ServerImpl& sv, Slot& slot) {
     slot.host_len = need.host;
     slot.sig_host = o_sigs;
     slot.busy = true;
-    slot.finished.store(false);
-    if (e == cudaSuccess) e = cudaLaunchHostFunc(s, on_batch_done, &slot);
+    slot.failed = false;
+    if (e == cudaSuccess) e = cudaEventRecord(slot.done, s);
     if (e != cudaSuccess) {
         sv.fatal = HS_ECUDA;
-        slot.finished.store(true);      // retire() marks the requests failed
+        slot.failed = true;             // retire() marks the requests failed
         cudaGetLastError();
     }
     sv.n_batches++;
@@ -324,8 +322,9 @@ void scheduler(ServerImpl* sv) {
         uint32_t busy = 0;
         for (auto& s : sv->slots) busy += s.busy ? 1 : 0;
         sv->max_inflight_seen = std::max(sv->max_inflight_seen, busy);
-        // sleep until a submit, a batch completion, or a short timeout
-        sv->cv_sched.wait_for(lk, std::chrono::milliseconds(busy ? 2 : 50));
+        // sleep until a submit or a short timeout (batch completions are polled)
+        if (busy) sv->cv_sched.wait_for(lk, std::chrono::microseconds(100));
+        else sv->cv_sched.wait_for(lk, std::chrono::milliseconds(50));
     }
     retire(*sv);
 }
@@ -376,10 +375,9 @@ HS_API hs_status hs_server_create(const hs_server_config* cfg, const uint8_t* co
         sv.dev_arena.reset(cfg->mem_budget_bytes);
         sv.host_arena.reset(host_bytes);
         sv.slots = std::vector<Slot>(cfg->max_inflight);
-        for (auto& sl : sv.slots) {
-            sl.server = &sv;
-            ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess;
-        }
+        for (auto& sl : sv.slots)
+            ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess;
     }
     if (!ok || !device_status_word()) {
         cudaGetLastError();
@@ -527,11 +525,13 @@ HS_API hs_status hs_server_destroy(hs_server* s) {
         sv.cv_sched.notify_all();
         sv.th.join();
     }
-    for (auto& sl : sv.slots)
+    for (auto& sl : sv.slots) {
         if (sl.stream) {
             cudaStreamSynchronize(sl.stream);
             cudaStreamDestroy(sl.stream);
         }
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
     for (int p = 0; p < 4; p++) {
         if (sv.sk_dev[p]) cudaFree(sv.sk_dev[p]);
         if (sv.kb_dev[p]) cudaFree(sv.kb_dev[p]);

@@ -67,6 +67,41 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
     ts.template finish<NW>(P::LEN * P::N, out);
 }
 
+// Merkle levels of one XMSS tree held by an aligned lane group (one leaf
+// node per lane): H(TREE) up h' levels by shuffles, the signing leaf's auth
+// nodes into the signature, root_j to scratch.
+template <class P>
+__device__ __forceinline__ void merkle_finish(const uint32_t* ms256, const uint32_t* msT, unsigned gmask,
+                                              uint32_t m, uint32_t j, uint32_t l, uint32_t sl, uint64_t tree,
+                                              uint32_t* node, uint8_t* __restrict__ sigs,
+                                              uint32_t* __restrict__ roots) {
+    constexpr int NW = P::NW, HP = P::HP;
+    uint8_t* auth = sigs + (size_t)m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES +
+                    (size_t)P::LEN * P::N;
+    if (l == (sl ^ 1u)) store_be<NW>(auth, node);
+#pragma unroll
+    for (int z = 1; z <= HP; z++) {
+        const int step = 1 << (z - 1);
+        uint32_t other[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) other[w] = __shfl_xor_sync(gmask, node[w], step);
+        if ((l & (2 * step - 1)) == 0) {
+            uint32_t lr[2 * NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) { lr[w] = node[w]; lr[NW + w] = other[w]; }
+            const uint32_t idx = l >> z;
+            hashH_ms<P>(ms256, msT, make_adrs(j, tree, T_TREE, 0, z, idx), lr, node);
+            if (z < HP && idx == ((sl >> z) ^ 1u)) store_be<NW>(auth + (size_t)z * P::N, node);
+        }
+    }
+    if (l == 0) {
+        uint32_t* rt = roots + ((size_t)m * P::D + j) * NW;
+#pragma unroll
+        for (int w = 0; w < NW; w++) rt[w] = node[w];
+    }
+}
+
+
 template <class P, int POL, int MINB>
 __global__ void __launch_bounds__(128, MINB) tree_kernel(const KeyBlock* __restrict__ keys,
                                                    const MsgInfo* __restrict__ infos, uint32_t count,
@@ -103,29 +138,94 @@ __global__ void __launch_bounds__(128, MINB) tree_kernel(const KeyBlock* __restr
     uint32_t node[NW];
     wots_leaf<P, POL>(ms256, msT, skseed, j, tree, l, node, mychk, ck, pp);
 
-    uint8_t* auth = sigs + (size_t)m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES +
-                    (size_t)P::LEN * P::N;
-    if (l == (sl ^ 1u)) store_be<NW>(auth, node);
+    merkle_finish<P>(ms256, msT, gmask, m, j, l, sl, tree, node, sigs, roots);
+}
+
+// TREE_Sign, chain-parallel form for batches too small to fill the GPU with
+// one thread per leaf: first one thread per WOTS+ chain of every leaf of
+// every layer (d 2^h' len threads per message) writes its chain end to
+// scratch [m][j][l][i], then one thread per leaf absorbs its len chain ends
+// into T_len and the lane groups merge the Merkle levels as above.  Same
+// results; ~len times more parallelism per message.
+template <class P, int POL>
+__global__ void __launch_bounds__(128) chains_kernel(const KeyBlock* __restrict__ keys,
+                                                     const MsgInfo* __restrict__ infos, uint32_t count,
+                                                     uint32_t* __restrict__ ends, uint32_t* __restrict__ chk,
+                                                     uint32_t ck, uint32_t one) {
+    constexpr int NW = P::NW, LV = P::LEAVES, LEN = P::LEN;
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t per_msg = (uint32_t)P::D * LV * LEN;
+    const uint64_t m = gid / per_msg;
+    const uint32_t r = (uint32_t)(gid % per_msg);
+    const uint32_t j = r / (LV * LEN);
+    const uint32_t l = (r / LEN) % LV;
+    const uint32_t i = r % LEN;
+    if (m >= count) return;
+    const MsgInfo& info = infos[m];
+    if (info.key == KEY_INVALID) return;
+    const KeyBlock& kb = keys[info.key];
+    uint32_t ms256[8], x[NW];
 #pragma unroll
-    for (int z = 1; z <= HP; z++) {
-        const int step = 1 << (z - 1);
-        uint32_t other[NW];
+    for (int w = 0; w < 8; w++) ms256[w] = kb.ms256[w];
 #pragma unroll
-        for (int w = 0; w < NW; w++) other[w] = __shfl_xor_sync(gmask, node[w], step);
-        if ((l & (2 * step - 1)) == 0) {
-            uint32_t lr[2 * NW];
+    for (int w = 0; w < NW; w++) x[w] = kb.sk_seed[w];
+    const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
+    const uint32_t sl = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
+    const Pipes<POL> pp(one);
+    uint32_t* mychk = nullptr;
+    const uint32_t per_chain = ck ? 16u / ck : 0u;
+    if (ck != 0 && l == sl) mychk = chk + (((size_t)m * P::D + j) * (size_t)LEN + i) * per_chain * NW;
+    ChainCtx cx;
+#pragma unroll 1
+    for (uint32_t s = 0; s < 16; s++) {
+        if (s <= 1) {
+            Adrs a = make_adrs(j, tree, s == 0 ? T_WOTS_PRF : T_WOTS_HASH, l, i, 0);
+            chain_ctx<POL>(ms256, a, cx, pp);
+        }
+        chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, x, x, pp);
+        if (mychk != nullptr && (s % ck) == 0) {
 #pragma unroll
-            for (int w = 0; w < NW; w++) { lr[w] = node[w]; lr[NW + w] = other[w]; }
-            const uint32_t idx = l >> z;
-            hashH_ms<P>(ms256, msT, make_adrs(j, tree, T_TREE, 0, z, idx), lr, node);
-            if (z < HP && idx == ((sl >> z) ^ 1u)) store_be<NW>(auth + (size_t)z * P::N, node);
+            for (int w = 0; w < NW; w++) mychk[(s / ck) * NW + w] = x[w];
         }
     }
-    if (l == 0) {
-        uint32_t* rt = roots + ((size_t)m * P::D + j) * NW;
+    uint32_t* e = ends + gid * NW;
 #pragma unroll
-        for (int w = 0; w < NW; w++) rt[w] = node[w];
-    }
+    for (int w = 0; w < NW; w++) e[w] = x[w];
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) leaves_kernel(const KeyBlock* __restrict__ keys,
+                                                     const MsgInfo* __restrict__ infos, uint32_t count,
+                                                     const uint32_t* __restrict__ ends, uint8_t* __restrict__ sigs,
+                                                     uint32_t* __restrict__ roots) {
+    constexpr int NW = P::NW, LV = P::LEAVES, LEN = P::LEN;
+    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t per_msg = (uint32_t)P::D * LV;
+    const uint32_t m = gid / per_msg;
+    const uint32_t r = gid % per_msg;
+    const uint32_t j = r / LV;
+    const uint32_t l = r % LV;
+    if (m >= count) return;                         // whole trees exit together
+    const MsgInfo& info = infos[m];
+    if (info.key == KEY_INVALID) return;
+    const unsigned gmask = ((LV == 32) ? 0xFFFFFFFFu : ((1u << LV) - 1u)) << (lane & ~(uint32_t)(LV - 1));
+    const KeyBlock& kb = keys[info.key];
+    uint32_t ms256[8], msT[P::BIG ? 16 : 8];
+#pragma unroll
+    for (int w = 0; w < 8; w++) ms256[w] = kb.ms256[w];
+#pragma unroll
+    for (int w = 0; w < (P::BIG ? 16 : 8); w++) msT[w] = P::BIG ? kb.ms512[w] : kb.ms256[w];
+    const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
+    const uint32_t sl = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
+    TStream<P::BIG> ts;
+    ts.init(msT, make_adrs(j, tree, T_WOTS_PK, l, 0, 0));
+    const uint32_t* e = ends + (size_t)gid * LEN * NW;
+#pragma unroll 1
+    for (int i = 0; i < LEN; i++) ts.template push_n<NW>(e + i * NW);
+    uint32_t node[NW];
+    ts.template finish<NW>(LEN * P::N, node);
+    merkle_finish<P>(ms256, msT, gmask, m, j, l, sl, tree, node, sigs, roots);
 }
 
 // Key generation: PK.root = root of tree 0 of the top layer d-1.  One lane

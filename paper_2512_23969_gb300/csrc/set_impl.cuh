@@ -46,6 +46,18 @@ struct SetImpl {
         tree_kernel<P, kChainPol, MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck, 1u);
         return cudaGetLastError();
     }
+    static cudaError_t tree_split(const Batch& b, cudaStream_t s) {
+        const uint32_t T = 128;
+        const uint64_t chains = (uint64_t)b.count * P::D * P::LEAVES * P::LEN;
+        chains_kernel<P, kChainPol><<<(uint32_t)((chains + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.ends,
+                                                                                  b.chk, b.ck, 1u);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const uint64_t leaves = (uint64_t)b.count * P::D * P::LEAVES;
+        leaves_kernel<P><<<(uint32_t)((leaves + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.ends, b.sigs,
+                                                                        b.roots);
+        return cudaGetLastError();
+    }
     static cudaError_t wots(const Batch& b, cudaStream_t s) {
         const uint64_t threads = (uint64_t)b.count * P::D * P::LEN;
         const uint32_t T = 256;
