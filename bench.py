@@ -257,6 +257,27 @@ def measure_other_configs(hs, inputs, args, stream, flush):
                    "unit": "signatures/s", "ms_per_step": round(sum(ms) / len(ms), 3),
                    "stage_ms": {a: round(b, 3) for a, b in prof.items()},
                    "verified": int(ok.sum().item()) == wl.count}
+    # the bench workload again with tree sharing on (same signatures, less work)
+    log("128f with tree sharing")
+    wl = inputs.config(1)
+    pk, sk = hs.hs_keygen("128f", dev(wl.seeds))
+    m, l, k = dev(wl.msgs), dev(wl.lens), dev(wl.key_idx)
+    sig = torch.empty(wl.count * hs.sig_bytes("128f"), dtype=torch.uint8, device="cuda")
+    ref = hs.hs_sign_batch("128f", sk, m, l, key_idx=k, num_keys=wl.num_keys).view(-1).clone()
+    hs.hs_set_tree_sharing(True)
+    try:
+        hs.hs_profile_enable(True)
+        ms = _time_steps(lambda: hs.hs_sign_batch("128f", sk, m, l, key_idx=k, sigs=sig, num_keys=wl.num_keys,
+                                                   stream=stream), stream, flush, steps, warmup)
+        prof = hs.hs_profile_read()
+        hs.hs_profile_enable(False)
+    finally:
+        hs.hs_set_tree_sharing(False)
+    res["128f_tree_sharing"] = {"workload": wl.name + ", repeated upper-layer trees built once per batch",
+                                "value": round(wl.count * len(ms) / (sum(ms) / 1e3), 1), "unit": "signatures/s",
+                                "ms_per_step": round(sum(ms) / len(ms), 3),
+                                "stage_ms": {a: round(b, 3) for a, b in prof.items()},
+                                "identical_to_full_work": bool(torch.equal(sig, ref))}
     # mixed-parameter batch (32768 messages 50/30/20, log-uniform 16 B - 64 KB, 64 keys)
     wls = inputs.mixed()
     jobs = []

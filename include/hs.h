@@ -270,6 +270,20 @@ hs_status hs_server_replay(hs_server *s, uint32_t count, const uint8_t *params,
                            uint32_t timeout_ms);
 hs_status hs_server_destroy(hs_server *s);
 
+/*
+ * hs_set_tree_sharing -- process-wide switch (default off) for hs_sign_batch
+ * and hs_sign_mixed.  The XMSS tree a message signs with at layer j depends
+ * only on (key, j, idx_tree >> (j h')) (paper Fig. 2), so in a batch where
+ * many messages share a key the upper layers repeat the same trees.  When
+ * on, each batch finds its distinct trees in the layers where at most half
+ * as many distinct trees as messages are possible, builds each of them once
+ * and copies every message's auth path and root from it.  Signatures are
+ * byte-identical either way; only repeated work is skipped (about 16 % of
+ * TREE_Sign for 16384 messages over 16 keys).  Extra scratch per distinct
+ * shared tree: its nodes and the checkpoints of all its leaves.
+ */
+hs_status hs_set_tree_sharing(int on);
+
 /* Size of the fixed device buffer that hs_sign_batch_noalloc works in. */
 #define HS_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 

@@ -72,6 +72,12 @@ cudaError_t launch_fors_pk(const Batch& b, cudaStream_t s) {
 cudaError_t launch_tree(const Batch& b, cudaStream_t s) {
     const SetOps* o = set_ops(b.pset);
     if (!o) return cudaErrorInvalidValue;
+    if (b.dedup_layer) {                  // shared upper layers first
+        cudaError_t e = cudaMemsetAsync(b.table, 0, sizeof(unsigned long long) << b.cap_log2, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b.nuniq, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = o->tree_dedup(b, s);
+        if (e != cudaSuccess) return e;
+    }
     return b.split ? o->tree_split(b, s) : o->tree(b, tune_get(b.pset, 1), s);
 }
 cudaError_t launch_wots(const Batch& b, cudaStream_t s) {

@@ -4,6 +4,7 @@
 // (the paper's decomposition, Sec. III and Fig. 2; FORS_Sign and TREE_Sign
 // are independent given the digest, WOTS+_Sign consumes both).
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -38,53 +39,126 @@ static hs_status cuda_fail(cudaError_t e, const char* what) {
     return fail(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-struct SetInfo { int n, d, k, len, sig, leaves; };
+struct SetInfo { int n, d, k, len, sig, leaves, hp, tree_bits; };
 static bool set_info(int p, SetInfo* s) {
+#define HS_SETINFO(P) {P::N, P::D, P::K, P::LEN, P::SIG_BYTES, P::LEAVES, P::HP, P::TREE_BITS}
     switch (p) {
-    case 0: *s = {P128f::N, P128f::D, P128f::K, P128f::LEN, P128f::SIG_BYTES, P128f::LEAVES}; return true;
-    case 1: *s = {P192f::N, P192f::D, P192f::K, P192f::LEN, P192f::SIG_BYTES, P192f::LEAVES}; return true;
-    case 2: *s = {P256f::N, P256f::D, P256f::K, P256f::LEN, P256f::SIG_BYTES, P256f::LEAVES}; return true;
-    case 3: *s = {PToy::N, PToy::D, PToy::K, PToy::LEN, PToy::SIG_BYTES, PToy::LEAVES}; return true;
+    case 0: *s = HS_SETINFO(P128f); return true;
+    case 1: *s = HS_SETINFO(P192f); return true;
+    case 2: *s = HS_SETINFO(P256f); return true;
+    case 3: *s = HS_SETINFO(PToy); return true;
     }
+#undef HS_SETINFO
     return false;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static size_t chk_bytes(const SetInfo& s, uint32_t count, uint32_t ck) {
-    return ck ? (size_t)count * s.d * s.len * (16 / ck) * (s.n / 4) * 4 : 0;
+// Tree sharing within a batch (process-wide switch, off by default).
+static bool g_share = false;
+
+void plan_dedup(Batch& b) {
+    b.dedup_layer = 0;
+    b.cap_log2 = 0;
+    b.max_uniq = 0;
+    SetInfo s;
+    if (!g_share || !set_info(b.pset, &s) || b.num_keys > (1u << 20) || b.count == 0) return;
+    // Share layers from the top down while the number of distinct trees a
+    // layer can hold (keys x 2^bits of its tree index, at most one per
+    // message) is at most half the messages, and the tree index fits the
+    // 27 bits of the table key.
+    uint32_t L = (uint32_t)s.d;
+    uint64_t total = 0;
+    for (int j = s.d - 1; j >= 1; j--) {
+        const int bits = s.tree_bits - j * s.hp > 0 ? s.tree_bits - j * s.hp : 0;
+        if (bits > 27) break;
+        const uint64_t u = std::min<uint64_t>(b.count, (uint64_t)b.num_keys << bits);
+        if (2 * u > b.count) break;
+        L = (uint32_t)j;
+        total += u;
+    }
+    if (L == (uint32_t)s.d) return;
+    const uint64_t entries = (uint64_t)b.count * (s.d - L);
+    uint32_t lg = 4;
+    while ((1ull << lg) < 2 * entries) lg++;
+    b.dedup_layer = L;
+    b.cap_log2 = lg;
+    b.max_uniq = (uint32_t)total;
 }
 
-static size_t ends_bytes(const SetInfo& s, uint32_t count, bool split) {
-    return split ? (size_t)count * s.d * s.leaves * s.len * (s.n / 4) * 4 : 0;
+// Every scratch region of a batch, in carve order (256-byte aligned each).
+static void scratch_layout(const Batch& b, const SetInfo& s, size_t sz[16], int* n) {
+    const size_t nw = (size_t)s.n / 4, cnt = b.count;
+    int i = 0;
+    sz[i++] = sizeof(uint32_t);                                      // reserved
+    sz[i++] = (size_t)b.num_keys * sizeof(KeyBlock);                 // keys
+    sz[i++] = (cnt + 1) * sizeof(uint64_t);                          // offsets
+    sz[i++] = cnt * sizeof(MsgInfo);                                 // infos
+    sz[i++] = cnt * s.k * nw * 4;                                    // fors_roots
+    sz[i++] = cnt * nw * 4;                                          // pk_fors
+    sz[i++] = cnt * s.d * nw * 4;                                    // roots
+    sz[i++] = b.ck ? cnt * s.d * s.len * (16 / b.ck) * nw * 4 : 0;   // chk
+    sz[i++] = b.split ? cnt * s.d * s.leaves * s.len * nw * 4 : 0;   // ends
+    const bool sh = b.dedup_layer != 0;
+    const size_t mj = sh ? cnt * (s.d - b.dedup_layer) : 0;
+    const size_t cap = sh ? ((size_t)1 << b.cap_log2) : 0;
+    sz[i++] = cap * sizeof(unsigned long long);                      // table
+    sz[i++] = mj * 4;                                                // mj_slot
+    sz[i++] = mj * 4;                                                // mj_id
+    sz[i++] = cap * 4;                                               // slot_id
+    sz[i++] = sh ? sizeof(uint32_t) : 0;                             // nuniq
+    sz[i++] = (size_t)b.max_uniq * sizeof(DedupDesc);                // desc
+    sz[i++] = (size_t)b.max_uniq * 2 * s.leaves * nw * 4 +           // nodes_u, then chk_u
+              (b.ck ? (size_t)b.max_uniq * s.leaves * s.len * (16 / b.ck) * nw * 4 : 0);
+    *n = i;
+}
+
+size_t scratch_bytes(const Batch& b) {
+    SetInfo s;
+    if (!set_info(b.pset, &s)) return 0;
+    size_t sz[16], t = 0;
+    int n;
+    scratch_layout(b, s, sz, &n);
+    for (int i = 0; i < n; i++) t += align256(sz[i]);
+    return t;
 }
 
 size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck, bool split) {
-    SetInfo s;
-    if (!set_info(pset, &s)) return 0;
-    const size_t nw = (size_t)s.n / 4;
-    return align256(sizeof(uint32_t)) + align256((size_t)num_keys * sizeof(KeyBlock)) +
-           align256(((size_t)count + 1) * sizeof(uint64_t)) + align256((size_t)count * sizeof(MsgInfo)) +
-           align256((size_t)count * s.k * nw * 4) + align256((size_t)count * nw * 4) +
-           align256((size_t)count * s.d * nw * 4) + align256(chk_bytes(s, count, ck)) +
-           align256(ends_bytes(s, count, split));
+    Batch b{};
+    b.pset = pset;
+    b.num_keys = num_keys;
+    b.count = count;
+    b.ck = ck;
+    b.split = split;
+    return scratch_bytes(b);
 }
 
 void carve_scratch(Batch& b, void* base) {
     SetInfo s;
     set_info(b.pset, &s);
-    const size_t nw = (size_t)s.n / 4;
+    size_t sz[16];
+    int n;
+    scratch_layout(b, s, sz, &n);
     char* p = static_cast<char*>(base);
-    p += align256(sizeof(uint32_t));   // reserved
-    b.keys = reinterpret_cast<KeyBlock*>(p);      p += align256((size_t)b.num_keys * sizeof(KeyBlock));
-    b.offsets = reinterpret_cast<uint64_t*>(p);   p += align256(((size_t)b.count + 1) * sizeof(uint64_t));
-    b.infos = reinterpret_cast<MsgInfo*>(p);      p += align256((size_t)b.count * sizeof(MsgInfo));
-    b.fors_roots = reinterpret_cast<uint32_t*>(p); p += align256((size_t)b.count * s.k * nw * 4);
-    b.pk_fors = reinterpret_cast<uint32_t*>(p);   p += align256((size_t)b.count * nw * 4);
-    b.roots = reinterpret_cast<uint32_t*>(p);     p += align256((size_t)b.count * s.d * nw * 4);
-    b.chk = b.ck ? reinterpret_cast<uint32_t*>(p) : nullptr;
-    p += align256(chk_bytes(s, b.count, b.ck));
-    b.ends = b.split ? reinterpret_cast<uint32_t*>(p) : nullptr;
+    char* r[16];
+    for (int i = 0; i < n; i++) { r[i] = p; p += align256(sz[i]); }
+    b.keys = reinterpret_cast<KeyBlock*>(r[1]);
+    b.offsets = reinterpret_cast<uint64_t*>(r[2]);
+    b.infos = reinterpret_cast<MsgInfo*>(r[3]);
+    b.fors_roots = reinterpret_cast<uint32_t*>(r[4]);
+    b.pk_fors = reinterpret_cast<uint32_t*>(r[5]);
+    b.roots = reinterpret_cast<uint32_t*>(r[6]);
+    b.chk = b.ck ? reinterpret_cast<uint32_t*>(r[7]) : nullptr;
+    b.ends = b.split ? reinterpret_cast<uint32_t*>(r[8]) : nullptr;
+    const bool sh = b.dedup_layer != 0;
+    b.table = sh ? reinterpret_cast<unsigned long long*>(r[9]) : nullptr;
+    b.mj_slot = sh ? reinterpret_cast<uint32_t*>(r[10]) : nullptr;
+    b.mj_id = sh ? reinterpret_cast<uint32_t*>(r[11]) : nullptr;
+    b.slot_id = sh ? reinterpret_cast<uint32_t*>(r[12]) : nullptr;
+    b.nuniq = sh ? reinterpret_cast<uint32_t*>(r[13]) : nullptr;
+    b.desc = sh ? reinterpret_cast<DedupDesc*>(r[14]) : nullptr;
+    b.nodes_u = sh ? reinterpret_cast<uint32_t*>(r[15]) : nullptr;
+    b.chk_u = (sh && b.ck) ? b.nodes_u + (size_t)b.max_uniq * 2 * s.leaves * (s.n / 4) : nullptr;
 }
 
 // ----------------------------------------------------------- device state
@@ -210,6 +284,11 @@ HS_API hs_status hs_tune_set(hs_params p, int knob, int32_t value) {
 }
 
 HS_API int32_t hs_tune_get(hs_params p, int knob) { return tune_get(p, knob); }
+
+HS_API hs_status hs_set_tree_sharing(int on) {
+    g_share = on != 0;
+    return HS_OK;
+}
 
 HS_API hs_status hs_set_chain_checkpoint(uint32_t stride) {
     if (stride != 0 && stride != 1 && stride != 2 && stride != 4 && stride != 8)
@@ -346,7 +425,8 @@ static hs_status run_batch(bool verify, hs_params p, const uint8_t* keys_in, uin
     b.status = d->status;
     b.ck = verify ? 0u : g_ck;
     b.split = !verify && tree_split(p, count);
-    const size_t scratch = scratch_bytes(p, num_keys, count, b.ck, b.split);
+    if (!verify) plan_dedup(b);
+    const size_t scratch = scratch_bytes(b);
     const size_t stage = (h_keys ? align256(key_bytes) : 0) + (h_idx ? align256((size_t)count * 4) : 0) +
                          (h_lens ? align256((size_t)count * 8) : 0) + (h_msgs ? align256(msg_total) : 0) +
                          (h_sig ? align256(sig_total) : 0) + (h_ok ? align256(count) : 0);

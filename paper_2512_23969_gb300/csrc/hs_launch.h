@@ -9,6 +9,13 @@
 
 namespace hs {
 
+// A distinct XMSS tree of a batch (tree sharing, kern_dedup.cuh).
+struct DedupDesc {
+    uint64_t tree;
+    uint32_t key;
+    uint32_t layer;
+};
+
 // Device buffers of one sign or verify call.  'sk' is the caller's key
 // buffer for signing (4n bytes per key) or public keys for verifying (2n).
 struct Batch {
@@ -32,6 +39,19 @@ struct Batch {
     uint32_t ck;              // checkpoint stride (1, 2, 4) or 0 = none
     bool split;               // TREE_Sign in its chain-parallel form (small batches)
     uint32_t* ends;           // chain ends of the split form: count * D * 2^h' * LEN * NW words
+    // tree sharing within the batch: layers dedup_layer .. D-1 are shared
+    // (dedup_layer == 0: off, every message builds all its layers)
+    uint32_t dedup_layer;
+    uint32_t cap_log2;        // hash table of 2^cap_log2 slots
+    uint32_t max_uniq;        // bound on the distinct trees
+    unsigned long long* table;
+    uint32_t* mj_slot;        // count * (D - L)
+    uint32_t* mj_id;          // count * (D - L)
+    uint32_t* slot_id;        // 2^cap_log2
+    uint32_t* nuniq;
+    DedupDesc* desc;          // max_uniq
+    uint32_t* nodes_u;        // max_uniq * 2 * 2^h' * NW words
+    uint32_t* chk_u;          // max_uniq * 2^h' * LEN * (16 / ck) * NW words
     uint32_t* status;         // per-device status word
 };
 
@@ -44,6 +64,11 @@ void set_last_error(const char* msg);
 uint32_t* device_status_word();
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
 uint32_t chain_checkpoint_stride();
+
+// Tree sharing plan of a batch: fills dedup_layer, cap_log2 and max_uniq
+// (dedup_layer = 0 when sharing is off or not worth it).
+void plan_dedup(Batch& b);
+size_t scratch_bytes(const Batch& b);
 
 // Scratch bytes for a batch (each region 256-byte aligned).
 size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck, bool split = false);
@@ -60,6 +85,7 @@ struct SetOps {
     cudaError_t (*fors_pk)(const Batch&, cudaStream_t);
     cudaError_t (*tree)(const Batch&, int, cudaStream_t);
     cudaError_t (*tree_split)(const Batch&, cudaStream_t);
+    cudaError_t (*tree_dedup)(const Batch&, cudaStream_t);
     cudaError_t (*wots)(const Batch&, cudaStream_t);
     cudaError_t (*verify)(const Batch&, cudaStream_t);
     cudaError_t (*keygen)(const uint8_t*, uint32_t, uint8_t*, uint8_t*, cudaStream_t);

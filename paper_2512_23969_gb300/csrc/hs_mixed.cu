@@ -131,9 +131,10 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
         b.sigs = jb.sigs;
         b.ck = chain_checkpoint_stride();
         b.split = tree_split(b.pset, b.count);
+        plan_dedup(b);
         bs.push_back(b);
         off.push_back(total);
-        total += scratch_bytes(b.pset, b.num_keys, b.count, b.ck, b.split);
+        total += scratch_bytes(b);
     }
     if (bs.empty()) return HS_OK;
     MixedDev* d = nullptr;

@@ -106,11 +106,12 @@ template <class P, int POL, int MINB>
 __global__ void __launch_bounds__(128, MINB) tree_kernel(const KeyBlock* __restrict__ keys,
                                                    const MsgInfo* __restrict__ infos, uint32_t count,
                                                    uint8_t* __restrict__ sigs, uint32_t* __restrict__ roots,
-                                                   uint32_t* __restrict__ chk, uint32_t ck, uint32_t one) {
+                                                   uint32_t* __restrict__ chk, uint32_t ck, uint32_t layers,
+                                                   uint32_t one) {
     constexpr int NW = P::NW, HP = P::HP, LV = P::LEAVES;
     const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t per_msg = (uint32_t)P::D * LV;
+    const uint32_t per_msg = layers * LV;           // layers 0 .. layers-1 of every message
     const uint32_t m = gid / per_msg;
     const uint32_t r = gid % per_msg;
     const uint32_t j = r / LV;                      // layer
@@ -151,10 +152,10 @@ template <class P, int POL>
 __global__ void __launch_bounds__(128) chains_kernel(const KeyBlock* __restrict__ keys,
                                                      const MsgInfo* __restrict__ infos, uint32_t count,
                                                      uint32_t* __restrict__ ends, uint32_t* __restrict__ chk,
-                                                     uint32_t ck, uint32_t one) {
+                                                     uint32_t ck, uint32_t layers, uint32_t one) {
     constexpr int NW = P::NW, LV = P::LEAVES, LEN = P::LEN;
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t per_msg = (uint32_t)P::D * LV * LEN;
+    const uint32_t per_msg = layers * LV * LEN;
     const uint64_t m = gid / per_msg;
     const uint32_t r = (uint32_t)(gid % per_msg);
     const uint32_t j = r / (LV * LEN);
@@ -197,11 +198,11 @@ template <class P>
 __global__ void __launch_bounds__(128) leaves_kernel(const KeyBlock* __restrict__ keys,
                                                      const MsgInfo* __restrict__ infos, uint32_t count,
                                                      const uint32_t* __restrict__ ends, uint8_t* __restrict__ sigs,
-                                                     uint32_t* __restrict__ roots) {
+                                                     uint32_t* __restrict__ roots, uint32_t layers) {
     constexpr int NW = P::NW, LV = P::LEAVES, LEN = P::LEN;
     const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t per_msg = (uint32_t)P::D * LV;
+    const uint32_t per_msg = layers * LV;
     const uint32_t m = gid / per_msg;
     const uint32_t r = gid % per_msg;
     const uint32_t j = r / LV;

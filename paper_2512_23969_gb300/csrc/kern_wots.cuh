@@ -26,7 +26,9 @@ __global__ void __launch_bounds__(256) wots_kernel(const KeyBlock* __restrict__ 
                                                    const MsgInfo* __restrict__ infos, uint32_t count,
                                                    const uint32_t* __restrict__ pk_fors,
                                                    const uint32_t* __restrict__ roots, uint8_t* __restrict__ sigs,
-                                                   const uint32_t* __restrict__ chk, uint32_t ck, uint32_t one) {
+                                                   const uint32_t* __restrict__ chk, uint32_t ck, uint32_t L,
+                                                   const uint32_t* __restrict__ mj_id,
+                                                   const uint32_t* __restrict__ chk_u, uint32_t one) {
     constexpr int NW = P::NW, LEN = P::LEN;
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t per_msg = (uint32_t)P::D * LEN;
@@ -66,7 +68,12 @@ __global__ void __launch_bounds__(256) wots_kernel(const KeyBlock* __restrict__ 
     if (ck != 0) {
         const uint32_t per_chain = 16u / ck;
         const uint32_t base = (digit / ck) * ck;
-        const uint32_t* c = chk + (((m * P::D + j) * (size_t)LEN + i) * per_chain + digit / ck) * NW;
+        // checkpoints of the message's own tree, or of the shared tree of
+        // its (key, layer, tree) when layer j is shared within the batch
+        const uint32_t* c =
+            (j >= L) ? chk_u + ((((size_t)mj_id[m * (P::D - L) + (j - L)] * P::LEAVES + kp) * LEN + i) * per_chain +
+                                digit / ck) * NW
+                     : chk + (((m * P::D + j) * (size_t)LEN + i) * per_chain + digit / ck) * NW;
 #pragma unroll
         for (int w = 0; w < NW; w++) x[w] = c[w];
         Adrs a = make_adrs(j, tree, T_WOTS_HASH, kp, i, 0);

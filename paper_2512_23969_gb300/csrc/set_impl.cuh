@@ -9,11 +9,16 @@
 #include "kern_tree.cuh"
 #include "kern_wots.cuh"
 #include "kern_verify.cuh"
+#include "kern_dedup.cuh"
 
 namespace hs {
 
 template <class P>
 struct SetImpl {
+    // layers each message builds itself: all of them unless the upper
+    // layers are shared within the batch (dedup_layer = first shared layer)
+    static uint32_t own_layers(const Batch& b) { return b.dedup_layer ? b.dedup_layer : (uint32_t)P::D; }
+
     static cudaError_t keyprep(const Batch& b, bool from_pk, cudaStream_t s) {
         const uint32_t T = 128, G = (b.num_keys + T - 1) / T;
         keyprep_kernel<P><<<G, T, 0, s>>>(b.keys_in, b.num_keys, from_pk ? 1 : 0, b.keys);
@@ -40,22 +45,46 @@ struct SetImpl {
     }
     template <int MINB>
     static cudaError_t tree(const Batch& b, cudaStream_t s) {
-        const uint64_t threads = (uint64_t)b.count * P::D * P::LEAVES;
+        const uint32_t L = own_layers(b);
+        const uint64_t threads = (uint64_t)b.count * L * P::LEAVES;
         const uint32_t T = 128;
         const uint32_t G = (uint32_t)((threads + T - 1) / T);
-        tree_kernel<P, kChainPol, MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck, 1u);
+        if (threads == 0) return cudaSuccess;
+        tree_kernel<P, kChainPol, MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck,
+                                                         L, 1u);
+        return cudaGetLastError();
+    }
+    static cudaError_t tree_dedup(const Batch& b, cudaStream_t s) {
+        const uint32_t T = 128, L = own_layers(b);
+        const uint64_t mj = (uint64_t)b.count * (P::D - L);
+        dedup_insert_kernel<P><<<(uint32_t)((mj + T - 1) / T), T, 0, s>>>(b.infos, b.count, L, b.table, b.cap_log2,
+                                                                          b.mj_slot, b.status);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const uint32_t cap = 1u << b.cap_log2;
+        dedup_compact_kernel<<<(cap + T - 1) / T, T, 0, s>>>(b.table, cap, b.slot_id, b.desc, b.nuniq, b.max_uniq,
+                                                             b.status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const uint64_t ut = (uint64_t)b.max_uniq * P::LEAVES;
+        utree_kernel<P, kChainPol><<<(uint32_t)((ut + T - 1) / T), T, 0, s>>>(b.keys, b.desc, b.nuniq, b.max_uniq,
+                                                                              b.nodes_u, b.chk_u, b.ck, 1u);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        dedup_scatter_kernel<P><<<(uint32_t)((mj + T - 1) / T), T, 0, s>>>(b.infos, b.count, L, b.mj_slot, b.slot_id,
+                                                                           b.nodes_u, b.sigs, b.roots, b.mj_id);
         return cudaGetLastError();
     }
     static cudaError_t tree_split(const Batch& b, cudaStream_t s) {
         const uint32_t T = 128;
-        const uint64_t chains = (uint64_t)b.count * P::D * P::LEAVES * P::LEN;
+        const uint32_t L = own_layers(b);
+        const uint64_t chains = (uint64_t)b.count * L * P::LEAVES * P::LEN;
+        if (chains == 0) return cudaSuccess;
         chains_kernel<P, kChainPol><<<(uint32_t)((chains + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.ends,
-                                                                                  b.chk, b.ck, 1u);
+                                                                                  b.chk, b.ck, L, 1u);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        const uint64_t leaves = (uint64_t)b.count * P::D * P::LEAVES;
+        const uint64_t leaves = (uint64_t)b.count * L * P::LEAVES;
         leaves_kernel<P><<<(uint32_t)((leaves + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.ends, b.sigs,
-                                                                        b.roots);
+                                                                        b.roots, L);
         return cudaGetLastError();
     }
     static cudaError_t wots(const Batch& b, cudaStream_t s) {
@@ -63,7 +92,7 @@ struct SetImpl {
         const uint32_t T = 256;
         const uint32_t G = (uint32_t)((threads + T - 1) / T);
         wots_kernel<P, kChainPol><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.pk_fors, b.roots, b.sigs, b.chk,
-                                                   b.ck, 1u);
+                                                   b.ck, own_layers(b), b.mj_id, b.chk_u, 1u);
         return cudaGetLastError();
     }
     static cudaError_t verify(const Batch& b, cudaStream_t s) {

@@ -65,6 +65,8 @@ def load():
     for name in ("hs_server_create", "hs_server_submit", "hs_server_wait", "hs_server_get_stats",
                  "hs_server_replay", "hs_server_destroy"):
         getattr(L, name).restype = C.c_int
+    L.hs_set_tree_sharing.argtypes = [C.c_int]
+    L.hs_set_tree_sharing.restype = C.c_int
     L.hs_set_chain_checkpoint.argtypes = [C.c_uint32]
     L.hs_set_chain_checkpoint.restype = C.c_int
     for name in ("hs_keygen", "hs_sign_batch", "hs_verify_batch", "hs_check_status"):
@@ -342,3 +344,8 @@ class Server:
 
 
 SIG_BY_ID = {0: 17088, 1: 35664, 2: 49856, 3: 1456}
+
+
+def hs_set_tree_sharing(on=True):
+    """Share repeated upper-layer XMSS trees within a batch (same bytes, less work)."""
+    _check(load().hs_set_tree_sharing(1 if on else 0))
