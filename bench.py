@@ -184,7 +184,8 @@ def run_reference(args):
     from paper_2512_23969_gb300 import inputs
     wl = inputs.config(1)
     sks = oracle_keys("128f", wl.seeds)
-    per_step = max(1.0, args.ref_step_seconds)
+    # each step is a bounded sample; the whole run stays near a minute
+    per_step = max(1.0, min(args.ref_step_seconds, 60.0 / max(1, args.steps)))
     for _ in range(args.warmup):
         oracle_rate("128f", sks, wl, 0.5)
     rates, total = [], 0
