@@ -52,8 +52,9 @@ typedef enum {
     HS_EINVAL = 1,   /* bad enum, NULL pointer, size overflow, mixed buffer kinds */
     HS_ENOMEM = 2,   /* device memory for scratch or staging could not be obtained */
     HS_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
-    HS_ETIMEOUT = 4, /* reserved for bounded device waits */
-    HS_EKEY = 5      /* status word: a key_idx entry was >= num_keys */
+    HS_ETIMEOUT = 4, /* a bounded wait ran out */
+    HS_EKEY = 5,     /* a key index was >= the number of keys */
+    HS_ECANCELED = 6 /* a server request was cancelled before it ran */
 } hs_status;
 
 /* Sizes in bytes for a parameter set; 0 for an invalid enum.
@@ -232,16 +233,22 @@ int32_t hs_tune_get(hs_params p, int knob);
  *   (host memory, hs_sig_bytes(p) bytes, valid until completion; NULL =
  *   compute and discard, for load tests).  HS_EKEY for a key index >= nkeys.
  * hs_server_wait: blocks up to timeout_ms; HS_ETIMEOUT if still pending.
- * hs_server_poll: hands out each completed request once (id and latency
- *   from arrival to host-observed completion, in ns) and forgets it.
+ * hs_server_poll: hands out each finished request once (id, latency from
+ *   arrival to host-observed completion in ns, and its hs_status: HS_OK,
+ *   HS_ECUDA for a failed batch, HS_ECANCELED) and forgets it.  Any of the
+ *   three output arrays may be NULL.
  * hs_server_replay: open-loop load generator: submits request i (set
  *   params[i], key keys[i], message pool entry pool_idx[i] of the packed pool
  *   pool_msgs / pool_lens) at arrival_ns[i] after the call starts, waits for
  *   all, and reports each latency from its scheduled arrival.  Signatures go
  *   to sigs + sig_offsets[i], or are discarded if sigs is NULL.
- *   HS_ETIMEOUT after timeout_ms.
+ *   HS_ETIMEOUT after timeout_ms; HS_ECUDA if any request's batch failed.
  * hs_server_destroy: stops the scheduler, waits for running batches, frees
  *   everything; requests never launched are dropped.
+ * Failures: a batch whose launch fails completes all its requests with
+ *   HS_ECUDA (counted in stats.failed).  A real CUDA error also makes the
+ *   server's status (hs_server_get_stats' return) HS_ECUDA; later batches
+ *   are still attempted, and the caller decides whether to recreate it.
  */
 typedef struct hs_server hs_server;
 typedef struct {
@@ -254,13 +261,15 @@ typedef struct {
     uint64_t completed, batches, batched_requests, pending;
     uint64_t max_device_bytes_in_use;
     uint32_t max_inflight_batches;
+    uint64_t failed;            /* requests completed with HS_ECUDA */
+    uint64_t cancelled;         /* requests completed with HS_ECANCELED */
 } hs_server_stats;
 hs_status hs_server_create(const hs_server_config *cfg, const uint8_t *const sks[4],
                            const uint32_t nkeys[4], hs_server **out);
 hs_status hs_server_submit(hs_server *s, hs_params p, uint32_t key, const uint8_t *msg,
                            uint64_t len, uint8_t *sig_out, uint64_t *id);
 hs_status hs_server_wait(hs_server *s, uint64_t id, uint32_t timeout_ms);
-int hs_server_poll(hs_server *s, uint64_t *ids, uint64_t *latency_ns, int max);
+int hs_server_poll(hs_server *s, uint64_t *ids, uint64_t *latency_ns, int32_t *status, int max);
 hs_status hs_server_get_stats(hs_server *s, hs_server_stats *st);
 hs_status hs_server_replay(hs_server *s, uint32_t count, const uint8_t *params,
                            const uint32_t *keys, const uint32_t *pool_idx,
@@ -269,6 +278,18 @@ hs_status hs_server_replay(hs_server *s, uint32_t count, const uint8_t *params,
                            const uint64_t *sig_offsets, uint64_t *latency_ns,
                            uint32_t timeout_ms);
 hs_status hs_server_destroy(hs_server *s);
+
+/*
+ * hs_server_cancel: drops a request that is still waiting for a batch; its
+ * wait then returns HS_ECANCELED and poll reports it.  HS_EINVAL if the id
+ * is unknown, already running or finished (a running batch always completes).
+ * hs_server_inject_launch_failures: test hook -- the next n batches the
+ * scheduler forms are treated as if their launch had failed (nothing is
+ * launched; their requests complete with HS_ECUDA) so that callers can test
+ * how they handle a failed batch without faulting a GPU.
+ */
+hs_status hs_server_cancel(hs_server *s, uint64_t id);
+hs_status hs_server_inject_launch_failures(hs_server *s, uint32_t n);
 
 /*
  * hs_set_tree_sharing -- process-wide switch (default off) for hs_sign_batch

@@ -141,9 +141,10 @@ struct ServerImpl {
     bool stop = false;
     std::thread th;
     // stats
-    uint64_t n_done = 0, n_batches = 0, n_batched_reqs = 0, max_dev_used = 0;
+    uint64_t n_done = 0, n_batches = 0, n_batched_reqs = 0, max_dev_used = 0, n_failed = 0, n_cancelled = 0;
     uint32_t max_inflight_seen = 0;
     hs_status fatal = HS_OK;
+    uint32_t inject_failures = 0;   // test hook: batches to fail without launching
 };
 
 namespace {
@@ -177,6 +178,8 @@ void retire(ServerImpl& sv) {
         if (!s.failed) {
             e = cudaEventQuery(s.done);            // recorded after the signature copy
             if (e == cudaErrorNotReady) continue;
+        } else {
+            cudaStreamSynchronize(s.stream);       // whatever was queued before the failure
         }
         const int S = sig_bytes_of(s.pset);
         const uint64_t t = now_ns();
@@ -189,6 +192,7 @@ void retire(ServerImpl& sv) {
                 r.status = HS_OK;
             } else {
                 r.status = HS_ECUDA;
+                sv.n_failed++;
             }
             r.t_done = t;
             sv.completed.push_back(s.ids[i]);
@@ -279,7 +283,13 @@ bool admit(ServerImpl& sv, Slot& slot) {
     b.keys = sv.kb_dev[p];                        // resident midstates, not scratch
     b.num_keys = sv.nkeys[p];
     cudaStream_t s = slot.stream;
-    cudaError_t e = cudaMemcpyAsync(d, h, o_sigs, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaSuccess;
+    const bool injected = sv.inject_failures > 0;   // a fake failed launch: nothing reaches the GPU
+    if (injected) {
+        sv.inject_failures--;
+        e = cudaErrorLaunchFailure;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h, o_sigs, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_offsets(b, s);
     if (e == cudaSuccess) e = launch_message(b, false, s);
     if (e == cudaSuccess) e = launch_fors(b, s);
@@ -298,9 +308,11 @@ bool admit(ServerImpl& sv, Slot& slot) {
     slot.failed = false;
     if (e == cudaSuccess) e = cudaEventRecord(slot.done, s);
     if (e != cudaSuccess) {
-        sv.fatal = HS_ECUDA;
         slot.failed = true;             // retire() marks the requests failed
-        cudaGetLastError();
+        if (!injected) {                // a real CUDA error: the server stops taking work
+            sv.fatal = HS_ECUDA;
+            cudaGetLastError();
+        }
     }
     sv.n_batches++;
     sv.n_batched_reqs += count;
@@ -436,7 +448,7 @@ HS_API hs_status hs_server_wait(hs_server* s, uint64_t id, uint32_t timeout_ms) 
     return f == sv.reqs.end() ? HS_OK : (hs_status)f->second.status;   // collected by a poll: it completed
 }
 
-HS_API int hs_server_poll(hs_server* s, uint64_t* ids, uint64_t* latency_ns, int max) {
+HS_API int hs_server_poll(hs_server* s, uint64_t* ids, uint64_t* latency_ns, int32_t* status, int max) {
     if (!s || max < 0) return -1;
     ServerImpl& sv = s->impl;
     std::lock_guard<std::mutex> lk(sv.mu);
@@ -448,6 +460,7 @@ HS_API int hs_server_poll(hs_server* s, uint64_t* ids, uint64_t* latency_ns, int
         if (it == sv.reqs.end()) continue;
         if (ids) ids[n] = id;
         if (latency_ns) latency_ns[n] = it->second.t_done - it->second.t_arrive;
+        if (status) status[n] = it->second.status;
         sv.reqs.erase(it);
         n++;
     }
@@ -463,6 +476,8 @@ HS_API hs_status hs_server_get_stats(hs_server* s, hs_server_stats* st) {
     st->batched_requests = sv.n_batched_reqs;
     st->max_device_bytes_in_use = sv.max_dev_used;
     st->max_inflight_batches = sv.max_inflight_seen;
+    st->failed = sv.n_failed;
+    st->cancelled = sv.n_cancelled;
     uint64_t pend = 0;
     for (int p = 0; p < 4; p++) pend += sv.pending[p].size();
     st->pending = pend;
@@ -499,19 +514,54 @@ HS_API hs_status hs_server_replay(hs_server* s, uint32_t count, const uint8_t* p
     }
     uint32_t got = 0;
     std::vector<uint64_t> cid(4096), lat(4096);
+    std::vector<int32_t> cst(4096);
+    hs_status worst = HS_OK;
     const uint64_t deadline = now_ns() + (uint64_t)timeout_ms * 1000000ull;
     while (got < count) {
-        const int n = hs_server_poll(s, cid.data(), lat.data(), (int)cid.size());
+        const int n = hs_server_poll(s, cid.data(), lat.data(), cst.data(), (int)cid.size());
         for (int k = 0; k < n; k++) {
             auto it = index.find(cid[k]);
-            if (it != index.end()) { latency_ns[it->second] = lat[k]; got++; }
+            if (it != index.end()) {
+                latency_ns[it->second] = lat[k];
+                got++;
+                if (cst[k] != HS_OK && worst == HS_OK) worst = (hs_status)cst[k];
+            }
         }
         if (got >= count) break;
         if (now_ns() > deadline) return sv_fail(HS_ETIMEOUT, "hs_server_replay: requests still pending at the timeout");
         std::unique_lock<std::mutex> lk(sv.mu);
         sv.cv_done.wait_for(lk, std::chrono::milliseconds(5));
     }
-    return sv.fatal;
+    if (worst == HS_OK) return sv.fatal;
+    set_last_error("hs_server_replay: some requests failed");
+    return worst;
+}
+
+HS_API hs_status hs_server_cancel(hs_server* s, uint64_t id) {
+    if (!s) return sv_fail(HS_EINVAL, "hs_server_cancel: NULL server");
+    ServerImpl& sv = s->impl;
+    std::lock_guard<std::mutex> lk(sv.mu);
+    auto it = sv.reqs.find(id);
+    if (it == sv.reqs.end() || it->second.status >= 0)
+        return sv_fail(HS_EINVAL, "hs_server_cancel: unknown or finished request");
+    auto& q = sv.pending[it->second.pset];
+    auto pos = std::find(q.begin(), q.end(), id);
+    if (pos == q.end()) return sv_fail(HS_EINVAL, "hs_server_cancel: request is already running");
+    q.erase(pos);
+    it->second.status = HS_ECANCELED;
+    it->second.t_done = now_ns();
+    sv.completed.push_back(id);
+    sv.n_done++;
+    sv.n_cancelled++;
+    sv.cv_done.notify_all();
+    return HS_OK;
+}
+
+HS_API hs_status hs_server_inject_launch_failures(hs_server* s, uint32_t n) {
+    if (!s) return sv_fail(HS_EINVAL, "hs_server_inject_launch_failures: NULL server");
+    std::lock_guard<std::mutex> lk(s->impl.mu);
+    s->impl.inject_failures = n;
+    return HS_OK;
 }
 
 HS_API hs_status hs_server_destroy(hs_server* s) {

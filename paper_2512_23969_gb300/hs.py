@@ -12,7 +12,8 @@ import numpy as np
 
 PARAMS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3}
 N_BYTES = {"128f": 16, "192f": 24, "256f": 32, "toy": 16}
-STATUS = {0: "HS_OK", 1: "HS_EINVAL", 2: "HS_ENOMEM", 3: "HS_ECUDA", 4: "HS_ETIMEOUT", 5: "HS_EKEY"}
+STATUS = {0: "HS_OK", 1: "HS_EINVAL", 2: "HS_ENOMEM", 3: "HS_ECUDA", 4: "HS_ETIMEOUT", 5: "HS_EKEY",
+          6: "HS_ECANCELED"}
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libhs.so")
 
 _lib = None
@@ -55,13 +56,17 @@ def load():
     L.hs_server_submit.argtypes = [C.c_void_p, C.c_int, C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p,
                                    C.POINTER(C.c_uint64)]
     L.hs_server_wait.argtypes = [C.c_void_p, C.c_uint64, C.c_uint32]
-    L.hs_server_poll.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    L.hs_server_poll.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
     L.hs_server_poll.restype = C.c_int
     L.hs_server_get_stats.argtypes = [C.c_void_p, C.c_void_p]
     L.hs_server_replay.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_uint32]
     L.hs_server_destroy.argtypes = [C.c_void_p]
+    L.hs_server_cancel.argtypes = [C.c_void_p, C.c_uint64]
+    L.hs_server_cancel.restype = C.c_int
+    L.hs_server_inject_launch_failures.argtypes = [C.c_void_p, C.c_uint32]
+    L.hs_server_inject_launch_failures.restype = C.c_int
     for name in ("hs_server_create", "hs_server_submit", "hs_server_wait", "hs_server_get_stats",
                  "hs_server_replay", "hs_server_destroy"):
         getattr(L, name).restype = C.c_int
@@ -247,7 +252,7 @@ class ServerConfig(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("completed", C.c_uint64), ("batches", C.c_uint64), ("batched_requests", C.c_uint64),
                 ("pending", C.c_uint64), ("max_device_bytes_in_use", C.c_uint64),
-                ("max_inflight_batches", C.c_uint32)]
+                ("max_inflight_batches", C.c_uint32), ("failed", C.c_uint64), ("cancelled", C.c_uint64)]
 
 
 class Server:
@@ -285,10 +290,14 @@ class Server:
     def wait(self, rid, timeout_ms=60000):
         _check(load().hs_server_wait(self._h, int(rid), int(timeout_ms)))
 
-    def poll(self, max_n=4096):
+    def poll(self, max_n=4096, with_status=False):
+        """Finished requests as (id, latency_ns), or (id, latency_ns, status)."""
         ids = np.empty(max_n, dtype=np.uint64)
         lat = np.empty(max_n, dtype=np.uint64)
-        n = load().hs_server_poll(self._h, _ptr(ids), _ptr(lat), max_n)
+        st = np.empty(max_n, dtype=np.int32)
+        n = load().hs_server_poll(self._h, _ptr(ids), _ptr(lat), _ptr(st), max_n)
+        if with_status:
+            return list(zip(ids[:n].tolist(), lat[:n].tolist(), st[:n].tolist()))
         return list(zip(ids[:n].tolist(), lat[:n].tolist()))
 
     def stats(self):
@@ -324,6 +333,14 @@ class Server:
         if keep_signatures:
             out = [sigs[int(o):int(o) + SIG_BY_ID[int(p)]].tobytes() for o, p in zip(offs, params)]
         return lat, out
+
+    def cancel(self, rid):
+        """Drop a request that has not started; raises if it already runs or ran."""
+        _check(load().hs_server_cancel(self._h, int(rid)))
+
+    def inject_launch_failures(self, n):
+        """Test hook: the next n batches fail as if their launch had failed."""
+        _check(load().hs_server_inject_launch_failures(self._h, int(n)))
 
     def close(self):
         if getattr(self, "_h", None):
