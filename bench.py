@@ -279,6 +279,25 @@ def measure_other_configs(hs, inputs, args, stream, flush):
                                 "ms_per_step": round(sum(ms) / len(ms), 3),
                                 "stage_ms": {a: round(b, 3) for a, b in prof.items()},
                                 "identical_to_full_work": bool(torch.equal(sig, ref))}
+    # the bench workload signed from a keyset with the top 4 layers of each key prebuilt
+    log("128f from a keyset with cached top layers")
+    sig.zero_()
+    t0 = time.perf_counter()
+    ks = hs.KeySet("128f", sk, cache_layers=4, stream=stream)
+    build_s = time.perf_counter() - t0
+    try:
+        hs.hs_profile_enable(True)
+        ms = _time_steps(lambda: ks.sign(m, l, key_idx=k, sigs=sig, stream=stream), stream, flush, steps, warmup)
+        prof = hs.hs_profile_read()
+        hs.hs_profile_enable(False)
+        res["128f_keyset_cache4"] = {
+            "workload": wl.name + ", keys resident with layers 18-21 of every key prebuilt (585 trees per key)",
+            "value": round(wl.count * len(ms) / (sum(ms) / 1e3), 1), "unit": "signatures/s",
+            "ms_per_step": round(sum(ms) / len(ms), 3), "stage_ms": {a: round(b, 3) for a, b in prof.items()},
+            "cache_build_s": round(build_s, 3), "keyset_bytes": ks.nbytes,
+            "identical_to_full_work": bool(torch.equal(sig, ref))}
+    finally:
+        ks.close()
     # mixed-parameter batch (32768 messages 50/30/20, log-uniform 16 B - 64 KB, 64 keys)
     wls = inputs.mixed()
     jobs = []
@@ -367,6 +386,27 @@ def measure_serving(hs, inputs, seconds, rhos, burst=60000):
         out["mean_batch"] = round(st["batched_requests"] / max(1, st["batches"]), 1)
         out["max_inflight_batches"] = st["max_inflight_batches"]
         out["max_device_bytes_in_use"] = st["max_device_bytes_in_use"]
+    # the same keys as keysets with their top 2 layers prebuilt: the same
+    # saturating burst and the load of the uncached peak rate
+    with hs.Server(keys, max_inflight=inflight, max_batch=max_batch, mem_budget=budget, cache_layers=2) as srv:
+        cached = {"cache_layers": 2}
+        for name, rate in (("burst", None), ("rho_1.00_of_uncached_peak", peak)):
+            if rate is None:
+                tr = inputs.serving_trace(rate=1e6, seconds=burst / 1e6, seed=inputs.BASE_SEED + 40)
+                tr["arrival_ns"][:] = 0
+            else:
+                tr = inputs.serving_trace(rate=rate, seconds=seconds, seed=inputs.BASE_SEED + 141)
+            n = len(tr["params"])
+            log("serving with cached top layers: %s, %d requests" % (name, n))
+            t0 = time.perf_counter()
+            lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
+                                tr["arrival_ns"], timeout_ms=int(seconds * 1000) + 120000)
+            wall = time.perf_counter() - t0
+            finish = (tr["arrival_ns"].astype(np.float64) + lat.astype(np.float64)).max() / 1e9
+            cached[name] = {"requests": n, "value": round(n / (wall if rate is None else finish), 1),
+                            "unit": "signatures/s", "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
+                            "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3)}
+        out["cached_top_layers"] = cached
     return out
 
 

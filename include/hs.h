@@ -245,6 +245,9 @@ int32_t hs_tune_get(hs_params p, int knob);
  *   HS_ETIMEOUT after timeout_ms; HS_ECUDA if any request's batch failed.
  * hs_server_destroy: stops the scheduler, waits for running batches, frees
  *   everything; requests never launched are dropped.
+ * With cache_layers > 0 each served set keeps its keys as a keyset with
+ *   that many top layers prebuilt (capped at d - 1; see hs_keyset_create
+ *   for the device memory it takes, outside mem_budget_bytes).
  * Failures: a batch whose launch fails completes all its requests with
  *   HS_ECUDA (counted in stats.failed).  A real CUDA error also makes the
  *   server's status (hs_server_get_stats' return) HS_ECUDA; later batches
@@ -256,6 +259,7 @@ typedef struct {
     uint32_t max_batch;         /* requests per batch */
     uint64_t mem_budget_bytes;  /* device arena for in-flight work (>= 1 MiB) */
     uint64_t pinned_bytes;      /* pinned host staging arena (0 = budget / 2) */
+    uint32_t cache_layers;      /* top hypertree layers prebuilt per key (hs_keyset; 0 = none) */
 } hs_server_config;
 typedef struct {
     uint64_t completed, batches, batched_requests, pending;
@@ -304,6 +308,37 @@ hs_status hs_server_inject_launch_failures(hs_server *s, uint32_t n);
  * shared tree: its nodes and the checkpoints of all its leaves.
  */
 hs_status hs_set_tree_sharing(int on);
+
+/*
+ * Keysets: signing keys kept resident on the device with the top hypertree
+ * layers prebuilt.  For a key, the tree of layer j a message signs with is
+ * fixed by idx_tree >> (j h') (paper Fig. 2), which takes 2^((d-1-j) h')
+ * values; a keyset builds all of them once for its top cache_layers layers
+ * (j = d - cache_layers .. d-1), with every Merkle node and the WOTS+ chain
+ * checkpoints of every leaf, so each later signature builds only its lower
+ * d - cache_layers layers and copies the rest.  Signatures are
+ * byte-identical to hs_sign_batch's with the same keys.
+ *
+ * hs_keyset_create: sk = num_keys keys (4n bytes each, host or device; the
+ *   keyset keeps its own copy); cache_layers in 0..d-1 (0 = resident keys
+ *   only), at most 2^24 trees per key and 2^32 in all.  The chain
+ *   checkpoint stride in force (hs_set_chain_checkpoint) is fixed into the
+ *   keyset.  Enqueued on 'stream' and waited for before returning; the
+ *   keyset belongs to the current device.  HS_ENOMEM if it does not fit.
+ *   Cached trees per key: sum over u < cache_layers of 2^(u h'); device
+ *   bytes per tree: 2^h' (2 n + len n 16 / stride) (about 36 KB at 128f,
+ *   stride 2) -- hs_keyset_bytes gives the total.
+ * hs_sign_keyset: as hs_sign_batch with the keyset's keys (key_idx indexes
+ *   them; NULL = key 0); call it on the keyset's device.
+ * hs_keyset_destroy: frees it (waits for the device); NULL is a no-op.
+ */
+typedef struct hs_keyset hs_keyset;
+hs_status hs_keyset_create(hs_params p, const uint8_t *sk, uint32_t num_keys, uint32_t cache_layers,
+                           void *stream, hs_keyset **out);
+size_t hs_keyset_bytes(const hs_keyset *ks);
+hs_status hs_sign_keyset(const hs_keyset *ks, const uint32_t *key_idx, const uint8_t *msgs,
+                         const uint64_t *lens, uint32_t count, uint8_t *sigs, void *stream);
+hs_status hs_keyset_destroy(hs_keyset *ks);
 
 /* Size of the fixed device buffer that hs_sign_batch_noalloc works in. */
 #define HS_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)

@@ -72,7 +72,10 @@ cudaError_t launch_fors_pk(const Batch& b, cudaStream_t s) {
 cudaError_t launch_tree(const Batch& b, cudaStream_t s) {
     const SetOps* o = set_ops(b.pset);
     if (!o) return cudaErrorInvalidValue;
-    if (b.dedup_layer) {                  // shared upper layers first
+    if (b.cached) {                       // prebuilt upper layers of a keyset
+        cudaError_t e = o->tree_cached(b, s);
+        if (e != cudaSuccess) return e;
+    } else if (b.dedup_layer) {           // shared upper layers first
         cudaError_t e = cudaMemsetAsync(b.table, 0, sizeof(unsigned long long) << b.cap_log2, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(b.nuniq, 0, sizeof(uint32_t), s);
         if (e == cudaSuccess) e = o->tree_dedup(b, s);

@@ -99,17 +99,18 @@ static void scratch_layout(const Batch& b, const SetInfo& s, size_t sz[16], int*
     sz[i++] = cnt * s.d * nw * 4;                                    // roots
     sz[i++] = b.ck ? cnt * s.d * s.len * (16 / b.ck) * nw * 4 : 0;   // chk
     sz[i++] = b.split ? cnt * s.d * s.leaves * s.len * nw * 4 : 0;   // ends
-    const bool sh = b.dedup_layer != 0;
-    const size_t mj = sh ? cnt * (s.d - b.dedup_layer) : 0;
+    const bool sh = b.dedup_layer != 0 && !b.cached;                 // in-batch sharing
+    const size_t mj = b.dedup_layer ? cnt * (s.d - b.dedup_layer) : 0;
     const size_t cap = sh ? ((size_t)1 << b.cap_log2) : 0;
     sz[i++] = cap * sizeof(unsigned long long);                      // table
-    sz[i++] = mj * 4;                                                // mj_slot
+    sz[i++] = sh ? mj * 4 : 0;                                       // mj_slot
     sz[i++] = mj * 4;                                                // mj_id
     sz[i++] = cap * 4;                                               // slot_id
     sz[i++] = sh ? sizeof(uint32_t) : 0;                             // nuniq
-    sz[i++] = (size_t)b.max_uniq * sizeof(DedupDesc);                // desc
-    sz[i++] = (size_t)b.max_uniq * 2 * s.leaves * nw * 4 +           // nodes_u, then chk_u
-              (b.ck ? (size_t)b.max_uniq * s.leaves * s.len * (16 / b.ck) * nw * 4 : 0);
+    const size_t mu = sh ? b.max_uniq : 0;
+    sz[i++] = mu * sizeof(DedupDesc);                                // desc
+    sz[i++] = mu * 2 * s.leaves * nw * 4 +                           // nodes_u, then chk_u
+              (b.ck ? mu * s.leaves * s.len * (16 / b.ck) * nw * 4 : 0);
     *n = i;
 }
 
@@ -123,13 +124,15 @@ size_t scratch_bytes(const Batch& b) {
     return t;
 }
 
-size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck, bool split) {
+size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck, bool split, uint32_t cached_from) {
     Batch b{};
     b.pset = pset;
     b.num_keys = num_keys;
     b.count = count;
     b.ck = ck;
     b.split = split;
+    b.dedup_layer = cached_from;
+    b.cached = cached_from != 0;
     return scratch_bytes(b);
 }
 
@@ -150,13 +153,14 @@ void carve_scratch(Batch& b, void* base) {
     b.roots = reinterpret_cast<uint32_t*>(r[6]);
     b.chk = b.ck ? reinterpret_cast<uint32_t*>(r[7]) : nullptr;
     b.ends = b.split ? reinterpret_cast<uint32_t*>(r[8]) : nullptr;
-    const bool sh = b.dedup_layer != 0;
+    const bool sh = b.dedup_layer != 0 && !b.cached;
     b.table = sh ? reinterpret_cast<unsigned long long*>(r[9]) : nullptr;
     b.mj_slot = sh ? reinterpret_cast<uint32_t*>(r[10]) : nullptr;
-    b.mj_id = sh ? reinterpret_cast<uint32_t*>(r[11]) : nullptr;
+    b.mj_id = b.dedup_layer ? reinterpret_cast<uint32_t*>(r[11]) : nullptr;
     b.slot_id = sh ? reinterpret_cast<uint32_t*>(r[12]) : nullptr;
     b.nuniq = sh ? reinterpret_cast<uint32_t*>(r[13]) : nullptr;
     b.desc = sh ? reinterpret_cast<DedupDesc*>(r[14]) : nullptr;
+    if (b.cached) return;             // nodes_u / chk_u belong to the keyset
     b.nodes_u = sh ? reinterpret_cast<uint32_t*>(r[15]) : nullptr;
     b.chk_u = (sh && b.ck) ? b.nodes_u + (size_t)b.max_uniq * 2 * s.leaves * (s.n / 4) : nullptr;
 }
@@ -378,8 +382,10 @@ HS_API hs_status hs_keygen(hs_params p, const uint8_t* seeds, uint32_t count, ui
     return HS_OK;
 }
 
-// Shared driver for sign (verify = false) and verify (verify = true).
-static hs_status run_batch(bool verify, hs_params p, const uint8_t* keys_in, uint32_t num_keys,
+// Shared driver for sign (verify = false) and verify (verify = true); ks =
+// a keyset whose resident keys (and cached top layers) replace keys_in.
+static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const uint8_t* keys_in,
+                           uint32_t num_keys,
                            const uint32_t* key_idx, const uint8_t* msgs, const uint64_t* lens,
                            const uint8_t* sigs_in, uint8_t* sigs_out, uint32_t count, uint8_t* ok, void* stream) {
     SetInfo si;
@@ -423,10 +429,18 @@ static hs_status run_batch(bool verify, hs_params p, const uint8_t* keys_in, uin
     b.num_keys = num_keys;
     b.count = count;
     b.status = d->status;
-    b.ck = verify ? 0u : g_ck;
+    b.ck = verify ? 0u : (ks ? ks->ck : g_ck);
     b.split = !verify && tree_split(p, count);
-    if (!verify) plan_dedup(b);
+    if (ks && ks->layers) {
+        b.dedup_layer = ks->first_layer;
+        b.cached = true;
+        b.cache_tpk = ks->tpk;
+    } else if (!verify) {
+        plan_dedup(b);
+    }
+    if (ks) b.num_keys = 0;                       // no key blocks in scratch: they are resident
     const size_t scratch = scratch_bytes(b);
+    b.num_keys = num_keys;
     const size_t stage = (h_keys ? align256(key_bytes) : 0) + (h_idx ? align256((size_t)count * 4) : 0) +
                          (h_lens ? align256((size_t)count * 8) : 0) + (h_msgs ? align256(msg_total) : 0) +
                          (h_sig ? align256(sig_total) : 0) + (h_ok ? align256(count) : 0);
@@ -434,6 +448,11 @@ static hs_status run_batch(bool verify, hs_params p, const uint8_t* keys_in, uin
     e = cudaMallocFromPoolAsync(&base, scratch + stage, d->pool, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(scratch)");
     carve_scratch(b, base);
+    if (ks) {
+        b.keys = ks->kb;
+        b.nodes_u = ks->nodes;
+        b.chk_u = ks->chk;
+    }
     Staging sg;
     sg.base = static_cast<char*>(base) + scratch;
 
@@ -464,7 +483,7 @@ static hs_status run_batch(bool verify, hs_params p, const uint8_t* keys_in, uin
 
     const bool prof = g_prof && !verify;
     if (prof) prof_mark(0, s);
-    e = launch_keyprep(b, verify, s);
+    e = ks ? cudaSuccess : launch_keyprep(b, verify, s);
     if (prof) prof_mark(1, s);
     if (e == cudaSuccess) e = launch_offsets(b, s);
     if (prof) prof_mark(2, s);
@@ -507,11 +526,111 @@ static hs_status run_batch(bool verify, hs_params p, const uint8_t* keys_in, uin
 HS_API hs_status hs_sign_batch(hs_params p, const uint8_t* sk, uint32_t num_keys, const uint32_t* key_idx,
                                const uint8_t* msgs, const uint64_t* lens, uint32_t count, uint8_t* sigs,
                                void* stream) {
-    return run_batch(false, p, sk, num_keys, key_idx, msgs, lens, nullptr, sigs, count, nullptr, stream);
+    return run_batch(nullptr, false, p, sk, num_keys, key_idx, msgs, lens, nullptr, sigs, count, nullptr, stream);
 }
 
 HS_API hs_status hs_verify_batch(hs_params p, const uint8_t* pk, uint32_t num_keys, const uint32_t* key_idx,
                                  const uint8_t* msgs, const uint64_t* lens, const uint8_t* sigs, uint32_t count,
                                  uint8_t* ok, void* stream) {
-    return run_batch(true, p, pk, num_keys, key_idx, msgs, lens, sigs, nullptr, count, ok, stream);
+    return run_batch(nullptr, true, p, pk, num_keys, key_idx, msgs, lens, sigs, nullptr, count, ok, stream);
+}
+
+// ----------------------------------------------------------- keysets
+static void keyset_free(hs_keyset* ks) {
+    if (!ks) return;
+    cudaFree(ks->sk);
+    cudaFree(ks->kb);
+    cudaFree(ks->nodes);
+    cudaFree(ks->chk);
+    delete ks;
+}
+
+HS_API hs_status hs_keyset_create(hs_params p, const uint8_t* sk, uint32_t num_keys, uint32_t cache_layers,
+                                  void* stream, hs_keyset** out) {
+    SetInfo si;
+    if (!set_info(p, &si)) return fail(HS_EINVAL, "invalid parameter set %d", (int)p);
+    if (!sk || !out || num_keys == 0) return fail(HS_EINVAL, "hs_keyset_create: NULL buffer or no keys");
+    if (cache_layers > (uint32_t)si.d - 1)
+        return fail(HS_EINVAL, "cache_layers %u: at most d - 1 = %d", cache_layers, si.d - 1);
+    if (cache_layers && (uint64_t)(cache_layers - 1) * si.hp > 24)
+        return fail(HS_EINVAL, "cache_layers %u: more than 2^24 trees per key", cache_layers);
+    uint64_t tpk = 0;
+    for (uint32_t u = 0; u < cache_layers; u++) tpk += 1ull << (u * si.hp);
+    const uint64_t trees = tpk * num_keys;
+    if (trees >= (1ull << 32)) return fail(HS_EINVAL, "hs_keyset_create: more than 2^32 cached trees");
+    DevState* d;
+    hs_status st = dev_state(&d);
+    if (st != HS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    hs_keyset* ks = new hs_keyset();
+    cudaGetDevice(&ks->device);
+    ks->pset = p;
+    ks->num_keys = num_keys;
+    ks->layers = cache_layers;
+    ks->first_layer = (uint32_t)si.d - cache_layers;
+    ks->tpk = (uint32_t)tpk;
+    ks->ck = g_ck;
+    const size_t nw = (size_t)si.n / 4, sk_bytes = (size_t)num_keys * 4 * si.n;
+    const size_t node_bytes = (size_t)trees * 2 * si.leaves * nw * 4;
+    const size_t chk_bytes = ks->ck ? (size_t)trees * si.leaves * si.len * (16 / ks->ck) * nw * 4 : 0;
+    ks->bytes = sk_bytes + (size_t)num_keys * sizeof(KeyBlock) + node_bytes + chk_bytes;
+    cudaError_t e = cudaMalloc(&ks->sk, sk_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ks->kb, (size_t)num_keys * sizeof(KeyBlock));
+    if (e == cudaSuccess && node_bytes) e = cudaMalloc(&ks->nodes, node_bytes);
+    if (e == cudaSuccess && chk_bytes) e = cudaMalloc(&ks->chk, chk_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        keyset_free(ks);
+        return cuda_fail(e, "hs_keyset_create: cudaMalloc");
+    }
+    e = cudaMemcpyAsync(ks->sk, sk, sk_bytes, cudaMemcpyDefault, s);
+    Batch b;
+    memset(&b, 0, sizeof(b));
+    b.pset = p;
+    b.keys_in = ks->sk;
+    b.num_keys = num_keys;
+    b.keys = ks->kb;
+    if (e == cudaSuccess) e = launch_keyprep(b, false, s);
+    void* desc = nullptr;
+    if (e == cudaSuccess && trees) {
+        e = cudaMallocFromPoolAsync(&desc, (size_t)trees * sizeof(DedupDesc), d->pool, s);
+        if (e == cudaSuccess)
+            e = set_ops(p)->cache_build(ks->kb, num_keys, ks->first_layer, ks->tpk, static_cast<DedupDesc*>(desc),
+                                        ks->nodes, ks->chk, ks->ck, s);
+        if (desc) {
+            const cudaError_t f = cudaFreeAsync(desc, s);
+            if (e == cudaSuccess) e = f;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(s);
+        keyset_free(ks);
+        return cuda_fail(e, "hs_keyset_create: build");
+    }
+    *out = ks;
+    return HS_OK;
+}
+
+HS_API size_t hs_keyset_bytes(const hs_keyset* ks) { return ks ? ks->bytes : 0; }
+
+HS_API hs_status hs_sign_keyset(const hs_keyset* ks, const uint32_t* key_idx, const uint8_t* msgs,
+                                const uint64_t* lens, uint32_t count, uint8_t* sigs, void* stream) {
+    if (!ks) return fail(HS_EINVAL, "hs_sign_keyset: NULL keyset");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != ks->device) return fail(HS_EINVAL, "hs_sign_keyset: keyset of device %d used on %d", ks->device, dev);
+    return run_batch(ks, false, (hs_params)ks->pset, ks->sk, ks->num_keys, key_idx, msgs, lens, nullptr, sigs, count,
+                     nullptr, stream);
+}
+
+HS_API hs_status hs_keyset_destroy(hs_keyset* ks) {
+    if (!ks) return HS_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ks->device);
+    keyset_free(ks);
+    cudaSetDevice(prev);
+    return HS_OK;
 }

@@ -52,6 +52,10 @@ struct Batch {
     DedupDesc* desc;          // max_uniq
     uint32_t* nodes_u;        // max_uniq * 2 * 2^h' * NW words
     uint32_t* chk_u;          // max_uniq * 2^h' * LEN * (16 / ck) * NW words
+    // keyset cache: layers dedup_layer .. D-1 come prebuilt from nodes_u /
+    // chk_u (owned by the keyset), tree ids computed directly (no table)
+    bool cached;
+    uint32_t cache_tpk;       // cached trees per key
     uint32_t* status;         // per-device status word
 };
 
@@ -71,7 +75,9 @@ void plan_dedup(Batch& b);
 size_t scratch_bytes(const Batch& b);
 
 // Scratch bytes for a batch (each region 256-byte aligned).
-size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck, bool split = false);
+// cached_from: first layer taken from a keyset's cache (0 = none).
+size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck, bool split = false,
+                     uint32_t cached_from = 0);
 void carve_scratch(Batch& b, void* base);
 
 // Per-parameter-set kernel launchers (one table per set_<name>.cu).  The
@@ -86,6 +92,9 @@ struct SetOps {
     cudaError_t (*tree)(const Batch&, int, cudaStream_t);
     cudaError_t (*tree_split)(const Batch&, cudaStream_t);
     cudaError_t (*tree_dedup)(const Batch&, cudaStream_t);
+    cudaError_t (*tree_cached)(const Batch&, cudaStream_t);
+    cudaError_t (*cache_build)(const KeyBlock*, uint32_t, uint32_t, uint32_t, DedupDesc*, uint32_t*, uint32_t*,
+                               uint32_t, cudaStream_t);
     cudaError_t (*wots)(const Batch&, cudaStream_t);
     cudaError_t (*verify)(const Batch&, cudaStream_t);
     cudaError_t (*keygen)(const uint8_t*, uint32_t, uint8_t*, uint8_t*, cudaStream_t);
@@ -117,3 +126,20 @@ cudaError_t launch_keygen(int pset, const uint8_t* seeds, uint32_t count, uint8_
                           cudaStream_t s);
 
 }  // namespace hs
+
+// A keyset (include/hs.h): resident keys and the prebuilt trees of their top
+// layers, shared by hs_sign_keyset and the server.
+struct hs_keyset {
+    int pset = 0;
+    int device = 0;
+    uint32_t num_keys = 0;
+    uint32_t layers = 0;        // cached top layers
+    uint32_t first_layer = 0;   // d - layers
+    uint32_t tpk = 0;           // cached trees per key
+    uint32_t ck = 0;            // chain checkpoint stride of the cache
+    uint8_t* sk = nullptr;      // num_keys * 4n bytes
+    hs::KeyBlock* kb = nullptr; // num_keys
+    uint32_t* nodes = nullptr;  // trees * 2 * 2^h' * NW words, heap order per tree
+    uint32_t* chk = nullptr;    // trees * 2^h' * len * (16 / ck) * NW words (ck != 0)
+    size_t bytes = 0;
+};

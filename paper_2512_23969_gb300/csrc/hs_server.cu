@@ -123,8 +123,7 @@ struct ServerImpl {
     hs_server_config cfg;
     int device = 0;
     // per set: resident keys and midstates
-    uint8_t* sk_dev[4] = {nullptr, nullptr, nullptr, nullptr};
-    KeyBlock* kb_dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    hs_keyset* ks[4] = {nullptr, nullptr, nullptr, nullptr};   // with the cached top layers
     uint32_t nkeys[4] = {0, 0, 0, 0};
     // arenas
     uint8_t* dev_base = nullptr;
@@ -162,11 +161,12 @@ int n_of(int p) { return p == 1 ? 24 : (p == 2 ? 32 : 16); }
 
 // Bytes a batch needs from each arena.
 struct Need { size_t dev, host; };
-Need batch_need(int pset, size_t count, size_t msg_bytes, uint32_t ck) {
+Need batch_need(int pset, size_t count, size_t msg_bytes, const hs_keyset* ks) {
     const size_t sig = (size_t)count * sig_bytes_of(pset);
     Need n;
     n.host = al256(msg_bytes) + al256(count * 8) + al256(count * 4) + al256(sig);
-    n.dev = n.host + al256(scratch_bytes(pset, 0, (uint32_t)count, ck, tree_split(pset, (uint32_t)count)));
+    n.dev = n.host + al256(scratch_bytes(pset, 0, (uint32_t)count, ks->ck, tree_split(pset, (uint32_t)count),
+                                         ks->layers ? ks->first_layer : 0));
     return n;
 }
 
@@ -220,7 +220,7 @@ bool admit(ServerImpl& sv, Slot& slot) {
         }
     if (best < 0) return false;
     const int p = best;
-    const uint32_t ck = chain_checkpoint_stride();
+    const hs_keyset* ks = sv.ks[p];
     // take requests while the cumulative need fits what the arenas could give
     size_t count = 0, msg_bytes = 0;
     const size_t limit = std::min<size_t>(sv.cfg.max_batch, sv.pending[p].size());
@@ -228,13 +228,13 @@ bool admit(ServerImpl& sv, Slot& slot) {
     const size_t host_free = sv.host_arena.cap() - sv.host_arena.used();
     while (count < limit) {
         const Request& r = sv.reqs[sv.pending[p][count]];
-        const Need n = batch_need(p, count + 1, msg_bytes + r.msg.size(), ck);
+        const Need n = batch_need(p, count + 1, msg_bytes + r.msg.size(), ks);
         if (n.dev > dev_free || n.host > host_free) break;
         msg_bytes += r.msg.size();
         count++;
     }
     if (count == 0) return false;
-    Need need = batch_need(p, count, msg_bytes, ck);
+    Need need = batch_need(p, count, msg_bytes, ks);
     size_t doff = sv.dev_arena.alloc(need.dev);
     size_t hoff = doff == SIZE_MAX ? SIZE_MAX : sv.host_arena.alloc(need.host);
     while ((doff == SIZE_MAX || hoff == SIZE_MAX) && count > 1) {   // fragmentation: shrink
@@ -242,7 +242,7 @@ bool admit(ServerImpl& sv, Slot& slot) {
         count = (count + 1) / 2;
         msg_bytes = 0;
         for (size_t i = 0; i < count; i++) msg_bytes += sv.reqs[sv.pending[p][i]].msg.size();
-        need = batch_need(p, count, msg_bytes, ck);
+        need = batch_need(p, count, msg_bytes, ks);
         doff = sv.dev_arena.alloc(need.dev);
         hoff = doff == SIZE_MAX ? SIZE_MAX : sv.host_arena.alloc(need.host);
     }
@@ -269,19 +269,26 @@ bool admit(ServerImpl& sv, Slot& slot) {
     }
     Batch b{};
     b.pset = p;
-    b.keys_in = sv.sk_dev[p];
+    b.keys_in = ks->sk;
     b.num_keys = 0;                               // scratch holds no key blocks (see below)
     b.key_idx = reinterpret_cast<const uint32_t*>(d + o_kidx);
     b.msgs = msg_bytes ? d : d + o_lens;          // never read when all lengths are 0
     b.lens = reinterpret_cast<const uint64_t*>(d + o_lens);
     b.count = (uint32_t)count;
     b.sigs = d + o_sigs;
-    b.ck = ck;
+    b.ck = ks->ck;
+    if (ks->layers) {                             // top layers from the keyset's cache
+        b.dedup_layer = ks->first_layer;
+        b.cached = true;
+        b.cache_tpk = ks->tpk;
+    }
     b.split = tree_split(p, (uint32_t)count);
     b.status = device_status_word();
     carve_scratch(b, d + o_scr);
-    b.keys = sv.kb_dev[p];                        // resident midstates, not scratch
-    b.num_keys = sv.nkeys[p];
+    b.keys = ks->kb;                              // resident midstates, not scratch
+    b.num_keys = ks->num_keys;
+    b.nodes_u = ks->nodes;
+    b.chk_u = ks->chk;
     cudaStream_t s = slot.stream;
     cudaError_t e = cudaSuccess;
     const bool injected = sv.inject_failures > 0;   // a fake failed launch: nothing reaches the GPU
@@ -367,18 +374,9 @@ HS_API hs_status hs_server_create(const hs_server_config* cfg, const uint8_t* co
         sv.nkeys[p] = nkeys[p];
         if (!nkeys[p]) continue;
         if (!sks[p]) { ok = false; break; }
-        const size_t kb = (size_t)nkeys[p] * 4 * n_of(p);
-        ok = cudaMalloc(&sv.sk_dev[p], kb) == cudaSuccess &&
-             cudaMalloc(&sv.kb_dev[p], (size_t)nkeys[p] * sizeof(KeyBlock)) == cudaSuccess &&
-             cudaMemcpy(sv.sk_dev[p], sks[p], kb, cudaMemcpyDefault) == cudaSuccess;
-        if (ok) {
-            Batch b{};
-            b.pset = p;
-            b.keys_in = sv.sk_dev[p];
-            b.num_keys = nkeys[p];
-            b.keys = sv.kb_dev[p];
-            ok = launch_keyprep(b, false, 0) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
-        }
+        const uint32_t d = p == 2 ? 17u : (p == 3 ? 2u : 22u);
+        const uint32_t layers = std::min<uint32_t>(cfg->cache_layers, d - 1);
+        ok = hs_keyset_create((hs_params)p, sks[p], nkeys[p], layers, nullptr, &sv.ks[p]) == HS_OK;
     }
     const size_t host_bytes = cfg->pinned_bytes ? cfg->pinned_bytes : cfg->mem_budget_bytes / 2;
     ok = ok && cudaMalloc(&sv.dev_base, cfg->mem_budget_bytes) == cudaSuccess &&
@@ -413,7 +411,7 @@ static hs_status submit_at(hs_server* s, hs_params p, uint32_t key, const uint8_
     r.msg.assign(msg, msg + len);
     r.out = sig_out;
     r.t_arrive = t_arrive;
-    const Need one = batch_need(p, 1, len, chain_checkpoint_stride());
+    const Need one = batch_need(p, 1, len, sv.ks[p]);
     if (one.dev > sv.dev_arena.cap() || one.host > sv.host_arena.cap())
         return sv_fail(HS_EINVAL, "hs_server_submit: request larger than the memory budget");
     uint64_t rid;
@@ -582,10 +580,7 @@ HS_API hs_status hs_server_destroy(hs_server* s) {
         }
         if (sl.done) cudaEventDestroy(sl.done);
     }
-    for (int p = 0; p < 4; p++) {
-        if (sv.sk_dev[p]) cudaFree(sv.sk_dev[p]);
-        if (sv.kb_dev[p]) cudaFree(sv.kb_dev[p]);
-    }
+    for (int p = 0; p < 4; p++) hs_keyset_destroy(sv.ks[p]);
     if (sv.dev_base) cudaFree(sv.dev_base);
     if (sv.host_base) cudaFreeHost(sv.host_base);
     delete s;

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128) utree_kernel(const KeyBlock* __restrict__
     const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t id = gid / LV, l = gid % LV;
-    if (id >= max_uniq || id >= *nuniq) return;          // whole trees exit together
+    if (id >= max_uniq || (nuniq && id >= *nuniq)) return;   // whole trees exit together
     const unsigned gmask = ((LV == 32) ? 0xFFFFFFFFu : ((1u << LV) - 1u)) << (lane & ~(uint32_t)(LV - 1));
     const DedupDesc d = desc[id];
     const KeyBlock& kb = keys[d.key];
@@ -143,6 +143,65 @@ __global__ void dedup_scatter_kernel(const MsgInfo* __restrict__ infos, uint32_t
     mj_id[gid] = id;
     const uint32_t sl = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
     const uint32_t* tn = nodes + (size_t)id * 2 * LV * NW;
+    uint8_t* auth = sigs + (size_t)m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES +
+                    (size_t)P::LEN * P::N;
+#pragma unroll
+    for (int z = 0; z < HP; z++) store_be<NW>(auth + (size_t)z * P::N, tn + ((LV >> z) + ((sl >> z) ^ 1u)) * NW);
+    uint32_t* rt = roots + ((size_t)m * P::D + j) * NW;
+#pragma unroll
+    for (int w = 0; w < NW; w++) rt[w] = tn[1 * NW + w];
+}
+
+// ---------------------------------------------------------------- key cache
+// A keyset keeps, per key, every tree of its top layers L..D-1 built once:
+// layer j holds 2^((D-1-j) h') trees (the possible values of
+// idx_tree >> (j h')).  Trees of one key are stored top layer first, so the
+// tree t of layer j has id  key * tpk + cache_off(j) + t.
+
+// Trees of the layers above j: sum over u < D-1-j of 2^(u h').
+template <class P>
+__host__ __device__ __forceinline__ uint64_t cache_off(uint32_t j) {
+    uint64_t off = 0;
+    for (uint32_t u = 0; u + 1 + j < (uint32_t)P::D; u++) off += 1ull << (u * P::HP);
+    return off;
+}
+
+// One thread per cached tree: its (key, layer, tree) description.
+template <class P>
+__global__ void cache_desc_kernel(uint32_t num_keys, uint32_t L, uint32_t tpk, DedupDesc* __restrict__ desc) {
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (uint64_t)num_keys * tpk) return;
+    const uint32_t key = (uint32_t)(gid / tpk);
+    uint64_t r = gid % tpk;
+    uint32_t j = (uint32_t)P::D - 1;
+    while (j > L && r >= (1ull << ((P::D - 1 - j) * P::HP))) {
+        r -= 1ull << ((P::D - 1 - j) * P::HP);
+        j--;
+    }
+    DedupDesc d;
+    d.tree = r;
+    d.layer = j;
+    d.key = key;
+    desc[gid] = d;
+}
+
+// One thread per (message, cached layer): auth path and root from the cache.
+template <class P>
+__global__ void cache_scatter_kernel(const MsgInfo* __restrict__ infos, uint32_t count, uint32_t L, uint32_t tpk,
+                                     const uint32_t* __restrict__ nodes, uint8_t* __restrict__ sigs,
+                                     uint32_t* __restrict__ roots, uint32_t* __restrict__ mj_id) {
+    constexpr int NW = P::NW, HP = P::HP, LV = P::LEAVES;
+    const uint32_t per_msg = (uint32_t)P::D - L;
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (uint64_t)count * per_msg) return;
+    const uint32_t m = (uint32_t)(gid / per_msg);
+    const uint32_t j = L + (uint32_t)(gid % per_msg);
+    const MsgInfo& info = infos[m];
+    if (info.key == KEY_INVALID) { mj_id[gid] = kNoSlot; return; }
+    const uint64_t id = (uint64_t)info.key * tpk + cache_off<P>(j) + layer_tree<P>(info.idx_tree, (int)j);
+    mj_id[gid] = (uint32_t)id;
+    const uint32_t sl = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
+    const uint32_t* tn = nodes + id * 2 * LV * NW;
     uint8_t* auth = sigs + (size_t)m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES +
                     (size_t)P::LEN * P::N;
 #pragma unroll

@@ -28,7 +28,8 @@ cudaError_t tree_variant(const Batch& b, int minb, cudaStream_t s) {
 
 extern const SetOps kOps_256F = {
     SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk, tree_variant,
-    SetImpl<P>::tree_split, SetImpl<P>::tree_dedup, SetImpl<P>::wots,    SetImpl<P>::verify,  SetImpl<P>::keygen,
+    SetImpl<P>::tree_split, SetImpl<P>::tree_dedup, SetImpl<P>::tree_cached, SetImpl<P>::cache_build,
+    SetImpl<P>::wots,       SetImpl<P>::verify,     SetImpl<P>::keygen,
     kForsLpt, 3, 4, kTreeMinb, 2, 0};
 
 }  // namespace hs

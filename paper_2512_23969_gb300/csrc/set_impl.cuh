@@ -73,6 +73,29 @@ struct SetImpl {
                                                                            b.nodes_u, b.sigs, b.roots, b.mj_id);
         return cudaGetLastError();
     }
+    // Cached top layers (keyset): auth paths, roots and tree ids from the cache.
+    static cudaError_t tree_cached(const Batch& b, cudaStream_t s) {
+        const uint32_t T = 128, L = own_layers(b);
+        const uint64_t mj = (uint64_t)b.count * (P::D - L);
+        if (mj == 0) return cudaSuccess;
+        cache_scatter_kernel<P><<<(uint32_t)((mj + T - 1) / T), T, 0, s>>>(b.infos, b.count, L, b.cache_tpk,
+                                                                           b.nodes_u, b.sigs, b.roots, b.mj_id);
+        return cudaGetLastError();
+    }
+    // Build every tree of layers L..D-1 of num_keys resident keys.
+    static cudaError_t cache_build(const KeyBlock* keys, uint32_t num_keys, uint32_t L, uint32_t tpk,
+                                   DedupDesc* desc, uint32_t* nodes, uint32_t* chk, uint32_t ck, cudaStream_t s) {
+        const uint32_t T = 128;
+        const uint64_t trees = (uint64_t)num_keys * tpk;
+        if (trees == 0) return cudaSuccess;
+        cache_desc_kernel<P><<<(uint32_t)((trees + T - 1) / T), T, 0, s>>>(num_keys, L, tpk, desc);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const uint64_t th = trees * P::LEAVES;
+        utree_kernel<P, kChainPol><<<(uint32_t)((th + T - 1) / T), T, 0, s>>>(keys, desc, nullptr, (uint32_t)trees,
+                                                                              nodes, chk, ck, 1u);
+        return cudaGetLastError();
+    }
     static cudaError_t tree_split(const Batch& b, cudaStream_t s) {
         const uint32_t T = 128;
         const uint32_t L = own_layers(b);

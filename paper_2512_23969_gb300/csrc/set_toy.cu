@@ -26,7 +26,8 @@ cudaError_t tree_variant(const Batch& b, int minb, cudaStream_t s) {
 
 extern const SetOps kOps_Toy = {
     SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk, tree_variant,
-    SetImpl<P>::tree_split, SetImpl<P>::tree_dedup, SetImpl<P>::wots,    SetImpl<P>::verify,  SetImpl<P>::keygen,
+    SetImpl<P>::tree_split, SetImpl<P>::tree_dedup, SetImpl<P>::tree_cached, SetImpl<P>::cache_build,
+    SetImpl<P>::wots,       SetImpl<P>::verify,     SetImpl<P>::keygen,
     kForsLpt, 2, 4, kTreeMinb, 1, 0};
 
 }  // namespace hs

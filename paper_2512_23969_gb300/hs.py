@@ -63,6 +63,14 @@ def load():
                                    C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_uint32]
     L.hs_server_destroy.argtypes = [C.c_void_p]
+    L.hs_keyset_create.argtypes = [C.c_int, vp, u32, u32, vp, C.POINTER(C.c_void_p)]
+    L.hs_keyset_create.restype = C.c_int
+    L.hs_keyset_bytes.argtypes = [vp]
+    L.hs_keyset_bytes.restype = C.c_size_t
+    L.hs_sign_keyset.argtypes = [vp, vp, vp, u64p, u32, vp, vp]
+    L.hs_sign_keyset.restype = C.c_int
+    L.hs_keyset_destroy.argtypes = [vp]
+    L.hs_keyset_destroy.restype = C.c_int
     L.hs_server_cancel.argtypes = [C.c_void_p, C.c_uint64]
     L.hs_server_cancel.restype = C.c_int
     L.hs_server_inject_launch_failures.argtypes = [C.c_void_p, C.c_uint32]
@@ -151,6 +159,53 @@ def hs_sign_batch(params, sk, msgs, lens, key_idx=None, sigs=None, num_keys=None
     _check(load().hs_sign_batch(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), _ptr(msgs), _ptr(lens),
                                 count, _ptr(sigs), _stream(stream)))
     return sigs.reshape(count, S)
+
+
+class KeySet:
+    """Resident signing keys with their top ``cache_layers`` hypertree layers
+    prebuilt (hs_keyset_* of include/hs.h); ``sign`` gives the same bytes as
+    hs_sign_batch with these keys."""
+
+    def __init__(self, params, sk, cache_layers=0, stream=None):
+        L = load()
+        n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+        self.params = params
+        self.num_keys = int(sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
+        h = C.c_void_p()
+        _check(L.hs_keyset_create(_pid(params), _ptr(sk), self.num_keys, int(cache_layers), _stream(stream),
+                                  C.byref(h)))
+        self._h = h
+        self.cache_layers = int(cache_layers)
+
+    @property
+    def nbytes(self):
+        return int(load().hs_keyset_bytes(self._h))
+
+    def sign(self, msgs, lens, key_idx=None, sigs=None, stream=None):
+        count = int(lens.shape[0])
+        S = sig_bytes(self.params)
+        sigs = _like(lens, count * S, np.uint8, "uint8") if sigs is None else sigs
+        msgs = _nonempty(msgs, lens)
+        _check(load().hs_sign_keyset(self._h, _ptr(key_idx), _ptr(msgs), _ptr(lens), count, _ptr(sigs),
+                                     _stream(stream)))
+        return sigs.reshape(count, S)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hs_keyset_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hs_verify_batch(params, pk, msgs, lens, sigs, key_idx=None, ok=None, num_keys=None, stream=None):
@@ -246,7 +301,7 @@ def hs_sign_mixed(jobs, use_graph=True, stream=None):
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_inflight", C.c_uint32), ("max_batch", C.c_uint32), ("mem_budget_bytes", C.c_uint64),
-                ("pinned_bytes", C.c_uint64)]
+                ("pinned_bytes", C.c_uint64), ("cache_layers", C.c_uint32)]
 
 
 class ServerStats(C.Structure):
@@ -261,7 +316,7 @@ class Server:
     ``keys``: {params: sk array/tensor [num_keys, 4n]} for the sets it serves.
     """
 
-    def __init__(self, keys, max_inflight=4, max_batch=1024, mem_budget=8 << 30, pinned=0):
+    def __init__(self, keys, max_inflight=4, max_batch=1024, mem_budget=8 << 30, pinned=0, cache_layers=0):
         L = load()
         self._keepalive = []
         sks = (C.c_void_p * 4)()
@@ -271,7 +326,7 @@ class Server:
             self._keepalive.append(sk)
             sks[pid] = _ptr(sk)
             nk[pid] = int(sk.shape[0])
-        cfg = ServerConfig(int(max_inflight), int(max_batch), int(mem_budget), int(pinned))
+        cfg = ServerConfig(int(max_inflight), int(max_batch), int(mem_budget), int(pinned), int(cache_layers))
         h = C.c_void_p()
         _check(L.hs_server_create(C.byref(cfg), sks, nk, C.byref(h)))
         self._h = h
