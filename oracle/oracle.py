@@ -9,7 +9,9 @@ from dataclasses import dataclass
 
 from . import build as _build
 
-PARAM_IDS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3}
+PARAM_IDS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3,
+             # the same sets in FIPS 205 mode (MSB-first FORS indices)
+             "slh-128f": 16, "slh-192f": 17, "slh-256f": 18, "slh-toy": 19}
 
 _lib = None
 
@@ -59,13 +61,17 @@ def lib():
         L.oracle_sign_fields.argtypes = [C.c_int, C.c_char_p, C.c_char_p, C.POINTER(C.c_uint32),
                                          C.c_uint64, C.c_uint32, C.c_char_p]
         L.oracle_verify.argtypes = [C.c_int, C.c_char_p, C.c_char_p, C.c_size_t, C.c_char_p]
+        L.oracle_slh_sign.argtypes = [C.c_int, C.c_char_p, C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t,
+                                      C.c_char_p]
+        L.oracle_slh_verify.argtypes = [C.c_int, C.c_char_p, C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t,
+                                        C.c_char_p]
         L.oracle_counters.argtypes = [C.POINTER(C.c_uint64), C.c_int]
         for name in ("oracle_params", "oracle_thash", "oracle_wots_digits", "oracle_hash_message",
                      "oracle_split_digest", "oracle_wots_chain", "oracle_wots_sk", "oracle_wots_pkgen",
                      "oracle_wots_sign", "oracle_wots_pk_from_sig", "oracle_xmss_node",
                      "oracle_xmss_root_from_sig", "oracle_fors_node", "oracle_fors_sk",
                      "oracle_fors_pk_from_sig", "oracle_keygen", "oracle_sign", "oracle_sign_fields",
-                     "oracle_verify"):
+                     "oracle_verify", "oracle_slh_sign", "oracle_slh_verify"):
             getattr(L, name).restype = C.c_int
         for name in ("oracle_sha256", "oracle_sha512", "oracle_hmac", "oracle_mgf1",
                      "oracle_sha_tables", "oracle_adrs_compress", "oracle_counters"):
@@ -308,6 +314,19 @@ def sign_fields(ps, sk, R, fidx, idx_tree, idx_leaf) -> bytes:
 
 def verify(ps, pk: bytes, m: bytes, sig: bytes) -> bool:
     return _check(lib().oracle_verify(_pid(ps), pk, m, len(m), sig)) == 1
+
+
+def slh_sign(ps, sk: bytes, ctx: bytes, m: bytes) -> bytes:
+    """FIPS 205 pure SLH-DSA signature (deterministic) of m under context ctx;
+    ps is the base set ("128f", ...)."""
+    P = params(ps)
+    sig = C.create_string_buffer(P.sig_bytes)
+    _check(lib().oracle_slh_sign(_pid(ps), sk, ctx, len(ctx), m, len(m), sig))
+    return sig.raw
+
+
+def slh_verify(ps, pk: bytes, ctx: bytes, m: bytes, sig: bytes) -> bool:
+    return _check(lib().oracle_slh_verify(_pid(ps), pk, ctx, len(ctx), m, len(m), sig)) == 1
 
 
 def counters(reset=False):

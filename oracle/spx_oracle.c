@@ -24,6 +24,12 @@
  * fully assembled input (no midstates), recursive Merkle node() with no
  * caching, and separately written verify climbs.  Nothing here is tuned.
  *
+ * FIPS 205 mode (parameter id + 16): SLH-DSA's two departures from the
+ * round-3.1 scheme, stated in FIPS 205 -- the FORS indices are the base-2^a
+ * digits of md read most significant bit first (its base_2b), and the pure
+ * signing interface signs M' = 0x00 || len(ctx) || ctx || M (oracle_slh_*).
+ * Keys, hashes, addresses and sizes are the same at these three sets.
+ *
  * Parity status: every exported function is pinned by tests/test_oracle_*.py
  * (hashlib/hmac for SHA-2, hand-derived byte layouts and digits, closed-form
  * sizes and call counts from the paper, sign/verify/tamper invariants and a
@@ -53,14 +59,18 @@ typedef struct {
     int len1, len2, len;
     int md_bytes, tree_bytes, leaf_bytes, m;
     int tree_bits, leaf_bits;
+    int fips;   /* 1: FORS indices in FIPS 205 order (MSB first)        */
     size_t fors_bytes, sig_bytes;
 } spx_params;
 
-/* ids: 0 = 128f, 1 = 192f, 2 = 256f, 3 = toy (n=16,h=4,d=2,h'=2,a=3,k=4) */
+/* ids: 0 = 128f, 1 = 192f, 2 = 256f, 3 = toy (n=16,h=4,d=2,h'=2,a=3,k=4);
+ * + 16 = the same set in FIPS 205 mode */
 static int params_init(int id, spx_params *p)
 {
     memset(p, 0, sizeof(*p));
-    switch (id) {
+    if (id < 0 || id > 31) return -1;
+    p->fips = id >> 4;
+    switch (id & 15) {
     case 0: p->n = 16; p->h = 66; p->d = 22; p->a = 6; p->k = 33; break;
     case 1: p->n = 24; p->h = 66; p->d = 22; p->a = 8; p->k = 33; break;
     case 2: p->n = 32; p->h = 68; p->d = 17; p->a = 9; p->k = 35; break;
@@ -420,6 +430,21 @@ static void hash_msg(const spx_ctx *c, const uint8_t *R, const uint8_t *m, size_
 static void message_to_indices(const spx_params *p, const uint8_t *md, uint32_t *idx)
 {
     int i, j, q = 0;
+    if (p->fips) {
+        /* FIPS 205 base_2b(md, a, k): bytes enter an accumulator from the
+         * left; each digit is the top a bits not yet used. */
+        uint64_t acc = 0;
+        int have = 0, in = 0;
+        for (i = 0; i < p->k; i++) {
+            while (have < p->a) {
+                acc = (acc << 8) | md[in++];
+                have += 8;
+            }
+            have -= p->a;
+            idx[i] = (uint32_t)((acc >> have) & (((uint64_t)1 << p->a) - 1));
+        }
+        return;
+    }
     for (i = 0; i < p->k; i++) {
         idx[i] = 0;
         for (j = 0; j < p->a; j++, q++)
@@ -1030,6 +1055,48 @@ SPX_EXPORT int oracle_verify(int pid, const uint8_t *pk, const uint8_t *m, size_
         tree >>= c.p.hp;
     }
     return memcmp(root, c.pk_root, n) == 0 ? 1 : 0;
+}
+
+/* FIPS 205 pure SLH-DSA (deterministic): sign / verify M' = 0x00 ||
+ * len(ctx) || ctx || M with the FIPS 205 index order; ctxlen <= 255. */
+static uint8_t *slh_wrap(const uint8_t *ctx, size_t ctxlen, const uint8_t *m, size_t mlen, size_t *outlen)
+{
+    uint8_t *w = (uint8_t *)malloc(2 + ctxlen + mlen + 1);
+    if (!w) return NULL;
+    w[0] = 0;
+    w[1] = (uint8_t)ctxlen;
+    if (ctxlen) memcpy(w + 2, ctx, ctxlen);
+    if (mlen) memcpy(w + 2 + ctxlen, m, mlen);
+    *outlen = 2 + ctxlen + mlen;
+    return w;
+}
+
+SPX_EXPORT int oracle_slh_sign(int pid, const uint8_t *sk, const uint8_t *ctx, size_t ctxlen,
+                               const uint8_t *m, size_t mlen, uint8_t *sig)
+{
+    size_t wl;
+    uint8_t *w;
+    int rc;
+    if (pid < 0 || pid > 15 || ctxlen > 255) return -1;
+    w = slh_wrap(ctx, ctxlen, m, mlen, &wl);
+    if (!w) return -1;
+    rc = oracle_sign(pid + 16, sk, w, wl, sig);
+    free(w);
+    return rc;
+}
+
+SPX_EXPORT int oracle_slh_verify(int pid, const uint8_t *pk, const uint8_t *ctx, size_t ctxlen,
+                                 const uint8_t *m, size_t mlen, const uint8_t *sig)
+{
+    size_t wl;
+    uint8_t *w;
+    int rc;
+    if (pid < 0 || pid > 15 || ctxlen > 255) return -1;
+    w = slh_wrap(ctx, ctxlen, m, mlen, &wl);
+    if (!w) return -1;
+    rc = oracle_verify(pid + 16, pk, w, wl, sig);
+    free(w);
+    return rc;
 }
 
 /* Counters: [0] SHA-256 blocks, [1] SHA-512 blocks, [2] F, [3] PRF, [4] H, [5] T. */

@@ -60,6 +60,12 @@ MUTANTS = [
     ("chain hash index off by one", "adrs_set_hash(A, (uint32_t)q);", "adrs_set_hash(A, (uint32_t)q + 1);", False),
     ("FORS PRF height 1", "adrs_set_height(&A, 0);\n    adrs_set_index(&A, g);\n    prf_addr(c, &A, out);", "adrs_set_height(&A, 1);\n    adrs_set_index(&A, g);\n    prf_addr(c, &A, out);", False),
     ("WOTS pk keypair dropped", "adrs_set_type(&A, ADDR_WOTS_PK);\n    adrs_set_keypair(&A, kp);", "adrs_set_type(&A, ADDR_WOTS_PK);", False),
+    ("FIPS base_2b bytes enter from the right", "acc = (acc << 8) | md[in++];",
+     "acc |= (uint64_t)md[in] << (8 * in); in++;", False),
+    ("FIPS digit from the low bits", "idx[i] = (uint32_t)((acc >> have) & (((uint64_t)1 << p->a) - 1));",
+     "idx[i] = (uint32_t)(acc & (((uint64_t)1 << p->a) - 1)); acc >>= p->a;", False),
+    ("FIPS prefix domain byte", "w[0] = 0;", "w[0] = 1;", False),
+    ("FIPS context length byte dropped", "w[1] = (uint8_t)ctxlen;", "w[1] = 0;", False),
 ]
 
 
@@ -143,6 +149,18 @@ def _pins_fail(O):
             s = O.sign("toy", skt, m)
             if s != toy.sign(m) or not O.verify("toy", pk, m, s):
                 return "toy sign/verify"
+        from test_oracle_fips205 import base_2b, fields
+        for ps in ("slh-toy", "slh-128f"):
+            P = O.params(ps)
+            for t in range(6):
+                dg = bytes(rng.getrandbits(8) for _ in range(P.m))
+                if O.split_digest(ps, dg)[0] != base_2b(dg[:P.md_bytes], P.a, P.k):
+                    return "FIPS base_2b"
+        P = O.params("toy")
+        for ctx in (b"", b"c1"):
+            mp = b"\x00" + bytes([len(ctx)]) + ctx + b"m"
+            if O.slh_sign("toy", skt, ctx, b"m") != toy.sign_fields(*fields(P, skt, mp)):
+                return "FIPS pure sign"
         pk1, sk1 = O.keygen("128f", bytes(range(48)))
         s = O.sign("128f", sk1, b"x")
         if not O.verify("128f", pk1, b"x", s):
