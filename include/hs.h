@@ -310,6 +310,29 @@ hs_status hs_server_inject_launch_failures(hs_server *s, uint32_t n);
 hs_status hs_set_tree_sharing(int on);
 
 /*
+ * FIPS 205 (SLH-DSA) mode -- a variant; the paper signs with SPHINCS+
+ * round 3.1.  At the SHA2 128f/192f/256f sets FIPS 205 keeps the keys,
+ * tweakable hashes, addresses and sizes and changes two things: the FORS
+ * indices are the base-2^a digits of md read most significant bit first
+ * (base_2b), and pure signing signs M' = 0x00 || len(ctx) || ctx || M.
+ * hs_slh_sign_batch / hs_slh_verify_batch are SLH-DSA.Sign (deterministic:
+ * opt_rand = PK.seed) and SLH-DSA.Verify for a batch, with one context
+ * string ctx (host memory, ctx_len <= 255) for the whole call; ctx_len =
+ * HS_SLH_INTERNAL signs / verifies the messages as given (FIPS 205's
+ * internal functions).  Keys come from hs_keygen.  Other arguments, layouts
+ * and errors as hs_sign_batch / hs_verify_batch; HS_EINVAL for ctx_len 256
+ * .. 0xFFFFFFFE.
+ */
+#define HS_SLH_INTERNAL 0xFFFFFFFFu
+hs_status hs_slh_sign_batch(hs_params p, const uint8_t *sk, uint32_t num_keys, const uint32_t *key_idx,
+                            const uint8_t *ctx, uint32_t ctx_len, const uint8_t *msgs,
+                            const uint64_t *lens, uint32_t count, uint8_t *sigs, void *stream);
+hs_status hs_slh_verify_batch(hs_params p, const uint8_t *pk, uint32_t num_keys,
+                              const uint32_t *key_idx, const uint8_t *ctx, uint32_t ctx_len,
+                              const uint8_t *msgs, const uint64_t *lens, const uint8_t *sigs,
+                              uint32_t count, uint8_t *ok, void *stream);
+
+/*
  * Keysets: signing keys kept resident on the device with the top hypertree
  * layers prebuilt.  For a key, the tree of layer j a message signs with is
  * fixed by idx_tree >> (j h') (paper Fig. 2), which takes 2^((d-1-j) h')

@@ -384,10 +384,12 @@ HS_API hs_status hs_keygen(hs_params p, const uint8_t* seeds, uint32_t count, ui
 
 // Shared driver for sign (verify = false) and verify (verify = true); ks =
 // a keyset whose resident keys (and cached top layers) replace keys_in.
+// fips: FIPS 205 index order, and prefix (host, plen <= 257 bytes) hashed
+// before every message.
 static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const uint8_t* keys_in,
-                           uint32_t num_keys,
-                           const uint32_t* key_idx, const uint8_t* msgs, const uint64_t* lens,
-                           const uint8_t* sigs_in, uint8_t* sigs_out, uint32_t count, uint8_t* ok, void* stream) {
+                           uint32_t num_keys, const uint32_t* key_idx, const uint8_t* msgs, const uint64_t* lens,
+                           const uint8_t* sigs_in, uint8_t* sigs_out, uint32_t count, uint8_t* ok, void* stream,
+                           bool fips = false, const uint8_t* prefix = nullptr, uint32_t plen = 0) {
     SetInfo si;
     if (!set_info(p, &si)) return fail(HS_EINVAL, "invalid parameter set %d", (int)p);
     if (count == 0) return HS_OK;
@@ -443,7 +445,7 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
     b.num_keys = num_keys;
     const size_t stage = (h_keys ? align256(key_bytes) : 0) + (h_idx ? align256((size_t)count * 4) : 0) +
                          (h_lens ? align256((size_t)count * 8) : 0) + (h_msgs ? align256(msg_total) : 0) +
-                         (h_sig ? align256(sig_total) : 0) + (h_ok ? align256(count) : 0);
+                         (h_sig ? align256(sig_total) : 0) + (h_ok ? align256(count) : 0) + align256(plen);
     void* base = nullptr;
     e = cudaMallocFromPoolAsync(&base, scratch + stage, d->pool, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(scratch)");
@@ -475,7 +477,10 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
     } else {
         b.sigs = h_sig ? reinterpret_cast<uint8_t*>(sg.take(sig_total)) : sigs_out;
     }
-    if (!b.keys_in || !b.lens || (h_msgs && !b.msgs) || !b.sigs) {
+    b.fips = fips;
+    b.prefix_len = plen;
+    b.prefix = plen ? static_cast<const uint8_t*>(h2d(prefix, plen, "copy prefix")) : nullptr;
+    if (!b.keys_in || !b.lens || (h_msgs && !b.msgs) || !b.sigs || (plen && !b.prefix)) {
         cudaFreeAsync(base, s);
         return HS_ECUDA;
     }
@@ -533,6 +538,42 @@ HS_API hs_status hs_verify_batch(hs_params p, const uint8_t* pk, uint32_t num_ke
                                  const uint8_t* msgs, const uint64_t* lens, const uint8_t* sigs, uint32_t count,
                                  uint8_t* ok, void* stream) {
     return run_batch(nullptr, true, p, pk, num_keys, key_idx, msgs, lens, sigs, nullptr, count, ok, stream);
+}
+
+// ----------------------------------------------------------- FIPS 205
+// The pure-signing prefix 0x00 || len(ctx) || ctx, or none for the
+// internal functions (ctx_len == HS_SLH_INTERNAL).
+static hs_status slh_prefix(const uint8_t* ctx, uint32_t ctx_len, uint8_t* out, uint32_t* plen) {
+    if (ctx_len == HS_SLH_INTERNAL) { *plen = 0; return HS_OK; }
+    if (ctx_len > 255) return fail(HS_EINVAL, "context string of %u bytes (at most 255)", ctx_len);
+    if (ctx_len && !ctx) return fail(HS_EINVAL, "NULL context string");
+    out[0] = 0;
+    out[1] = (uint8_t)ctx_len;
+    if (ctx_len) memcpy(out + 2, ctx, ctx_len);
+    *plen = 2 + ctx_len;
+    return HS_OK;
+}
+
+HS_API hs_status hs_slh_sign_batch(hs_params p, const uint8_t* sk, uint32_t num_keys, const uint32_t* key_idx,
+                                   const uint8_t* ctx, uint32_t ctx_len, const uint8_t* msgs, const uint64_t* lens,
+                                   uint32_t count, uint8_t* sigs, void* stream) {
+    uint8_t pre[258];
+    uint32_t plen = 0;
+    const hs_status st = slh_prefix(ctx, ctx_len, pre, &plen);
+    if (st != HS_OK) return st;
+    return run_batch(nullptr, false, p, sk, num_keys, key_idx, msgs, lens, nullptr, sigs, count, nullptr, stream,
+                     true, pre, plen);
+}
+
+HS_API hs_status hs_slh_verify_batch(hs_params p, const uint8_t* pk, uint32_t num_keys, const uint32_t* key_idx,
+                                     const uint8_t* ctx, uint32_t ctx_len, const uint8_t* msgs, const uint64_t* lens,
+                                     const uint8_t* sigs, uint32_t count, uint8_t* ok, void* stream) {
+    uint8_t pre[258];
+    uint32_t plen = 0;
+    const hs_status st = slh_prefix(ctx, ctx_len, pre, &plen);
+    if (st != HS_OK) return st;
+    return run_batch(nullptr, true, p, pk, num_keys, key_idx, msgs, lens, sigs, nullptr, count, ok, stream, true,
+                     pre, plen);
 }
 
 // ----------------------------------------------------------- keysets

@@ -56,6 +56,11 @@ struct Batch {
     // chk_u (owned by the keyset), tree ids computed directly (no table)
     bool cached;
     uint32_t cache_tpk;       // cached trees per key
+    // FIPS 205 mode: FORS indices MSB first; prefix bytes hashed before
+    // every message (0x00 || len(ctx) || ctx for pure signing; none = 0)
+    bool fips;
+    const uint8_t* prefix;    // device, prefix_len bytes
+    uint32_t prefix_len;
     uint32_t* status;         // per-device status word
 };
 

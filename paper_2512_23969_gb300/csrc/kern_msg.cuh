@@ -4,6 +4,9 @@
 //   R      = Trunc_n(HMAC-SHA-x(SK.prf, PK.seed || M))          (PRF_msg)
 //   digest = MGF1-SHA-x(R || PK.seed || SHA-x(R || PK.seed || PK.root || M), m)
 //   digest = md || tree bytes || leaf bytes -> k FORS indices, idx_tree, idx_leaf
+// FIPS 205 mode: M is preceded by a per-call prefix (0x00 || len(ctx) || ctx
+// for pure SLH-DSA) in both hashes, and the FORS indices are read from md
+// most significant bit first (FIPS 205 base_2b).
 // One thread per message; the work is serial in the message length (two
 // passes over M), which is the only length-dependent part of signing.
 #pragma once
@@ -171,7 +174,8 @@ template <class P>
 __global__ void message_kernel(const KeyBlock* __restrict__ keys, uint32_t num_keys,
                                const uint32_t* __restrict__ key_idx, const uint8_t* __restrict__ msgs,
                                const uint64_t* __restrict__ off, uint32_t count, uint8_t* __restrict__ sigs,
-                               MsgInfo* __restrict__ infos, uint32_t* __restrict__ status, int verify) {
+                               MsgInfo* __restrict__ infos, uint32_t* __restrict__ status, int verify,
+                               const uint8_t* __restrict__ prefix, uint32_t plen, int msb_first) {
     const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= count) return;
     constexpr int NW = P::NW;
@@ -210,6 +214,7 @@ __global__ void message_kernel(const KeyBlock* __restrict__ keys, uint32_t num_k
             h.words(&x, 4);
         }
         h.words(kb.pk_seed, P::N);
+        if (plen) h.mem(prefix, plen);
         h.mem(M, mlen);
         h.finish(inner);
         h.init();
@@ -231,6 +236,7 @@ __global__ void message_kernel(const KeyBlock* __restrict__ keys, uint32_t num_k
     h.words(R, P::N);
     h.words(kb.pk_seed, P::N);
     h.words(kb.pk_root, P::N);
+    if (plen) h.mem(prefix, plen);
     h.mem(M, mlen);
     h.finish(inner);
     uint32_t dg[16];                     // >= m bytes (m <= 49)
@@ -246,12 +252,15 @@ __global__ void message_kernel(const KeyBlock* __restrict__ keys, uint32_t num_k
         for (int i = 0; i < DW && got < P::M; i++, got += 4) dg[got >> 2] = blockd[i];
     }
     // md -> FORS indices: md read as a little-endian bit stream, index i from
-    // stream bits i*a .. i*a+a-1, first bit least significant.
+    // stream bits i*a .. i*a+a-1, first bit least significant; in FIPS 205
+    // mode bit q is bit 7 - q mod 8 of byte q/8 and the first bit read is the
+    // most significant.
     for (int i = 0; i < P::K; i++) {
         uint32_t v = 0;
         for (int j = 0; j < P::A; j++) {
             const int q = i * P::A + j;
-            v |= ((digest_byte<P>(dg, q >> 3) >> (q & 7)) & 1u) << j;
+            if (msb_first) v |= ((digest_byte<P>(dg, q >> 3) >> (7 - (q & 7))) & 1u) << (P::A - 1 - j);
+            else v |= ((digest_byte<P>(dg, q >> 3) >> (q & 7)) & 1u) << j;
         }
         info.fors_idx[i] = (uint16_t)v;
     }

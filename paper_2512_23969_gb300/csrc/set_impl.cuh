@@ -27,7 +27,8 @@ struct SetImpl {
     static cudaError_t message(const Batch& b, bool verify, cudaStream_t s) {
         const uint32_t T = 64, G = (b.count + T - 1) / T;
         message_kernel<P><<<G, T, 0, s>>>(b.keys, b.num_keys, b.key_idx, b.msgs, b.offsets, b.count, b.sigs,
-                                          b.infos, b.status, verify ? 1 : 0);
+                                          b.infos, b.status, verify ? 1 : 0, b.prefix, b.prefix_len,
+                                          b.fips ? 1 : 0);
         return cudaGetLastError();
     }
     template <int LPT>

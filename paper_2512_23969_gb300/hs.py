@@ -63,6 +63,10 @@ def load():
                                    C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_uint32]
     L.hs_server_destroy.argtypes = [C.c_void_p]
+    L.hs_slh_sign_batch.argtypes = [C.c_int, vp, u32, vp, vp, u32, vp, u64p, u32, vp, vp]
+    L.hs_slh_sign_batch.restype = C.c_int
+    L.hs_slh_verify_batch.argtypes = [C.c_int, vp, u32, vp, vp, u32, vp, u64p, vp, u32, vp, vp]
+    L.hs_slh_verify_batch.restype = C.c_int
     L.hs_keyset_create.argtypes = [C.c_int, vp, u32, u32, vp, C.POINTER(C.c_void_p)]
     L.hs_keyset_create.restype = C.c_int
     L.hs_keyset_bytes.argtypes = [vp]
@@ -159,6 +163,47 @@ def hs_sign_batch(params, sk, msgs, lens, key_idx=None, sigs=None, num_keys=None
     _check(load().hs_sign_batch(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), _ptr(msgs), _ptr(lens),
                                 count, _ptr(sigs), _stream(stream)))
     return sigs.reshape(count, S)
+
+
+SLH_INTERNAL = 0xFFFFFFFF
+
+
+def _ctx(ctx):
+    """(buffer, length) of a context string; None = the internal functions."""
+    if ctx is None:
+        return None, SLH_INTERNAL
+    ctx = bytes(ctx)
+    return (C.create_string_buffer(ctx, len(ctx)) if ctx else None), len(ctx)
+
+
+def hs_slh_sign_batch(params, sk, msgs, lens, ctx=b"", key_idx=None, sigs=None, num_keys=None, stream=None):
+    """FIPS 205 SLH-DSA signatures (deterministic) of every message under one
+    context string; ctx=None signs the messages as given (internal function)."""
+    count = int(lens.shape[0])
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    if num_keys is None:
+        num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
+    S = sig_bytes(params)
+    sigs = _like(lens, count * S, np.uint8, "uint8") if sigs is None else sigs
+    msgs = _nonempty(msgs, lens)
+    cbuf, clen = _ctx(ctx)
+    _check(load().hs_slh_sign_batch(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), cbuf, clen, _ptr(msgs),
+                                    _ptr(lens), count, _ptr(sigs), _stream(stream)))
+    return sigs.reshape(count, S)
+
+
+def hs_slh_verify_batch(params, pk, msgs, lens, sigs, ctx=b"", key_idx=None, ok=None, num_keys=None, stream=None):
+    """1/0 per FIPS 205 signature under one context string."""
+    count = int(lens.shape[0])
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    if num_keys is None:
+        num_keys = (pk.shape[0] if pk.ndim == 2 else pk.shape[0] // (2 * n))
+    ok = _like(lens, count, np.uint8, "uint8") if ok is None else ok
+    msgs = _nonempty(msgs, lens)
+    cbuf, clen = _ctx(ctx)
+    _check(load().hs_slh_verify_batch(_pid(params), _ptr(pk), int(num_keys), _ptr(key_idx), cbuf, clen, _ptr(msgs),
+                                      _ptr(lens), _ptr(sigs), count, _ptr(ok), _stream(stream)))
+    return ok
 
 
 class KeySet:
