@@ -9,9 +9,10 @@ from dataclasses import dataclass
 
 from . import build as _build
 
-PARAM_IDS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3,
+PARAM_IDS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3, "128s": 4, "192s": 5, "256s": 6,
              # the same sets in FIPS 205 mode (MSB-first FORS indices)
-             "slh-128f": 16, "slh-192f": 17, "slh-256f": 18, "slh-toy": 19}
+             "slh-128f": 16, "slh-192f": 17, "slh-256f": 18, "slh-toy": 19,
+             "slh-128s": 20, "slh-192s": 21, "slh-256s": 22}
 
 _lib = None
 

@@ -63,8 +63,9 @@ typedef struct {
     size_t fors_bytes, sig_bytes;
 } spx_params;
 
-/* ids: 0 = 128f, 1 = 192f, 2 = 256f, 3 = toy (n=16,h=4,d=2,h'=2,a=3,k=4);
- * + 16 = the same set in FIPS 205 mode */
+/* ids: 0 = 128f, 1 = 192f, 2 = 256f, 3 = toy (n=16,h=4,d=2,h'=2,a=3,k=4),
+ * 4 = 128s, 5 = 192s, 6 = 256s (the scheme's small-signature sets, a
+ * variant the paper does not use); + 16 = the same set in FIPS 205 mode */
 static int params_init(int id, spx_params *p)
 {
     memset(p, 0, sizeof(*p));
@@ -75,6 +76,9 @@ static int params_init(int id, spx_params *p)
     case 1: p->n = 24; p->h = 66; p->d = 22; p->a = 8; p->k = 33; break;
     case 2: p->n = 32; p->h = 68; p->d = 17; p->a = 9; p->k = 35; break;
     case 3: p->n = 16; p->h = 4;  p->d = 2;  p->a = 3; p->k = 4;  break;
+    case 4: p->n = 16; p->h = 63; p->d = 7;  p->a = 12; p->k = 14; break;
+    case 5: p->n = 24; p->h = 63; p->d = 7;  p->a = 14; p->k = 17; break;
+    case 6: p->n = 32; p->h = 64; p->d = 8;  p->a = 14; p->k = 22; break;
     default: return -1;
     }
     p->w = 16;
