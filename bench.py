@@ -55,6 +55,16 @@ STAGE_WORK = {
     "256f": {"tree": (17 * 16 * 67 * 16, 17 * 16 * 18 + 17 * 15),
              "fors": (35 * 512 * 2, 35 * 511 + 10),
              "wots": (17 * 67 * (1 + 7.5), 0)},
+    # the small-signature sets (2^h' = 512 / 512 / 256 leaves, FORS height 12 / 14 / 14)
+    "128s": {"tree": (7 * 512 * 35 * 16 + 7 * 512 * 10 + 7 * 511, 0),
+             "fors": (14 * 4096 * 2 + 14 * 4095 + 4, 0),
+             "wots": (7 * 35 * (1 + 7.5), 0)},
+    "192s": {"tree": (7 * 512 * 51 * 16, 7 * 512 * 10 + 7 * 511),
+             "fors": (17 * 16384 * 2, 17 * 16383 + 4),
+             "wots": (7 * 51 * (1 + 7.5), 0)},
+    "256s": {"tree": (8 * 256 * 67 * 16, 8 * 256 * 18 + 8 * 255),
+             "fors": (22 * 16384 * 2, 22 * 16383 + 6),
+             "wots": (8 * 67 * (1 + 7.5), 0)},
 }
 
 
@@ -237,14 +247,18 @@ def _time_steps(fn, stream, flush, steps, warmup):
     return ms
 
 
-def measure_other_configs(hs, inputs, args, stream, flush):
+def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
     import torch
     res = {}
     dev = lambda x: torch.from_numpy(x).cuda()
     steps, warmup = max(2, args.steps // 2), 3
-    for ps in ("192f", "256f"):
-        log("config 2 %s" % ps)
-        wl = inputs.config(2, ps)
+    for ps in ("192f", "256f", "128s", "192s", "256s"):
+        log("config %s" % ps)
+        if ps.endswith("f"):
+            wl = inputs.config(2, ps)
+        else:       # the same shape of workload, 1024 messages, for the small-signature sets
+            wl = inputs.make(ps, 1024, 16, ("uniform", 32, 1024), inputs.BASE_SEED + 3,
+                             "%s-16keys-1024xU[32,1024]B" % ps)
         pk, sk = hs.hs_keygen(ps, dev(wl.seeds))
         m, l, k = dev(wl.msgs), dev(wl.lens), dev(wl.key_idx)
         sig = torch.empty(wl.count * hs.sig_bytes(ps), dtype=torch.uint8, device="cuda")
@@ -257,6 +271,8 @@ def measure_other_configs(hs, inputs, args, stream, flush):
         res[ps] = {"workload": wl.name, "value": round(wl.count * len(ms) / (sum(ms) / 1e3), 1),
                    "unit": "signatures/s", "ms_per_step": round(sum(ms) / len(ms), 3),
                    "stage_ms": {a: round(b, 3) for a, b in prof.items()},
+                   "alu_frac": {st: round(alu_ops_per_sig(ps, st) * wl.count / (prof[st] / 1e3) / 1e12 / alu_peak, 4)
+                                for st in ("tree", "fors") if prof.get(st, 0) > 0},
                    "verified": int(ok.sum().item()) == wl.count}
     # the bench workload again with tree sharing on (same signatures, less work)
     log("128f with tree sharing")
@@ -544,7 +560,7 @@ def run_own(args):
     others = {}
     if args.other_configs and rank == 0:
         try:
-            others = measure_other_configs(hs, inputs, args, stream, flush)
+            others = measure_other_configs(hs, inputs, args, stream, flush, alu_peak)
         except Exception as exc:      # keep the main line; report what failed
             others = {"error": repr(exc)[:300]}
 

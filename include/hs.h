@@ -42,10 +42,19 @@
 extern "C" {
 #endif
 
-/* Parameter sets.  HS_TOY is a test-only miniature (n=16, h=4, d=2, h'=2,
+/* Parameter sets.  HS_128F/192F/256F are the sets the paper signs with
+ * (its Table 1).  HS_TOY is a test-only miniature (n=16, h=4, d=2, h'=2,
  * a=3, k=4, 1456-byte signatures) with no security; it exists so that every
- * tree of the hypertree can be brute-forced in tests. */
-typedef enum { HS_128F = 0, HS_192F = 1, HS_256F = 2, HS_TOY = 3 } hs_params;
+ * tree of the hypertree can be brute-forced in tests.  HS_128S/192S/256S are
+ * the scheme's small-signature sets (a variant the paper does not use):
+ * (n, h, d, h', a, k) = (16, 63, 7, 9, 12, 14), (24, 63, 7, 9, 14, 17),
+ * (32, 64, 8, 8, 14, 22); 7856 / 16224 / 29792-byte signatures.  Tree
+ * sharing and keyset caches are not offered for them. */
+typedef enum {
+    HS_128F = 0, HS_192F = 1, HS_256F = 2, HS_TOY = 3,
+    HS_128S = 4, HS_192S = 5, HS_256S = 6
+} hs_params;
+#define HS_NUM_PARAMS 7
 
 typedef enum {
     HS_OK = 0,
@@ -259,7 +268,8 @@ typedef struct {
     uint32_t max_batch;         /* requests per batch */
     uint64_t mem_budget_bytes;  /* device arena for in-flight work (>= 1 MiB) */
     uint64_t pinned_bytes;      /* pinned host staging arena (0 = budget / 2) */
-    uint32_t cache_layers;      /* top hypertree layers prebuilt per key (hs_keyset; 0 = none) */
+    uint32_t cache_layers;      /* top hypertree layers prebuilt per key (hs_keyset; 0 = none;
+                                   ignored for the s sets) */
 } hs_server_config;
 typedef struct {
     uint64_t completed, batches, batched_requests, pending;
@@ -268,8 +278,8 @@ typedef struct {
     uint64_t failed;            /* requests completed with HS_ECUDA */
     uint64_t cancelled;         /* requests completed with HS_ECANCELED */
 } hs_server_stats;
-hs_status hs_server_create(const hs_server_config *cfg, const uint8_t *const sks[4],
-                           const uint32_t nkeys[4], hs_server **out);
+hs_status hs_server_create(const hs_server_config *cfg, const uint8_t *const sks[HS_NUM_PARAMS],
+                           const uint32_t nkeys[HS_NUM_PARAMS], hs_server **out);
 hs_status hs_server_submit(hs_server *s, hs_params p, uint32_t key, const uint8_t *msg,
                            uint64_t len, uint8_t *sig_out, uint64_t *id);
 hs_status hs_server_wait(hs_server *s, uint64_t id, uint32_t timeout_ms);

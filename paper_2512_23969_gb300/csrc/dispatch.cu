@@ -11,15 +11,20 @@ const SetOps* set_ops(int pset) {
     case 1: return &kOps_192F;
     case 2: return &kOps_256F;
     case 3: return &kOps_Toy;
+    case 4: return &kOps_128S;
+    case 5: return &kOps_192S;
+    case 6: return &kOps_256S;
     }
     return nullptr;
 }
 
 namespace {
 // -1 = not set: use the table's default.
-std::atomic<int> g_tune[4][3] = {{{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}};
+std::atomic<int> g_tune[kNumSets][3] = {{{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}},
+                                        {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}},
+                                        {{-1}, {-1}, {-1}}};
 // Default batch size below which TREE_Sign runs chain-parallel, per set.
-constexpr int kSplitDefault[4] = {8192, 2048, 4096, 0};
+constexpr int kSplitDefault[kNumSets] = {8192, 2048, 4096, 0, 64, 64, 64};
 }
 
 int tune_get(int pset, int knob) {

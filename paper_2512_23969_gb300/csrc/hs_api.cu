@@ -47,12 +47,25 @@ static bool set_info(int p, SetInfo* s) {
     case 1: *s = HS_SETINFO(P192f); return true;
     case 2: *s = HS_SETINFO(P256f); return true;
     case 3: *s = HS_SETINFO(PToy); return true;
+    case 4: *s = HS_SETINFO(P128s); return true;
+    case 5: *s = HS_SETINFO(P192s); return true;
+    case 6: *s = HS_SETINFO(P256s); return true;
     }
 #undef HS_SETINFO
     return false;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool set_shape(int pset, SetShape* out) {
+    SetInfo s;
+    if (!set_info(pset, &s)) return false;
+    out->n = s.n;
+    out->d = s.d;
+    out->sig = s.sig;
+    out->leaves = s.leaves;
+    return true;
+}
 
 // Tree sharing within a batch (process-wide switch, off by default).
 static bool g_share = false;
@@ -63,6 +76,7 @@ void plan_dedup(Batch& b) {
     b.max_uniq = 0;
     SetInfo s;
     if (!g_share || !set_info(b.pset, &s) || b.num_keys > (1u << 20) || b.count == 0) return;
+    if (s.leaves > 32) return;        // wide trees: no sharing
     // Share layers from the top down while the number of distinct trees a
     // layer can hold (keys x 2^bits of its tree index, at most one per
     // message) is at most half the messages, and the tree index fits the
@@ -87,7 +101,8 @@ void plan_dedup(Batch& b) {
 }
 
 // Every scratch region of a batch, in carve order (256-byte aligned each).
-static void scratch_layout(const Batch& b, const SetInfo& s, size_t sz[16], int* n) {
+static constexpr int kRegions = 17;
+static void scratch_layout(const Batch& b, const SetInfo& s, size_t sz[kRegions], int* n) {
     const size_t nw = (size_t)s.n / 4, cnt = b.count;
     int i = 0;
     sz[i++] = sizeof(uint32_t);                                      // reserved
@@ -111,13 +126,14 @@ static void scratch_layout(const Batch& b, const SetInfo& s, size_t sz[16], int*
     sz[i++] = mu * sizeof(DedupDesc);                                // desc
     sz[i++] = mu * 2 * s.leaves * nw * 4 +                           // nodes_u, then chk_u
               (b.ck ? mu * s.leaves * s.len * (16 / b.ck) * nw * 4 : 0);
+    sz[i++] = s.leaves > 32 ? cnt * s.d * s.leaves * nw * 4 : 0;     // leafv
     *n = i;
 }
 
 size_t scratch_bytes(const Batch& b) {
     SetInfo s;
     if (!set_info(b.pset, &s)) return 0;
-    size_t sz[16], t = 0;
+    size_t sz[kRegions], t = 0;
     int n;
     scratch_layout(b, s, sz, &n);
     for (int i = 0; i < n; i++) t += align256(sz[i]);
@@ -139,11 +155,11 @@ size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck, b
 void carve_scratch(Batch& b, void* base) {
     SetInfo s;
     set_info(b.pset, &s);
-    size_t sz[16];
+    size_t sz[kRegions];
     int n;
     scratch_layout(b, s, sz, &n);
     char* p = static_cast<char*>(base);
-    char* r[16];
+    char* r[kRegions];
     for (int i = 0; i < n; i++) { r[i] = p; p += align256(sz[i]); }
     b.keys = reinterpret_cast<KeyBlock*>(r[1]);
     b.offsets = reinterpret_cast<uint64_t*>(r[2]);
@@ -153,6 +169,7 @@ void carve_scratch(Batch& b, void* base) {
     b.roots = reinterpret_cast<uint32_t*>(r[6]);
     b.chk = b.ck ? reinterpret_cast<uint32_t*>(r[7]) : nullptr;
     b.ends = b.split ? reinterpret_cast<uint32_t*>(r[8]) : nullptr;
+    b.leafv = s.leaves > 32 ? reinterpret_cast<uint32_t*>(r[16]) : nullptr;
     const bool sh = b.dedup_layer != 0 && !b.cached;
     b.table = sh ? reinterpret_cast<unsigned long long*>(r[9]) : nullptr;
     b.mj_slot = sh ? reinterpret_cast<uint32_t*>(r[10]) : nullptr;
@@ -593,6 +610,8 @@ HS_API hs_status hs_keyset_create(hs_params p, const uint8_t* sk, uint32_t num_k
     if (!sk || !out || num_keys == 0) return fail(HS_EINVAL, "hs_keyset_create: NULL buffer or no keys");
     if (cache_layers > (uint32_t)si.d - 1)
         return fail(HS_EINVAL, "cache_layers %u: at most d - 1 = %d", cache_layers, si.d - 1);
+    if (cache_layers && si.leaves > 32)
+        return fail(HS_EINVAL, "cache_layers: not offered for the s sets (2^h' = %d leaves per tree)", si.leaves);
     if (cache_layers && (uint64_t)(cache_layers - 1) * si.hp > 24)
         return fail(HS_EINVAL, "cache_layers %u: more than 2^24 trees per key", cache_layers);
     uint64_t tpk = 0;

@@ -39,6 +39,7 @@ struct Batch {
     uint32_t ck;              // checkpoint stride (1, 2, 4) or 0 = none
     bool split;               // TREE_Sign in its chain-parallel form (small batches)
     uint32_t* ends;           // chain ends of the split form: count * D * 2^h' * LEN * NW words
+    uint32_t* leafv;          // wide trees (2^h' > 32): leaves, count * D * 2^h' * NW words
     // tree sharing within the batch: layers dedup_layer .. D-1 are shared
     // (dedup_layer == 0: off, every message builds all its layers)
     uint32_t dedup_layer;
@@ -110,7 +111,12 @@ struct SetOps {
     int n_tree_minb;
     int tree_minb_default;
 };
-extern const SetOps kOps_128F, kOps_192F, kOps_256F, kOps_Toy;
+extern const SetOps kOps_128F, kOps_192F, kOps_256F, kOps_Toy, kOps_128S, kOps_192S, kOps_256S;
+constexpr int kNumSets = 7;   // 128f, 192f, 256f, toy, 128s, 192s, 256s
+
+// Shape of a parameter set for host code (false for an unknown id).
+struct SetShape { int n, d, sig, leaves; };
+bool set_shape(int pset, SetShape* out);
 const SetOps* set_ops(int pset);
 
 // Tuned launch shape per set (knob 0 = FORS lanes per tree, 1 = TREE min

@@ -113,7 +113,7 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
     size_t total = 0;
     for (uint32_t j = 0; j < njobs; j++) {
         const hs_sign_job& jb = jobs[j];
-        if ((int)jb.params < 0 || (int)jb.params > 3) return mx_fail(HS_EINVAL, "hs_sign_mixed: invalid parameter set");
+        if ((int)jb.params < 0 || (int)jb.params >= kNumSets) return mx_fail(HS_EINVAL, "hs_sign_mixed: invalid parameter set");
         if (jb.count == 0) continue;
         if (!jb.sk || !jb.msgs || !jb.lens || !jb.sigs || jb.num_keys == 0)
             return mx_fail(HS_EINVAL, "hs_sign_mixed: NULL buffer or num_keys == 0");

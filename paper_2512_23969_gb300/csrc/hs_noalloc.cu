@@ -73,7 +73,7 @@ using namespace hs;
 HS_API hs_status hs_sign_batch_noalloc(hs_params p, const uint8_t* sk, uint32_t num_keys,
                                        const uint32_t* key_idx, const uint8_t* msgs, const uint64_t* lens,
                                        uint32_t count, uint8_t* sigs, void* stream) {
-    if ((int)p < 0 || (int)p > 3) return na_fail(HS_EINVAL, "hs_sign_batch_noalloc: invalid parameter set");
+    if ((int)p < 0 || (int)p >= kNumSets) return na_fail(HS_EINVAL, "hs_sign_batch_noalloc: invalid parameter set");
     if (count == 0) return HS_OK;
     if (!sk || !msgs || !lens || !sigs) return na_fail(HS_EINVAL, "hs_sign_batch_noalloc: NULL buffer");
     if (num_keys == 0) return na_fail(HS_EINVAL, "hs_sign_batch_noalloc: num_keys must be > 0");

@@ -36,16 +36,25 @@ using P128f = Params<16, 66, 22, 6, 33>;
 using P192f = Params<24, 66, 22, 8, 33>;
 using P256f = Params<32, 68, 17, 9, 35>;
 using PToy  = Params<16, 4, 2, 3, 4>;
+// The small-signature sets of the same scheme (a variant; the paper uses
+// the f sets only): h' = 9 / 9 / 8, FORS height 12 / 14 / 14.
+using P128s = Params<16, 63, 7, 12, 14>;
+using P192s = Params<24, 63, 7, 14, 17>;
+using P256s = Params<32, 64, 8, 14, 22>;
 
 static_assert(P128f::SIG_BYTES == 17088, "128f signature size");
 static_assert(P192f::SIG_BYTES == 35664, "192f signature size");
 static_assert(P256f::SIG_BYTES == 49856, "256f signature size");
 static_assert(PToy::SIG_BYTES == 1456, "toy signature size");
+static_assert(P128s::SIG_BYTES == 7856 && P192s::SIG_BYTES == 16224 && P256s::SIG_BYTES == 29792,
+              "s signature sizes");
+static_assert(P128s::M == 30 && P192s::M == 39 && P256s::M == 47, "s digest bytes");
 static_assert(P128f::LEN == 35 && P192f::LEN == 51 && P256f::LEN == 67, "WOTS len");
 static_assert(P128f::M == 34 && P192f::M == 42 && P256f::M == 49, "digest bytes");
 // every signature starts 16-byte aligned when the buffer does
 static_assert(P128f::SIG_BYTES % 16 == 0 && P192f::SIG_BYTES % 16 == 0 &&
-              P256f::SIG_BYTES % 16 == 0 && PToy::SIG_BYTES % 16 == 0, "sig alignment");
+              P256f::SIG_BYTES % 16 == 0 && PToy::SIG_BYTES % 16 == 0 && P128s::SIG_BYTES % 16 == 0 &&
+              P192s::SIG_BYTES % 16 == 0 && P256s::SIG_BYTES % 16 == 0, "sig alignment");
 
 // Address types of the scheme's ADRS.
 enum : uint32_t { T_WOTS_HASH = 0, T_WOTS_PK = 1, T_TREE = 2, T_FORS_TREE = 3,

@@ -123,8 +123,8 @@ struct ServerImpl {
     hs_server_config cfg;
     int device = 0;
     // per set: resident keys and midstates
-    hs_keyset* ks[4] = {nullptr, nullptr, nullptr, nullptr};   // with the cached top layers
-    uint32_t nkeys[4] = {0, 0, 0, 0};
+    hs_keyset* ks[kNumSets] = {};     // resident keys (with the cached top layers)
+    uint32_t nkeys[kNumSets] = {};
     // arenas
     uint8_t* dev_base = nullptr;
     uint8_t* host_base = nullptr;
@@ -134,7 +134,7 @@ struct ServerImpl {
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::unordered_map<uint64_t, Request> reqs;
-    std::deque<uint64_t> pending[4];
+    std::deque<uint64_t> pending[kNumSets];
     std::deque<uint64_t> completed;
     uint64_t next_id = 1;
     bool stop = false;
@@ -149,15 +149,9 @@ struct ServerImpl {
 namespace {
 
 int sig_bytes_of(int p) {
-    switch (p) {
-    case 0: return P128f::SIG_BYTES;
-    case 1: return P192f::SIG_BYTES;
-    case 2: return P256f::SIG_BYTES;
-    case 3: return PToy::SIG_BYTES;
-    }
-    return 0;
+    SetShape sh;
+    return set_shape(p, &sh) ? sh.sig : 0;
 }
-int n_of(int p) { return p == 1 ? 24 : (p == 2 ? 32 : 16); }
 
 // Bytes a batch needs from each arena.
 struct Need { size_t dev, host; };
@@ -213,7 +207,7 @@ void retire(ServerImpl& sv) {
 bool admit(ServerImpl& sv, Slot& slot) {
     int best = -1;
     uint64_t oldest = UINT64_MAX;
-    for (int p = 0; p < 4; p++)
+    for (int p = 0; p < kNumSets; p++)
         if (!sv.pending[p].empty()) {
             const uint64_t t = sv.reqs[sv.pending[p].front()].t_arrive;
             if (t < oldest) { oldest = t; best = p; }
@@ -360,8 +354,8 @@ static hs_status sv_fail(hs_status st, const char* msg) {
     return st;
 }
 
-HS_API hs_status hs_server_create(const hs_server_config* cfg, const uint8_t* const sks[4],
-                                  const uint32_t nkeys[4], hs_server** out) {
+HS_API hs_status hs_server_create(const hs_server_config* cfg, const uint8_t* const sks[HS_NUM_PARAMS],
+                                  const uint32_t nkeys[HS_NUM_PARAMS], hs_server** out) {
     if (!cfg || !sks || !nkeys || !out) return sv_fail(HS_EINVAL, "hs_server_create: NULL argument");
     if (cfg->max_inflight < 1 || cfg->max_inflight > 16 || cfg->max_batch < 1 || cfg->mem_budget_bytes < (1u << 20))
         return sv_fail(HS_EINVAL, "hs_server_create: max_inflight 1..16, max_batch >= 1, budget >= 1 MiB");
@@ -370,12 +364,13 @@ HS_API hs_status hs_server_create(const hs_server_config* cfg, const uint8_t* co
     sv.cfg = *cfg;
     cudaGetDevice(&sv.device);
     bool ok = true;
-    for (int p = 0; p < 4 && ok; p++) {
+    for (int p = 0; p < kNumSets && ok; p++) {
         sv.nkeys[p] = nkeys[p];
         if (!nkeys[p]) continue;
         if (!sks[p]) { ok = false; break; }
-        const uint32_t d = p == 2 ? 17u : (p == 3 ? 2u : 22u);
-        const uint32_t layers = std::min<uint32_t>(cfg->cache_layers, d - 1);
+        SetShape sh;
+        set_shape(p, &sh);
+        const uint32_t layers = sh.leaves > 32 ? 0u : std::min<uint32_t>(cfg->cache_layers, (uint32_t)sh.d - 1);
         ok = hs_keyset_create((hs_params)p, sks[p], nkeys[p], layers, nullptr, &sv.ks[p]) == HS_OK;
     }
     const size_t host_bytes = cfg->pinned_bytes ? cfg->pinned_bytes : cfg->mem_budget_bytes / 2;
@@ -401,7 +396,7 @@ HS_API hs_status hs_server_create(const hs_server_config* cfg, const uint8_t* co
 
 static hs_status submit_at(hs_server* s, hs_params p, uint32_t key, const uint8_t* msg, uint64_t len,
                            uint8_t* sig_out, uint64_t* id, uint64_t t_arrive) {
-    if (!s || (int)p < 0 || (int)p > 3 || (len && !msg))
+    if (!s || (int)p < 0 || (int)p >= kNumSets || (len && !msg))
         return sv_fail(HS_EINVAL, "hs_server_submit: bad argument");
     ServerImpl& sv = s->impl;
     if (key >= sv.nkeys[p]) return sv_fail(HS_EKEY, "hs_server_submit: key index out of range");
@@ -477,7 +472,7 @@ HS_API hs_status hs_server_get_stats(hs_server* s, hs_server_stats* st) {
     st->failed = sv.n_failed;
     st->cancelled = sv.n_cancelled;
     uint64_t pend = 0;
-    for (int p = 0; p < 4; p++) pend += sv.pending[p].size();
+    for (int p = 0; p < kNumSets; p++) pend += sv.pending[p].size();
     st->pending = pend;
     return sv.fatal;
 }
@@ -580,7 +575,7 @@ HS_API hs_status hs_server_destroy(hs_server* s) {
         }
         if (sl.done) cudaEventDestroy(sl.done);
     }
-    for (int p = 0; p < 4; p++) hs_keyset_destroy(sv.ks[p]);
+    for (int p = 0; p < kNumSets; p++) hs_keyset_destroy(sv.ks[p]);
     if (sv.dev_base) cudaFree(sv.dev_base);
     if (sv.host_base) cudaFreeHost(sv.host_base);
     delete s;

@@ -10,7 +10,9 @@
 // height R = a - log2(LPT) over 2^R consecutive leaves with a register
 // treehash (one H call site, left siblings kept in a small select-indexed
 // stack), then the top log2(LPT) levels are merged across the group with
-// warp shuffles.  No shared memory and no block barriers; the grid is flat
+// warp shuffles.  Lane subtrees taller than 7 levels (a = 12-14 of the s
+// sets) are built as 2^(R-7) consecutive height-7 subtrees whose roots are
+// merged through a second stack of at most 3 nodes.  No shared memory and no block barriers; the grid is flat
 // over (message, tree, lane), so every message's k trees run in parallel.
 #pragma once
 #include <cuda_runtime.h>
@@ -30,7 +32,9 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
                                                    uint32_t one) {
     constexpr int NW = P::NW, A = P::A, K = P::K;
     constexpr int R = A - Log2<LPT>::v;           // height built inside one lane
-    static_assert(R >= 1 && R <= 7, "lane subtree height");
+    constexpr int RI = R < 7 ? R : 7;             // inner treehash height
+    constexpr int RO = R - RI;                    // levels merged by the outer stack
+    static_assert(R >= 1 && RO <= 3, "lane subtree height");
     const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t L = gid % LPT;                  // lane within the tree group
@@ -59,50 +63,83 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
     uint8_t* sf = sigs + (size_t)m * P::SIG_BYTES + P::N + (size_t)i * (A + 1) * P::N;
 
     const Pipes<POL> pp(one);
-    uint32_t stk[R][NW];                           // left siblings, levels 0..R-1
+    uint32_t stk[RI][NW];                          // left siblings, levels 0..RI-1
+    uint32_t ostk[RO > 0 ? RO : 1][NW];            // left siblings, levels RI..R-1
     uint32_t node[NW];
     const uint32_t base = L << R;                  // first leaf of this lane (within tree)
 #pragma unroll 1
-    for (uint32_t p = 0; p < (1u << R); p++) {
-        const uint32_t t = base + p;               // leaf index within tree
-        const uint32_t g = (i << A) + t;           // global leaf index
-        // leaf g: sk = PRF(FORS_PRF(g)), then F(FORS_TREE(height 0, g), sk);
-        // both through one call site of the compression
-#pragma unroll
-        for (int w = 0; w < NW; w++) node[w] = skseed[w];
+    for (uint32_t ob = 0; ob < (1u << RO); ob++) {
 #pragma unroll 1
-        for (int s = 0; s < 2; s++) {
-            hashF_fast<POL, NW>(ms256, make_adrs(0, tree, s == 0 ? T_FORS_PRF : T_FORS_TREE, kp, 0, g), node,
-                                node, pp);
-            if (s == 0 && t == gs) store_be<NW>(sf, node);
-        }
-        if (t == (gs ^ 1u)) store_be<NW>(sf + P::N, node);
-        // merge with stacked left siblings while this node is a right child
-        uint32_t z = 0, idx = t;
+        for (uint32_t p = 0; p < (1u << RI); p++) {
+            const uint32_t t = base + (ob << RI) + p;  // leaf index within tree
+            const uint32_t g = (i << A) + t;           // global leaf index
+            // leaf g: sk = PRF(FORS_PRF(g)), then F(FORS_TREE(height 0, g), sk);
+            // both through one call site of the compression
+#pragma unroll
+            for (int w = 0; w < NW; w++) node[w] = skseed[w];
 #pragma unroll 1
-        while ((idx & 1u) && z < (uint32_t)R) {
-            uint32_t lr[2 * NW];
-#pragma unroll
-            for (int w = 0; w < NW; w++) {
-                uint32_t v = stk[0][w];
-#pragma unroll
-                for (int zz = 1; zz < R; zz++) v = (z == (uint32_t)zz) ? stk[zz][w] : v;
-                lr[w] = v;
-                lr[NW + w] = node[w];
+            for (int s = 0; s < 2; s++) {
+                hashF_fast<POL, NW>(ms256, make_adrs(0, tree, s == 0 ? T_FORS_PRF : T_FORS_TREE, kp, 0, g), node,
+                                    node, pp);
+                if (s == 0 && t == gs) store_be<NW>(sf, node);
             }
-            z++;
-            idx >>= 1;
-            hashH_ms<P>(ms256, ms512,
-                        make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node);
-            if (z < (uint32_t)A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
-        }
-        if (z < (uint32_t)R) {
+            if (t == (gs ^ 1u)) store_be<NW>(sf + P::N, node);
+            // merge with stacked left siblings while this node is a right child
+            uint32_t z = 0, idx = t;
+#pragma unroll 1
+            while ((idx & 1u) && z < (uint32_t)RI) {
+                uint32_t lr[2 * NW];
 #pragma unroll
-            for (int zz = 0; zz < R; zz++)
-                if (z == (uint32_t)zz) {
+                for (int w = 0; w < NW; w++) {
+                    uint32_t v = stk[0][w];
 #pragma unroll
-                    for (int w = 0; w < NW; w++) stk[zz][w] = node[w];
+                    for (int zz = 1; zz < RI; zz++) v = (z == (uint32_t)zz) ? stk[zz][w] : v;
+                    lr[w] = v;
+                    lr[NW + w] = node[w];
                 }
+                z++;
+                idx >>= 1;
+                hashH_ms<P>(ms256, ms512,
+                            make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node);
+                if (z < (uint32_t)A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
+            }
+            if (z < (uint32_t)RI) {
+#pragma unroll
+                for (int zz = 0; zz < RI; zz++)
+                    if (z == (uint32_t)zz) {
+#pragma unroll
+                        for (int w = 0; w < NW; w++) stk[zz][w] = node[w];
+                    }
+            }
+        }
+        if constexpr (RO > 0) {
+            // node = root of inner subtree ob (level RI); merge with the outer stack
+            uint32_t z = RI, idx = (base >> RI) + ob;
+#pragma unroll 1
+            while ((idx & 1u) && z < (uint32_t)R) {
+                uint32_t lr[2 * NW];
+#pragma unroll
+                for (int w = 0; w < NW; w++) {
+                    uint32_t v = ostk[0][w];
+#pragma unroll
+                    for (int zz = 1; zz < RO; zz++) v = (z - RI == (uint32_t)zz) ? ostk[zz][w] : v;
+                    lr[w] = v;
+                    lr[NW + w] = node[w];
+                }
+                z++;
+                idx >>= 1;
+                hashH_ms<P>(ms256, ms512,
+                            make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node);
+                if (z < (uint32_t)A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
+            }
+            if (z < (uint32_t)R) {
+#pragma unroll
+                for (int zz = 0; zz < RO; zz++)
+                    if (z - RI == (uint32_t)zz) {
+#pragma unroll
+                        for (int w = 0; w < NW; w++) ostk[zz][w] = node[w];
+                    }
+            }
         }
     }
     // node = lane subtree root, level R, index L within the tree

@@ -10,11 +10,16 @@
 #include "kern_wots.cuh"
 #include "kern_verify.cuh"
 #include "kern_dedup.cuh"
+#include "kern_stree.cuh"
 
 namespace hs {
 
 template <class P>
 struct SetImpl {
+    // XMSS trees wider than a warp (s sets) take the two-launch form of
+    // kern_stree.cuh; tree sharing and keyset caches are not offered there.
+    static constexpr bool kWide = P::LEAVES > 32;
+
     // layers each message builds itself: all of them unless the upper
     // layers are shared within the batch (dedup_layer = first shared layer)
     static uint32_t own_layers(const Batch& b) { return b.dedup_layer ? b.dedup_layer : (uint32_t)P::D; }
@@ -51,11 +56,29 @@ struct SetImpl {
         const uint32_t T = 128;
         const uint32_t G = (uint32_t)((threads + T - 1) / T);
         if (threads == 0) return cudaSuccess;
-        tree_kernel<P, kChainPol, MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck,
-                                                         L, 1u);
+        if constexpr (kWide) {
+            bleaf_kernel<P, kChainPol, MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.leafv, b.chk, b.ck, L, 1u);
+            cudaError_t e = cudaGetLastError();
+            return e == cudaSuccess ? merge(b, s) : e;
+        } else {
+            tree_kernel<P, kChainPol, MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck,
+                                                             L, 1u);
+            return cudaGetLastError();
+        }
+    }
+    // Wide trees: one block per (message, layer) merges the stored leaves.
+    static cudaError_t merge(const Batch& b, cudaStream_t s) {
+        const uint32_t L = own_layers(b);
+        const uint64_t blocks = (uint64_t)b.count * L;
+        if (blocks == 0) return cudaSuccess;
+        bmerkle_kernel<P><<<(uint32_t)blocks, kMergeThreads, 0, s>>>(b.keys, b.infos, b.count, b.leafv, b.sigs,
+                                                                     b.roots, L);
         return cudaGetLastError();
     }
     static cudaError_t tree_dedup(const Batch& b, cudaStream_t s) {
+        if constexpr (kWide) {
+            return cudaErrorNotSupported;
+        } else {
         const uint32_t T = 128, L = own_layers(b);
         const uint64_t mj = (uint64_t)b.count * (P::D - L);
         dedup_insert_kernel<P><<<(uint32_t)((mj + T - 1) / T), T, 0, s>>>(b.infos, b.count, L, b.table, b.cap_log2,
@@ -73,6 +96,7 @@ struct SetImpl {
         dedup_scatter_kernel<P><<<(uint32_t)((mj + T - 1) / T), T, 0, s>>>(b.infos, b.count, L, b.mj_slot, b.slot_id,
                                                                            b.nodes_u, b.sigs, b.roots, b.mj_id);
         return cudaGetLastError();
+        }
     }
     // Cached top layers (keyset): auth paths, roots and tree ids from the cache.
     static cudaError_t tree_cached(const Batch& b, cudaStream_t s) {
@@ -86,6 +110,7 @@ struct SetImpl {
     // Build every tree of layers L..D-1 of num_keys resident keys.
     static cudaError_t cache_build(const KeyBlock* keys, uint32_t num_keys, uint32_t L, uint32_t tpk,
                                    DedupDesc* desc, uint32_t* nodes, uint32_t* chk, uint32_t ck, cudaStream_t s) {
+        if constexpr (kWide) return cudaErrorNotSupported;
         const uint32_t T = 128;
         const uint64_t trees = (uint64_t)num_keys * tpk;
         if (trees == 0) return cudaSuccess;
@@ -93,8 +118,10 @@ struct SetImpl {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const uint64_t th = trees * P::LEAVES;
-        utree_kernel<P, kChainPol><<<(uint32_t)((th + T - 1) / T), T, 0, s>>>(keys, desc, nullptr, (uint32_t)trees,
-                                                                              nodes, chk, ck, 1u);
+        if constexpr (!kWide)
+            utree_kernel<P, kChainPol><<<(uint32_t)((th + T - 1) / T), T, 0, s>>>(keys, desc, nullptr,
+                                                                                  (uint32_t)trees, nodes, chk, ck,
+                                                                                  1u);
         return cudaGetLastError();
     }
     static cudaError_t tree_split(const Batch& b, cudaStream_t s) {
@@ -107,9 +134,16 @@ struct SetImpl {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const uint64_t leaves = (uint64_t)b.count * L * P::LEAVES;
-        leaves_kernel<P><<<(uint32_t)((leaves + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.ends, b.sigs,
-                                                                        b.roots, L);
-        return cudaGetLastError();
+        if constexpr (kWide) {
+            bleaf_from_ends_kernel<P><<<(uint32_t)((leaves + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count,
+                                                                                    b.ends, b.leafv, L);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            return merge(b, s);
+        } else {
+            leaves_kernel<P><<<(uint32_t)((leaves + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.ends,
+                                                                            b.sigs, b.roots, L);
+            return cudaGetLastError();
+        }
     }
     static cudaError_t wots(const Batch& b, cudaStream_t s) {
         const uint64_t threads = (uint64_t)b.count * P::D * P::LEN;
@@ -128,8 +162,30 @@ struct SetImpl {
         const uint64_t threads = (uint64_t)count * P::LEAVES;
         const uint32_t T = 128;
         const uint32_t G = (uint32_t)((threads + T - 1) / T);
-        keygen_kernel<P><<<G, T, 0, s>>>(seeds, count, pk, sk, 1u);
-        return cudaGetLastError();
+        if constexpr (kWide) {
+            // key blocks, top-tree leaves, then one block per key for the root
+            const size_t kb_bytes = ((size_t)count * sizeof(KeyBlock) + 255) & ~(size_t)255;
+            void* scratch = nullptr;
+            cudaError_t e = pool_alloc(&scratch, kb_bytes + threads * P::NW * 4, s);
+            if (e != cudaSuccess) return e;
+            KeyBlock* kbs = static_cast<KeyBlock*>(scratch);
+            uint32_t* leafv = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) + kb_bytes);
+            seed_keys_kernel<P><<<(count + T - 1) / T, T, 0, s>>>(seeds, count, kbs);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) {
+                bkeygen_leaf_kernel<P, kChainPol><<<G, T, 0, s>>>(kbs, count, leafv, 1u);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) {
+                bkeygen_root_kernel<P><<<count, kMergeThreads, 0, s>>>(kbs, seeds, count, leafv, pk, sk);
+                e = cudaGetLastError();
+            }
+            const cudaError_t f = cudaFreeAsync(scratch, s);
+            return e == cudaSuccess ? f : e;
+        } else {
+            keygen_kernel<P><<<G, T, 0, s>>>(seeds, count, pk, sk, 1u);
+            return cudaGetLastError();
+        }
     }
 };
 

@@ -10,8 +10,9 @@ import os
 
 import numpy as np
 
-PARAMS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3}
-N_BYTES = {"128f": 16, "192f": 24, "256f": 32, "toy": 16}
+PARAMS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3, "128s": 4, "192s": 5, "256s": 6}
+N_BYTES = {"128f": 16, "192f": 24, "256f": 32, "toy": 16, "128s": 16, "192s": 24, "256s": 32}
+NUM_PARAMS = 7
 STATUS = {0: "HS_OK", 1: "HS_EINVAL", 2: "HS_ENOMEM", 3: "HS_ECUDA", 4: "HS_ETIMEOUT", 5: "HS_EKEY",
           6: "HS_ECANCELED"}
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libhs.so")
@@ -143,7 +144,7 @@ def sig_bytes(params):
 
 def hs_keygen(params, seeds, pk=None, sk=None, stream=None):
     """(pk, sk) for each 3n-byte seed row of ``seeds`` (uint8 [count, 3n])."""
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
     count = seeds.shape[0] if seeds.ndim == 2 else seeds.shape[0] // (3 * n)
     pk = _like(seeds, count * 2 * n, np.uint8, "uint8") if pk is None else pk
     sk = _like(seeds, count * 4 * n, np.uint8, "uint8") if sk is None else sk
@@ -154,7 +155,7 @@ def hs_keygen(params, seeds, pk=None, sk=None, stream=None):
 def hs_sign_batch(params, sk, msgs, lens, key_idx=None, sigs=None, num_keys=None, stream=None):
     """Signatures (uint8 [count, SIG]) of the packed messages ``msgs`` with lengths ``lens``."""
     count = int(lens.shape[0])
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
     if num_keys is None:
         num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
     S = sig_bytes(params)
@@ -180,7 +181,7 @@ def hs_slh_sign_batch(params, sk, msgs, lens, ctx=b"", key_idx=None, sigs=None, 
     """FIPS 205 SLH-DSA signatures (deterministic) of every message under one
     context string; ctx=None signs the messages as given (internal function)."""
     count = int(lens.shape[0])
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
     if num_keys is None:
         num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
     S = sig_bytes(params)
@@ -195,7 +196,7 @@ def hs_slh_sign_batch(params, sk, msgs, lens, ctx=b"", key_idx=None, sigs=None, 
 def hs_slh_verify_batch(params, pk, msgs, lens, sigs, ctx=b"", key_idx=None, ok=None, num_keys=None, stream=None):
     """1/0 per FIPS 205 signature under one context string."""
     count = int(lens.shape[0])
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
     if num_keys is None:
         num_keys = (pk.shape[0] if pk.ndim == 2 else pk.shape[0] // (2 * n))
     ok = _like(lens, count, np.uint8, "uint8") if ok is None else ok
@@ -213,7 +214,7 @@ class KeySet:
 
     def __init__(self, params, sk, cache_layers=0, stream=None):
         L = load()
-        n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+        n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
         self.params = params
         self.num_keys = int(sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
         h = C.c_void_p()
@@ -256,7 +257,7 @@ class KeySet:
 def hs_verify_batch(params, pk, msgs, lens, sigs, key_idx=None, ok=None, num_keys=None, stream=None):
     """1/0 per signature (uint8 [count])."""
     count = int(lens.shape[0])
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
     if num_keys is None:
         num_keys = (pk.shape[0] if pk.ndim == 2 else pk.shape[0] // (2 * n))
     ok = _like(lens, count, np.uint8, "uint8") if ok is None else ok
@@ -301,7 +302,7 @@ def hs_sign_batch_noalloc(params, sk, msgs, lens, sigs, key_idx=None, num_keys=N
     all buffers (including the output ``sigs``) are caller-provided device
     tensors, and the library works in its fixed 8 MiB device buffer."""
     count = int(lens.shape[0])
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16][params]
+    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
     if num_keys is None:
         num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
     _check(load().hs_sign_batch_noalloc(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), _ptr(msgs),
@@ -334,7 +335,7 @@ def hs_sign_mixed(jobs, use_graph=True, stream=None):
     arr = (SignJob * len(jobs))()
     for j, jb in enumerate(jobs):
         ps = jb["params"]
-        n = N_BYTES[ps] if isinstance(ps, str) else [16, 24, 32, 16][ps]
+        n = N_BYTES[ps] if isinstance(ps, str) else [16, 24, 32, 16, 16, 24, 32][ps]
         sk = jb["sk"]
         nk = jb.get("num_keys") or (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
         msgs = _nonempty(jb["msgs"], jb["lens"])
@@ -364,8 +365,8 @@ class Server:
     def __init__(self, keys, max_inflight=4, max_batch=1024, mem_budget=8 << 30, pinned=0, cache_layers=0):
         L = load()
         self._keepalive = []
-        sks = (C.c_void_p * 4)()
-        nk = (C.c_uint32 * 4)()
+        sks = (C.c_void_p * NUM_PARAMS)()
+        nk = (C.c_uint32 * NUM_PARAMS)()
         for ps, sk in keys.items():
             pid = PARAMS[ps]
             self._keepalive.append(sk)
@@ -460,7 +461,7 @@ class Server:
             pass
 
 
-SIG_BY_ID = {0: 17088, 1: 35664, 2: 49856, 3: 1456}
+SIG_BY_ID = {0: 17088, 1: 35664, 2: 49856, 3: 1456, 4: 7856, 5: 16224, 6: 29792}
 
 
 def hs_set_tree_sharing(on=True):

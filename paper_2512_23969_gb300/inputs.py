@@ -14,7 +14,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-N_BYTES = {"128f": 16, "192f": 24, "256f": 32, "toy": 16}
+N_BYTES = {"128f": 16, "192f": 24, "256f": 32, "toy": 16, "128s": 16, "192s": 24, "256s": 32}
 BASE_SEED = 23969
 
 
