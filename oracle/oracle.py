@@ -13,6 +13,9 @@ PARAM_IDS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3, "128s": 4, "192s": 5, "2
              # the same sets in FIPS 205 mode (MSB-first FORS indices)
              "slh-128f": 16, "slh-192f": 17, "slh-256f": 18, "slh-toy": 19,
              "slh-128s": 20, "slh-192s": 21, "slh-256s": 22}
+# the SHAKE instantiation of each set: id + 32 ("shake-128f", "slh-shake-128f", ...)
+PARAM_IDS.update({"shake-" + k: v + 32 for k, v in list(PARAM_IDS.items()) if not k.startswith("slh-")})
+PARAM_IDS.update({"slh-shake-" + k[4:]: v + 32 for k, v in list(PARAM_IDS.items()) if k.startswith("slh-")})
 
 _lib = None
 
@@ -67,6 +70,8 @@ def lib():
         L.oracle_slh_verify.argtypes = [C.c_int, C.c_char_p, C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t,
                                         C.c_char_p]
         L.oracle_counters.argtypes = [C.POINTER(C.c_uint64), C.c_int]
+        L.oracle_shake256.argtypes = [C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t]
+        L.oracle_keccak_f1600.argtypes = [C.POINTER(C.c_uint64)]
         for name in ("oracle_params", "oracle_thash", "oracle_wots_digits", "oracle_hash_message",
                      "oracle_split_digest", "oracle_wots_chain", "oracle_wots_sk", "oracle_wots_pkgen",
                      "oracle_wots_sign", "oracle_wots_pk_from_sig", "oracle_xmss_node",
@@ -328,6 +333,19 @@ def slh_sign(ps, sk: bytes, ctx: bytes, m: bytes) -> bytes:
 
 def slh_verify(ps, pk: bytes, ctx: bytes, m: bytes, sig: bytes) -> bool:
     return _check(lib().oracle_slh_verify(_pid(ps), pk, ctx, len(ctx), m, len(m), sig)) == 1
+
+
+def shake256(m: bytes, outlen: int) -> bytes:
+    out = C.create_string_buffer(max(outlen, 1))
+    lib().oracle_shake256(m, len(m), out, outlen)
+    return out.raw[:outlen]
+
+
+def keccak_f1600(lanes):
+    """One Keccak-f[1600] permutation of 25 little-endian 64-bit lanes A[x + 5y]."""
+    st = (C.c_uint64 * 25)(*lanes)
+    lib().oracle_keccak_f1600(st)
+    return list(st)
 
 
 def counters(reset=False):

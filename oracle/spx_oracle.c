@@ -24,6 +24,14 @@
  * fully assembled input (no midstates), recursive Merkle node() with no
  * caching, and separately written verify climbs.  Nothing here is tuned.
  *
+ * SHAKE instantiation (parameter id + 32; a variant): every tweakable hash
+ * is SHAKE256(PK.seed || ADRS || payload, 8n) with the full 32-byte ADRS,
+ * PRF_msg = SHAKE256(SK.prf || opt_rand || M, 8n) and
+ * H_msg = SHAKE256(R || PK.seed || PK.root || M, 8m) (SPHINCS+ round 3.1
+ * SHAKE-simple; FIPS 205 Sec. 11.1).  Keccak-f[1600] is written from
+ * FIPS 202 Sec. 3: round constants come from its LFSR (Algorithm 5) and the
+ * rotation offsets from its (x, y) walk (Algorithm 2), not from tables.
+ *
  * FIPS 205 mode (parameter id + 16): SLH-DSA's two departures from the
  * round-3.1 scheme, stated in FIPS 205 -- the FORS indices are the base-2^a
  * digits of md read most significant bit first (its base_2b), and the pure
@@ -60,17 +68,20 @@ typedef struct {
     int md_bytes, tree_bytes, leaf_bytes, m;
     int tree_bits, leaf_bits;
     int fips;   /* 1: FORS indices in FIPS 205 order (MSB first)        */
+    int shake;  /* 1: SHAKE256 tweakable hashes instead of SHA-2         */
     size_t fors_bytes, sig_bytes;
 } spx_params;
 
 /* ids: 0 = 128f, 1 = 192f, 2 = 256f, 3 = toy (n=16,h=4,d=2,h'=2,a=3,k=4),
  * 4 = 128s, 5 = 192s, 6 = 256s (the scheme's small-signature sets, a
- * variant the paper does not use); + 16 = the same set in FIPS 205 mode */
+ * variant the paper does not use); + 16 = the same set in FIPS 205 mode,
+ * + 32 = its SHAKE instantiation */
 static int params_init(int id, spx_params *p)
 {
     memset(p, 0, sizeof(*p));
-    if (id < 0 || id > 31) return -1;
-    p->fips = id >> 4;
+    if (id < 0 || id > 63) return -1;
+    p->fips = (id >> 4) & 1;
+    p->shake = (id >> 5) & 1;
     switch (id & 15) {
     case 0: p->n = 16; p->h = 66; p->d = 22; p->a = 6; p->k = 33; break;
     case 1: p->n = 24; p->h = 66; p->d = 22; p->a = 8; p->k = 33; break;
@@ -313,6 +324,112 @@ static void mgf1_shax(int big, const uint8_t *seed, size_t seedlen, uint8_t *out
 }
 
 /* ------------------------------------------------------------------------ */
+/* Keccak-f[1600] and SHAKE256 (FIPS 202)                                    */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t rotl64(uint64_t x, int r)
+{
+    r &= 63;
+    return r ? (x << r) | (x >> (64 - r)) : x;
+}
+
+/* rc(t) of FIPS 202 Algorithm 5: the output bit of an 8-bit LFSR. */
+static int keccak_rc(int t)
+{
+    uint32_t R = 1;   /* R = 10000000 with bit 0 first */
+    int i;
+    if (t % 255 == 0) return 1;
+    for (i = 1; i <= t % 255; i++) {
+        uint32_t b8;
+        R <<= 1;                              /* R = 0 || R */
+        b8 = (R >> 8) & 1;
+        R ^= b8 | (b8 << 4) | (b8 << 5) | (b8 << 6);   /* R[0,4,5,6] ^= R[8] */
+        R &= 0xFF;
+    }
+    return (int)(R & 1);
+}
+
+/* Round constants and rotation offsets, derived once per thread by the
+ * definitions above (not typed in). */
+static _Thread_local int g_keccak_ready;
+static _Thread_local uint64_t g_keccak_rc[24];
+static _Thread_local int g_keccak_off[25];
+
+static void keccak_tables(void)
+{
+    int x, y, t, ir, j;
+    /* rho offsets: (x, y) walks from (1, 0); lane t is rotated by (t+1)(t+2)/2 */
+    g_keccak_off[0] = 0;
+    x = 1; y = 0;
+    for (t = 0; t < 24; t++) {
+        int nx = y, ny = (2 * x + 3 * y) % 5;
+        g_keccak_off[x + 5 * y] = ((t + 1) * (t + 2) / 2) % 64;
+        x = nx; y = ny;
+    }
+    /* iota: bit 2^j - 1 of RC[ir] is rc(j + 7 ir) */
+    for (ir = 0; ir < 24; ir++) {
+        g_keccak_rc[ir] = 0;
+        for (j = 0; j <= 6; j++)
+            if (keccak_rc(j + 7 * ir)) g_keccak_rc[ir] |= (uint64_t)1 << ((1 << j) - 1);
+    }
+    g_keccak_ready = 1;
+}
+
+/* A[x + 5 y], lanes as little-endian 64-bit integers. */
+static void keccak_f1600(uint64_t A[25])
+{
+    int x, y, ir;
+    const int *off = g_keccak_off;
+    if (!g_keccak_ready) keccak_tables();
+    for (ir = 0; ir < 24; ir++) {
+        uint64_t C[5], D[5], B[25];
+        for (x = 0; x < 5; x++) C[x] = A[x] ^ A[x + 5] ^ A[x + 10] ^ A[x + 15] ^ A[x + 20];
+        for (x = 0; x < 5; x++) D[x] = C[(x + 4) % 5] ^ rotl64(C[(x + 1) % 5], 1);
+        for (x = 0; x < 5; x++)
+            for (y = 0; y < 5; y++) A[x + 5 * y] ^= D[x];
+        /* rho then pi: B[x, y] = rot(A[(x + 3y) mod 5, x]) */
+        for (x = 0; x < 5; x++)
+            for (y = 0; y < 5; y++) {
+                int sx = (x + 3 * y) % 5, sy = x;
+                B[x + 5 * y] = rotl64(A[sx + 5 * sy], off[sx + 5 * sy]);
+            }
+        /* chi */
+        for (x = 0; x < 5; x++)
+            for (y = 0; y < 5; y++)
+                A[x + 5 * y] = B[x + 5 * y] ^ (~B[(x + 1) % 5 + 5 * y] & B[(x + 2) % 5 + 5 * y]);
+        A[0] ^= g_keccak_rc[ir];   /* iota */
+    }
+}
+
+/* SHAKE256(M, 8 outlen): rate 136 bytes, domain bits 1111 then pad10*1. */
+static void shake256(const uint8_t *in, size_t inlen, uint8_t *out, size_t outlen)
+{
+    uint64_t A[25];
+    const size_t rate = 136;
+    size_t i, off = 0;
+    memset(A, 0, sizeof(A));
+    for (;;) {
+        size_t take = inlen - off < rate ? inlen - off : rate;
+        for (i = 0; i < take; i++) A[i / 8] ^= (uint64_t)in[off + i] << (8 * (i % 8));
+        off += take;
+        if (take < rate) {
+            A[take / 8] ^= (uint64_t)0x1F << (8 * (take % 8));
+            A[(rate - 1) / 8] ^= (uint64_t)0x80 << (8 * ((rate - 1) % 8));
+            keccak_f1600(A);
+            break;
+        }
+        keccak_f1600(A);
+    }
+    for (off = 0;;) {
+        size_t take = outlen - off < rate ? outlen - off : rate;
+        for (i = 0; i < take; i++) out[off + i] = (uint8_t)(A[i / 8] >> (8 * (i % 8)));
+        off += take;
+        if (off == outlen) break;
+        keccak_f1600(A);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* ADRS (32-byte address) and its 22-byte compressed form ADRSc             */
 /* ------------------------------------------------------------------------ */
 
@@ -351,6 +468,13 @@ static void adrs_compress(const adrs_t *A, uint8_t out[22])
     put_be32(out + 18, A->w[7]);
 }
 
+/* The full 32-byte ADRS: the eight words big-endian. */
+static void adrs_full(const adrs_t *A, uint8_t out[32])
+{
+    int i;
+    for (i = 0; i < 8; i++) put_be32(out + 4 * i, A->w[i]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Keys and tweakable hashes                                                 */
 /* ------------------------------------------------------------------------ */
@@ -366,6 +490,17 @@ static void thash(const spx_ctx *c, int big, const adrs_t *A,
                   const uint8_t *in, size_t inlen, uint8_t *out)
 {
     size_t B = big ? 128 : 64;
+    if (c->p.shake) {
+        /* SHAKE-simple: SHAKE256(PK.seed || ADRS || in, 8n) */
+        size_t n = (size_t)c->p.n;
+        uint8_t *sb = (uint8_t *)malloc(n + 32 + inlen);
+        memcpy(sb, c->pk_seed, n);
+        adrs_full(A, sb + n);
+        memcpy(sb + n + 32, in, inlen);
+        shake256(sb, n + 32 + inlen, out, n);
+        free(sb);
+        return;
+    }
     uint8_t *buf = (uint8_t *)malloc(B + 22 + inlen);
     uint8_t dig[64];
     memset(buf, 0, B);
@@ -403,6 +538,16 @@ static void prf_addr(const spx_ctx *c, const adrs_t *A, uint8_t *out)
 static void prf_msg(const spx_ctx *c, const uint8_t *opt, const uint8_t *m, size_t mlen, uint8_t *R)
 {
     uint8_t mac[64];
+    if (c->p.shake) {   /* SHAKE256(SK.prf || opt_rand || M, 8n) */
+        size_t n = (size_t)c->p.n;
+        uint8_t *sb = (uint8_t *)malloc(2 * n + mlen + 1);
+        memcpy(sb, c->sk_prf, n);
+        memcpy(sb + n, opt, n);
+        if (mlen) memcpy(sb + 2 * n, m, mlen);
+        shake256(sb, 2 * n + mlen, R, n);
+        free(sb);
+        return;
+    }
     hmac_shax(c->p.big, c->sk_prf, c->p.n, opt, c->p.n, m, mlen, mac);
     memcpy(R, mac, c->p.n);
 }
@@ -416,6 +561,11 @@ static void hash_msg(const spx_ctx *c, const uint8_t *R, const uint8_t *m, size_
     uint8_t *buf = (uint8_t *)malloc(3 * (size_t)n + mlen + 1);
     uint8_t inner[64], seed[32 + 32 + 64];
     size_t off = cat4(buf, 3 * (size_t)n + mlen + 1, R, n, c->pk_seed, n, c->pk_root, n, m, mlen);
+    if (c->p.shake) {   /* SHAKE256(R || PK.seed || PK.root || M, 8m) */
+        shake256(buf, off, digest, (size_t)c->p.m);
+        free(buf);
+        return;
+    }
     shax(big, buf, off, inner);
     free(buf);
     off = cat4(seed, sizeof(seed), R, n, c->pk_seed, n, inner, D, NULL, 0);
@@ -828,6 +978,9 @@ SPX_EXPORT int oracle_params(int pid, int64_t *info)
 
 SPX_EXPORT void oracle_sha256(const uint8_t *m, size_t len, uint8_t *out) { sha256(m, len, out); }
 SPX_EXPORT void oracle_sha512(const uint8_t *m, size_t len, uint8_t *out) { sha512(m, len, out); }
+SPX_EXPORT void oracle_shake256(const uint8_t *m, size_t len, uint8_t *out, size_t outlen)
+{ shake256(m, len, out, outlen); }
+SPX_EXPORT void oracle_keccak_f1600(uint64_t *state25) { keccak_f1600(state25); }
 SPX_EXPORT void oracle_hmac(int big, const uint8_t *key, size_t keylen, const uint8_t *m, size_t len, uint8_t *out)
 { hmac_shax(big, key, keylen, m, len, NULL, 0, out); }
 SPX_EXPORT void oracle_mgf1(int big, const uint8_t *seed, size_t seedlen, uint8_t *out, size_t outlen)

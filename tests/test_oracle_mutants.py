@@ -37,8 +37,8 @@ MUTANTS = [
     ("adrs tree words swapped", "put_be32(out + 1, A->w[2]);\n    put_be32(out + 5, A->w[3]);",
      "put_be32(out + 1, A->w[3]);\n    put_be32(out + 5, A->w[2]);", False),
     ("T_len drops the last chain", "hash_T(c, &A, ends, c->p.len, pk);", "hash_T(c, &A, ends, c->p.len - 1, pk);", False),
-    ("blockpad always 64 bytes", "size_t B = big ? 128 : 64;\n    uint8_t *buf = (uint8_t *)malloc(B + 22 + inlen);",
-     "size_t B = 64;\n    uint8_t *buf = (uint8_t *)malloc(B + 22 + inlen);", False),
+    ("blockpad always 64 bytes", "size_t B = big ? 128 : 64;\n    if (c->p.shake) {",
+     "size_t B = 64;\n    if (c->p.shake) {", False),
     ("H always SHA-256", "thash(c, c->p.big, A, buf, 2 * (size_t)c->p.n, out);", "thash(c, 0, A, buf, 2 * (size_t)c->p.n, out);", False),
     ("PRF uses SHA-512 when big", "g_calls_prf++; thash(c, 0, A,", "g_calls_prf++; thash(c, c->p.big, A,", False),
     ("checksum not shifted", "csum <<= (8 - (p->len2 * 4) % 8) % 8;", "", False),
@@ -66,6 +66,18 @@ MUTANTS = [
      "idx[i] = (uint32_t)(acc & (((uint64_t)1 << p->a) - 1)); acc >>= p->a;", False),
     ("FIPS prefix domain byte", "w[0] = 0;", "w[0] = 1;", False),
     ("FIPS context length byte dropped", "w[1] = (uint8_t)ctxlen;", "w[1] = 0;", False),
+    ("Keccak rho offset walk", "int nx = y, ny = (2 * x + 3 * y) % 5;", "int nx = y, ny = (3 * x + 2 * y) % 5;", False),
+    ("Keccak pi source lane", "int sx = (x + 3 * y) % 5, sy = x;", "int sx = (3 * x + y) % 5, sy = x;", False),
+    ("Keccak chi operand order", "B[x + 5 * y] ^ (~B[(x + 1) % 5 + 5 * y] & B[(x + 2) % 5 + 5 * y])",
+     "B[x + 5 * y] ^ (B[(x + 1) % 5 + 5 * y] & ~B[(x + 2) % 5 + 5 * y])", False),
+    ("Keccak iota bit position", "g_keccak_rc[ir] |= (uint64_t)1 << ((1 << j) - 1);",
+     "g_keccak_rc[ir] |= (uint64_t)1 << (1 << j);", False),
+    ("SHAKE domain padding", "A[take / 8] ^= (uint64_t)0x1F << (8 * (take % 8));",
+     "A[take / 8] ^= (uint64_t)0x06 << (8 * (take % 8));", False),
+    ("SHAKE full ADRS word order", "for (i = 0; i < 8; i++) put_be32(out + 4 * i, A->w[i]);",
+     "for (i = 0; i < 8; i++) put_be32(out + 4 * i, A->w[7 - i]);", False),
+    ("SHAKE PRF_msg operand order", "memcpy(sb, c->sk_prf, n);\n        memcpy(sb + n, opt, n);",
+     "memcpy(sb, opt, n);\n        memcpy(sb + n, c->sk_prf, n);", False),
 ]
 
 
@@ -161,6 +173,15 @@ def _pins_fail(O):
             mp = b"\x00" + bytes([len(ctx)]) + ctx + b"m"
             if O.slh_sign("toy", skt, ctx, b"m") != toy.sign_fields(*fields(P, skt, mp)):
                 return "FIPS pure sign"
+        from test_oracle_shake import ToyShake
+        for L in (0, 135, 136, 300):
+            m = bytes(rng.getrandbits(8) for _ in range(L))
+            if O.shake256(m, 200) != hashlib.shake_256(m).digest(200):
+                return "shake256 vs hashlib"
+        ts = ToyShake(bytes(range(48)))
+        pks, sks = O.keygen("shake-toy", bytes(range(48)))
+        if pks != ts.pk_seed + ts.pk_root() or O.sign("shake-toy", sks, b"mm") != ts.sign(b"mm"):
+            return "shake toy"
         pk1, sk1 = O.keygen("128f", bytes(range(48)))
         s = O.sign("128f", sk1, b"x")
         if not O.verify("128f", pk1, b"x", s):
