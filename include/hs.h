@@ -49,12 +49,17 @@ extern "C" {
  * the scheme's small-signature sets (a variant the paper does not use):
  * (n, h, d, h', a, k) = (16, 63, 7, 9, 12, 14), (24, 63, 7, 9, 14, 17),
  * (32, 64, 8, 8, 14, 22); 7856 / 16224 / 29792-byte signatures.  Tree
- * sharing and keyset caches are not offered for them. */
+ * sharing and keyset caches are not offered for them.  HS_SHAKE_* are the
+ * SHAKE256 instantiations of the six sets (SPHINCS+ SHAKE-simple, FIPS 205
+ * Sec. 11.1): same sizes and key layout, every hash SHAKE256 with the full
+ * 32-byte address; another variant the paper does not use. */
 typedef enum {
     HS_128F = 0, HS_192F = 1, HS_256F = 2, HS_TOY = 3,
-    HS_128S = 4, HS_192S = 5, HS_256S = 6
+    HS_128S = 4, HS_192S = 5, HS_256S = 6,
+    HS_SHAKE_128F = 7, HS_SHAKE_192F = 8, HS_SHAKE_256F = 9,
+    HS_SHAKE_128S = 10, HS_SHAKE_192S = 11, HS_SHAKE_256S = 12
 } hs_params;
-#define HS_NUM_PARAMS 7
+#define HS_NUM_PARAMS 13
 
 typedef enum {
     HS_OK = 0,

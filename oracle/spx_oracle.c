@@ -1234,7 +1234,7 @@ SPX_EXPORT int oracle_slh_sign(int pid, const uint8_t *sk, const uint8_t *ctx, s
     size_t wl;
     uint8_t *w;
     int rc;
-    if (pid < 0 || pid > 15 || ctxlen > 255) return -1;
+    if (pid < 0 || pid > 47 || (pid & 16) || ctxlen > 255) return -1;   /* a base set, SHA2 or SHAKE */
     w = slh_wrap(ctx, ctxlen, m, mlen, &wl);
     if (!w) return -1;
     rc = oracle_sign(pid + 16, sk, w, wl, sig);
@@ -1248,7 +1248,7 @@ SPX_EXPORT int oracle_slh_verify(int pid, const uint8_t *pk, const uint8_t *ctx,
     size_t wl;
     uint8_t *w;
     int rc;
-    if (pid < 0 || pid > 15 || ctxlen > 255) return -1;
+    if (pid < 0 || pid > 47 || (pid & 16) || ctxlen > 255) return -1;
     w = slh_wrap(ctx, ctxlen, m, mlen, &wl);
     if (!w) return -1;
     rc = oracle_verify(pid + 16, pk, w, wl, sig);

@@ -14,17 +14,29 @@ const SetOps* set_ops(int pset) {
     case 4: return &kOps_128S;
     case 5: return &kOps_192S;
     case 6: return &kOps_256S;
+    case 7: return &kOps_K128F;
+    case 8: return &kOps_K192F;
+    case 9: return &kOps_K256F;
+    case 10: return &kOps_K128S;
+    case 11: return &kOps_K192S;
+    case 12: return &kOps_K256S;
     }
     return nullptr;
 }
 
 namespace {
 // -1 = not set: use the table's default.
-std::atomic<int> g_tune[kNumSets][3] = {{{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}},
-                                        {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}},
-                                        {{-1}, {-1}, {-1}}};
+struct TuneSlots {
+    std::atomic<int> v[kNumSets][3];
+    TuneSlots() {
+        for (auto& row : v)
+            for (auto& x : row) x.store(-1);
+    }
+};
+TuneSlots g_slots;
+auto& g_tune = g_slots.v;
 // Default batch size below which TREE_Sign runs chain-parallel, per set.
-constexpr int kSplitDefault[kNumSets] = {8192, 2048, 4096, 0, 64, 64, 64};
+constexpr int kSplitDefault[kNumSets] = {8192, 2048, 4096, 0, 64, 64, 64, 8192, 2048, 4096, 64, 64, 64};
 }
 
 int tune_get(int pset, int knob) {

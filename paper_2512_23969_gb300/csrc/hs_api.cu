@@ -50,6 +50,12 @@ static bool set_info(int p, SetInfo* s) {
     case 4: *s = HS_SETINFO(P128s); return true;
     case 5: *s = HS_SETINFO(P192s); return true;
     case 6: *s = HS_SETINFO(P256s); return true;
+    case 7: *s = HS_SETINFO(PK128f); return true;
+    case 8: *s = HS_SETINFO(PK192f); return true;
+    case 9: *s = HS_SETINFO(PK256f); return true;
+    case 10: *s = HS_SETINFO(PK128s); return true;
+    case 11: *s = HS_SETINFO(PK192s); return true;
+    case 12: *s = HS_SETINFO(PK256s); return true;
     }
 #undef HS_SETINFO
     return false;

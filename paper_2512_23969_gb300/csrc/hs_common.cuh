@@ -11,28 +11,13 @@
 // 2-byte offset inside a word; mid16() builds the straddling words.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include "hs_params.cuh"
 #include "sha2.cuh"
+#include "adrs.cuh"
+#include "keccak.cuh"
 
 namespace hs {
-
-// Compressed address ADRSc as five full message words plus the 16-bit half
-// word that precedes the payload: layer(1) tree(8) type(1) w5(4) w6(4) w7(4).
-struct Adrs {
-    uint32_t w0, w1, w2, w3, w4, half;
-};
-
-__device__ __forceinline__ Adrs make_adrs(uint32_t layer, uint64_t tree, uint32_t type,
-                                          uint32_t kp, uint32_t w6, uint32_t w7) {
-    Adrs a;
-    a.w0 = (layer << 24) | (uint32_t)(tree >> 40);
-    a.w1 = (uint32_t)(tree >> 8);
-    a.w2 = ((uint32_t)tree << 24) | (type << 16) | (kp >> 16);
-    a.w3 = (kp << 16) | (w6 >> 16);
-    a.w4 = (w6 << 16) | (w7 >> 16);
-    a.half = w7 & 0xFFFFu;
-    return a;
-}
 
 // Fill the words of one message block after the midstate: ADRSc, payload of
 // PW words, 0x80 pad byte; zero the rest (length added by the caller).
@@ -78,22 +63,26 @@ __device__ __forceinline__ void thash512(const uint32_t ms[16], const Adrs& a, c
 }
 
 // F / PRF: always SHA-256 over an n-byte payload (chain steps use FULL).
+// (SHAKE sets: ms256 holds PK.seed and the hash is SHAKE256, keccak.cuh.)
 template <class P, bool FULL = true>
 __device__ __forceinline__ void hashF(const uint32_t ms256[8], const Adrs& a, const uint32_t* x, uint32_t* out) {
-    thash256<P::NW, P::NW, FULL>(ms256, a, x, out);
+    if constexpr (P::SHAKE) shake_thash1<P::NW, P::NW>(ms256, a, x, out);
+    else thash256<P::NW, P::NW, FULL>(ms256, a, x, out);
 }
 
 // H: two n-byte children; SHA-512 for n > 16.
 template <class P>
 __device__ __forceinline__ void hashH(const KeyBlock& kb, const Adrs& a, const uint32_t* lr, uint32_t* out) {
-    if constexpr (P::BIG) thash512<2 * P::NW, P::NW>(kb.ms512, a, lr, out);
+    if constexpr (P::SHAKE) shake_thash1<P::NW, 2 * P::NW>(kb.ms256, a, lr, out);
+    else if constexpr (P::BIG) thash512<2 * P::NW, P::NW>(kb.ms512, a, lr, out);
     else thash256<2 * P::NW, P::NW, false>(kb.ms256, a, lr, out);
 }
 // Same, with the midstates passed separately (kernels that keep them in registers).
 template <class P>
 __device__ __forceinline__ void hashH_ms(const uint32_t* ms256, const uint32_t* ms512, const Adrs& a,
                                          const uint32_t* lr, uint32_t* out) {
-    if constexpr (P::BIG) thash512<2 * P::NW, P::NW>(ms512, a, lr, out);
+    if constexpr (P::SHAKE) shake_thash1<P::NW, 2 * P::NW>(ms256, a, lr, out);
+    else if constexpr (P::BIG) thash512<2 * P::NW, P::NW>(ms512, a, lr, out);
     else thash256<2 * P::NW, P::NW, false>(ms256, a, lr, out);
 }
 
@@ -157,6 +146,12 @@ struct TStream {
         for (int i = 0; i < NW; i++) out[i] = st[i];
     }
 };
+
+// T_l stream of a parameter set: SHA-2 as above, or SHAKE256 (whose init
+// takes PK.seed where the SHA-2 stream takes the midstate).
+template <class P>
+using TStreamP = std::conditional_t<P::SHAKE, ShakeStream<P::NW, (P::LEN > P::K ? P::LEN : P::K) * P::NW>,
+                                    TStream<P::BIG>>;
 
 // ------------------------------------------------------------ byte I/O
 

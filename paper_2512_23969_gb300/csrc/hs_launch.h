@@ -112,7 +112,10 @@ struct SetOps {
     int tree_minb_default;
 };
 extern const SetOps kOps_128F, kOps_192F, kOps_256F, kOps_Toy, kOps_128S, kOps_192S, kOps_256S;
-constexpr int kNumSets = 7;   // 128f, 192f, 256f, toy, 128s, 192s, 256s
+extern const SetOps kOps_K128F, kOps_K192F, kOps_K256F, kOps_K128S, kOps_K192S, kOps_K256S;
+// 128f, 192f, 256f, toy, 128s, 192s, 256s, then the SHAKE instantiations of
+// 128f .. 256s
+constexpr int kNumSets = 13;
 
 // Shape of a parameter set for host code (false for an unknown id).
 struct SetShape { int n, d, sig, leaves; };

@@ -7,8 +7,10 @@ namespace hs {
 
 // N: hash bytes, H: hypertree height, D: layers, A: FORS height, K: FORS trees.
 // BIG: H, T_l, H_msg, PRF_msg use SHA-512 (n = 24 / 32).
-template <int N_, int H_, int D_, int A_, int K_>
+// SHAKE_: the SHAKE256 instantiation (a variant; the paper uses SHA-2).
+template <int N_, int H_, int D_, int A_, int K_, bool SHAKE_ = false>
 struct Params {
+    static constexpr bool SHAKE = SHAKE_;
     static constexpr int N = N_;
     static constexpr int H = H_;
     static constexpr int D = D_;
@@ -16,7 +18,7 @@ struct Params {
     static constexpr int A = A_;
     static constexpr int K = K_;
     static constexpr int W = 16;
-    static constexpr bool BIG = (N_ > 16);
+    static constexpr bool BIG = !SHAKE_ && (N_ > 16);
     static constexpr int NW = N_ / 4;              // n in 32-bit words
     static constexpr int LEN1 = 2 * N_;            // 8n / log2(w)
     static constexpr int LEN2 = 3;                 // all three sets (and toy)
@@ -41,6 +43,13 @@ using PToy  = Params<16, 4, 2, 3, 4>;
 using P128s = Params<16, 63, 7, 12, 14>;
 using P192s = Params<24, 63, 7, 14, 17>;
 using P256s = Params<32, 64, 8, 14, 22>;
+// The SHAKE instantiation of each of them.
+using PK128f = Params<16, 66, 22, 6, 33, true>;
+using PK192f = Params<24, 66, 22, 8, 33, true>;
+using PK256f = Params<32, 68, 17, 9, 35, true>;
+using PK128s = Params<16, 63, 7, 12, 14, true>;
+using PK192s = Params<24, 63, 7, 14, 17, true>;
+using PK256s = Params<32, 64, 8, 14, 22, true>;
 
 static_assert(P128f::SIG_BYTES == 17088, "128f signature size");
 static_assert(P192f::SIG_BYTES == 35664, "192f signature size");

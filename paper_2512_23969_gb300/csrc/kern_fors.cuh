@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
             for (int w = 0; w < NW; w++) node[w] = skseed[w];
 #pragma unroll 1
             for (int s = 0; s < 2; s++) {
-                hashF_fast<POL, NW>(ms256, make_adrs(0, tree, s == 0 ? T_FORS_PRF : T_FORS_TREE, kp, 0, g), node,
-                                    node, pp);
+                hashF_p<P, POL>(ms256, make_adrs(0, tree, s == 0 ? T_FORS_PRF : T_FORS_TREE, kp, 0, g), node,
+                                node, pp);
                 if (s == 0 && t == gs) store_be<NW>(sf, node);
             }
             if (t == (gs ^ 1u)) store_be<NW>(sf + P::N, node);
@@ -176,7 +176,7 @@ __global__ void fors_pk_kernel(const KeyBlock* __restrict__ keys, const MsgInfo*
     if (info.key == KEY_INVALID) return;
     const KeyBlock& kb = keys[info.key];
     constexpr int NW = P::NW;
-    TStream<P::BIG> ts;
+    TStreamP<P> ts;
     ts.init(P::BIG ? kb.ms512 : kb.ms256, make_adrs(0, info.idx_tree, T_FORS_ROOTS, info.idx_leaf, 0, 0));
     const uint32_t* r = fors_roots + (size_t)m * P::K * NW;
     for (int i = 0; i < P::K; i++) ts.template push_n<NW>(r + i * NW);

@@ -145,7 +145,9 @@ __global__ void keyprep_kernel(const uint8_t* __restrict__ in, uint32_t num_keys
         load_be_unaligned<NW>(p + 2 * P::N, kb.pk_seed);
         load_be_unaligned<NW>(p + 3 * P::N, kb.pk_root);
     }
-    {
+    if constexpr (P::SHAKE) {         // the SHAKE hashes take PK.seed itself
+        for (int i = 0; i < 8; i++) kb.ms256[i] = (i < NW) ? kb.pk_seed[i] : 0u;
+    } else {
         uint32_t W[16];
         for (int i = 0; i < 16; i++) W[i] = (i < NW) ? kb.pk_seed[i] : 0u;
         sha256_iv(kb.ms256);
@@ -202,6 +204,30 @@ __global__ void message_kernel(const KeyBlock* __restrict__ keys, uint32_t num_k
     const uint64_t mlen = off[m + 1] - off[m];
 
     uint32_t R[8];
+    uint32_t dg[16];                     // digest words, >= m bytes (m <= 49)
+    if constexpr (P::SHAKE) {
+        // PRF_msg = SHAKE256(SK.prf || opt_rand || M, 8n), H_msg =
+        // SHAKE256(R || PK.seed || PK.root || M, 8m); M may carry a prefix
+        ByteShake k;
+        if (!verify) {
+            k.init();
+            k.words(kb.sk_prf, P::N);
+            k.words(kb.pk_seed, P::N);
+            if (plen) k.mem(prefix, plen);
+            k.mem(M, mlen);
+            k.finish(R, P::N);
+            store_be<NW>(sig, R);
+        } else {
+            load_be<NW>(sig, R);
+        }
+        k.init();
+        k.words(R, P::N);
+        k.words(kb.pk_seed, P::N);
+        k.words(kb.pk_root, P::N);
+        if (plen) k.mem(prefix, plen);
+        k.mem(M, mlen);
+        k.finish(dg, P::M);
+    } else {
     ByteSha<P::BIG> h;
     if (!verify) {
         // PRF_msg = HMAC-SHA-x(SK.prf, opt_rand || M), opt_rand = PK.seed
@@ -239,7 +265,6 @@ __global__ void message_kernel(const KeyBlock* __restrict__ keys, uint32_t num_k
     if (plen) h.mem(prefix, plen);
     h.mem(M, mlen);
     h.finish(inner);
-    uint32_t dg[16];                     // >= m bytes (m <= 49)
     int got = 0;
     for (uint32_t c = 0; got < P::M; c++) {
         h.init();
@@ -250,6 +275,7 @@ __global__ void message_kernel(const KeyBlock* __restrict__ keys, uint32_t num_k
         uint32_t blockd[DW];
         h.finish(blockd);
         for (int i = 0; i < DW && got < P::M; i++, got += 4) dg[got >> 2] = blockd[i];
+    }
     }
     // md -> FORS indices: md read as a little-endian bit stream, index i from
     // stream bits i*a .. i*a+a-1, first bit least significant; in FIPS 205

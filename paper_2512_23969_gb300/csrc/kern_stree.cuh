@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(128) bleaf_from_ends_kernel(const KeyBlock* __
     if (info.key == KEY_INVALID) return;
     const KeyBlock& kb = keys[info.key];
     const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
-    TStream<P::BIG> ts;
+    TStreamP<P> ts;
     ts.init(P::BIG ? kb.ms512 : kb.ms256, make_adrs(j, tree, T_WOTS_PK, l, 0, 0));
     const uint32_t* e = ends + (size_t)gid * LEN * NW;
 #pragma unroll 1
@@ -166,7 +166,9 @@ __global__ void seed_keys_kernel(const uint8_t* __restrict__ seeds, uint32_t cou
     load_be_unaligned<NW>(sd, kb.sk_seed);
     load_be_unaligned<NW>(sd + P::N, kb.sk_prf);
     load_be_unaligned<NW>(sd + 2 * P::N, kb.pk_seed);
-    {
+    if constexpr (P::SHAKE) {         // the SHAKE hashes take PK.seed itself
+        for (int i = 0; i < 8; i++) kb.ms256[i] = (i < NW) ? kb.pk_seed[i] : 0u;
+    } else {
         uint32_t W[16];
         for (int i = 0; i < 16; i++) W[i] = (i < NW) ? kb.pk_seed[i] : 0u;
         sha256_iv(kb.ms256);

@@ -35,7 +35,7 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
                                           uint32_t layer, uint64_t tree, uint32_t kp, uint32_t* out,
                                           uint32_t* chk, uint32_t ck, const Pipes<POL>& pp) {
     constexpr int NW = P::NW;
-    TStream<P::BIG> ts;
+    TStreamP<P> ts;
     ts.init(msT, make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0));
     const Adrs aprf = make_adrs(layer, tree, T_WOTS_PRF, kp, 0, 0);
     const Adrs ahash = make_adrs(layer, tree, T_WOTS_HASH, kp, 0, 0);
@@ -50,12 +50,19 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
         // step s >= 1: F(WOTS_HASH(kp, chain i, hash s-1)) = position s.
 #pragma unroll 1
         for (uint32_t s = 0; s < 16; s++) {
-            if (s <= 1) {
+            if constexpr (P::SHAKE) {
                 Adrs a = (s == 0) ? aprf : ahash;
-                a.w4 = i << 16;                  // chain i (< 2^16) | hash >> 16 (= 0)
-                chain_ctx<POL>(ms256, a, cx, pp);
+                a.w4 = i << 16;
+                a.half = s == 0 ? 0u : s - 1u;
+                hashF_p<P, POL>(ms256, a, x, x, pp);
+            } else {
+                if (s <= 1) {
+                    Adrs a = (s == 0) ? aprf : ahash;
+                    a.w4 = i << 16;              // chain i (< 2^16) | hash >> 16 (= 0)
+                    chain_ctx<POL>(ms256, a, cx, pp);
+                }
+                chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, x, x, pp);
             }
-            chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, x, x, pp);
             if (chk != nullptr && (s % ck) == 0) {
                 uint32_t* d = chk + ((size_t)i * per_chain + s / ck) * NW;
 #pragma unroll
@@ -179,11 +186,16 @@ __global__ void __launch_bounds__(128) chains_kernel(const KeyBlock* __restrict_
     ChainCtx cx;
 #pragma unroll 1
     for (uint32_t s = 0; s < 16; s++) {
-        if (s <= 1) {
-            Adrs a = make_adrs(j, tree, s == 0 ? T_WOTS_PRF : T_WOTS_HASH, l, i, 0);
-            chain_ctx<POL>(ms256, a, cx, pp);
+        if constexpr (P::SHAKE) {
+            hashF_p<P, POL>(ms256, make_adrs(j, tree, s == 0 ? T_WOTS_PRF : T_WOTS_HASH, l, i, s == 0 ? 0u : s - 1u),
+                            x, x, pp);
+        } else {
+            if (s <= 1) {
+                Adrs a = make_adrs(j, tree, s == 0 ? T_WOTS_PRF : T_WOTS_HASH, l, i, 0);
+                chain_ctx<POL>(ms256, a, cx, pp);
+            }
+            chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, x, x, pp);
         }
-        chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, x, x, pp);
         if (mychk != nullptr && (s % ck) == 0) {
 #pragma unroll
             for (int w = 0; w < NW; w++) mychk[(s / ck) * NW + w] = x[w];
@@ -219,7 +231,7 @@ __global__ void __launch_bounds__(128) leaves_kernel(const KeyBlock* __restrict_
     for (int w = 0; w < (P::BIG ? 16 : 8); w++) msT[w] = P::BIG ? kb.ms512[w] : kb.ms256[w];
     const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
     const uint32_t sl = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
-    TStream<P::BIG> ts;
+    TStreamP<P> ts;
     ts.init(msT, make_adrs(j, tree, T_WOTS_PK, l, 0, 0));
     const uint32_t* e = ends + (size_t)gid * LEN * NW;
 #pragma unroll 1
@@ -247,7 +259,10 @@ __global__ void __launch_bounds__(128) keygen_kernel(const uint8_t* __restrict__
     load_be_unaligned<NW>(sd, skseed);
     load_be_unaligned<NW>(sd + 2 * N, pkseed);
     uint32_t ms256[8], msT[P::BIG ? 16 : 8];
-    {
+    if constexpr (P::SHAKE) {         // the SHAKE hashes take PK.seed itself
+#pragma unroll
+        for (int i = 0; i < 8; i++) ms256[i] = (i < NW) ? pkseed[i] : 0u;
+    } else {
         uint32_t W[16];
 #pragma unroll
         for (int i = 0; i < 16; i++) W[i] = (i < NW) ? pkseed[i] : 0u;

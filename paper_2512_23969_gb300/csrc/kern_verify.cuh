@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128) verify_kernel(const KeyBlock* __restrict_
     }
     __syncwarp();
     if (lane == 0) {
-        TStream<P::BIG> ts;
+        TStreamP<P> ts;
         ts.init(msT, make_adrs(0, info.idx_tree, T_FORS_ROOTS, info.idx_leaf, 0, 0));
         for (int i = 0; i < K; i++) ts.template push_n<NW>(buf + i * NW);
         uint32_t pkf[NW];
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(128) verify_kernel(const KeyBlock* __restrict_
         }
         __syncwarp();
         if (lane == 0) {
-            TStream<P::BIG> ts;
+            TStreamP<P> ts;
             ts.init(msT, make_adrs(j, tree, T_WOTS_PK, kp, 0, 0));
             for (int i = 0; i < LEN; i++) ts.template push_n<NW>(buf + i * NW);
             uint32_t node[NW];

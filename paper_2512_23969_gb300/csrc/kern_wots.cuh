@@ -80,17 +80,23 @@ __global__ void __launch_bounds__(256) wots_kernel(const KeyBlock* __restrict__ 
 #pragma unroll 1
         for (uint32_t q = base; q < digit; q++) {
             a.half = q;
-            hashF_fast<POL, NW>(ms256, a, x, x, pp);
+            hashF_p<P, POL>(ms256, a, x, x, pp);
         }
     } else {
 #pragma unroll
         for (int w = 0; w < NW; w++) x[w] = kb.sk_seed[w];
+        if constexpr (P::SHAKE) {
+            hashF_p<P, POL>(ms256, make_adrs(j, tree, T_WOTS_PRF, kp, i, 0), x, x, pp);
+#pragma unroll 1
+            for (uint32_t q = 0; q < digit; q++) hashF_p<P, POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, q), x, x, pp);
+        } else {
         ChainCtx cx;
         chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_PRF, kp, i, 0), cx, pp);
         chain_step<POL, NW>(cx, ms256, 0u, x, x, pp);
         if (digit > 0) chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, 0), cx, pp);
 #pragma unroll 1
         for (uint32_t q = 0; q < digit; q++) chain_step<POL, NW>(cx, ms256, q, x, x, pp);
+        }
     }
     store_be<NW>(sigs + m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES + (size_t)i * P::N, x);
 }

@@ -1,0 +1,32 @@
+// set_shake_128f.cu -- every kernel instantiated for SPHINCS+-SHAKE-128f
+// (the SHAKE256 instantiation: a variant beside the paper's SHA-2 sets),
+// with the launch-shape variants the tuner may pick from.
+#include "set_impl.cuh"
+
+namespace hs {
+namespace {
+using P = PK128f;
+const int kForsLpt[] = {2, 4, 8};
+const int kTreeMinb[] = {0};
+
+cudaError_t fors_variant(const Batch& b, int lpt, cudaStream_t s) {
+    switch (lpt) {
+    case 2: return SetImpl<P>::fors<2>(b, s);
+    case 4: return SetImpl<P>::fors<4>(b, s);
+    case 8: return SetImpl<P>::fors<8>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tree_variant(const Batch& b, int minb, cudaStream_t s) {
+    return minb == 0 ? SetImpl<P>::tree<1>(b, s) : cudaErrorInvalidValue;
+}
+}  // namespace
+
+extern const SetOps kOps_K128F = {
+    SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk, tree_variant,
+    SetImpl<P>::tree_split, SetImpl<P>::tree_dedup, SetImpl<P>::tree_cached, SetImpl<P>::cache_build,
+    SetImpl<P>::wots,       SetImpl<P>::verify,     SetImpl<P>::keygen,
+    kForsLpt, 3, 2, kTreeMinb, 1, 0};
+
+}  // namespace hs

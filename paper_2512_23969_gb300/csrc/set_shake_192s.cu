@@ -1,0 +1,31 @@
+// set_shake_192s.cu -- every kernel instantiated for SPHINCS+-SHAKE-192s
+// (the SHAKE256 instantiation: a variant beside the paper's SHA-2 sets),
+// with the launch-shape variants the tuner may pick from.
+#include "set_impl.cuh"
+
+namespace hs {
+namespace {
+using P = PK192s;
+const int kForsLpt[] = {16, 32};
+const int kTreeMinb[] = {0};
+
+cudaError_t fors_variant(const Batch& b, int lpt, cudaStream_t s) {
+    switch (lpt) {
+    case 16: return SetImpl<P>::fors<16>(b, s);
+    case 32: return SetImpl<P>::fors<32>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tree_variant(const Batch& b, int minb, cudaStream_t s) {
+    return minb == 0 ? SetImpl<P>::tree<1>(b, s) : cudaErrorInvalidValue;
+}
+}  // namespace
+
+extern const SetOps kOps_K192S = {
+    SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk, tree_variant,
+    SetImpl<P>::tree_split, SetImpl<P>::tree_dedup, SetImpl<P>::tree_cached, SetImpl<P>::cache_build,
+    SetImpl<P>::wots,       SetImpl<P>::verify,     SetImpl<P>::keygen,
+    kForsLpt, 2, 32, kTreeMinb, 1, 0};
+
+}  // namespace hs

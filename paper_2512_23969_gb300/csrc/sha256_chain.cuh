@@ -160,4 +160,13 @@ __device__ __forceinline__ void hashF_fast(const uint32_t ms[8], const Adrs& a, 
     for (int i = 0; i < NW; i++) out[i] = v[i] + ms[i];
 }
 
+// F / PRF of a parameter set: the chain-specialised SHA-256 call above, or
+// one SHAKE256 block for the SHAKE sets (ms256 then holds PK.seed).
+template <class P, int POL>
+__device__ __forceinline__ void hashF_p(const uint32_t ms256[8], const Adrs& a, const uint32_t* x, uint32_t* out,
+                                        const Pipes<POL>& pp) {
+    if constexpr (P::SHAKE) shake_thash1<P::NW, P::NW>(ms256, a, x, out);
+    else hashF_fast<POL, P::NW>(ms256, a, x, out, pp);
+}
+
 }  // namespace hs

@@ -10,9 +10,12 @@ import os
 
 import numpy as np
 
-PARAMS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3, "128s": 4, "192s": 5, "256s": 6}
+PARAMS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3, "128s": 4, "192s": 5, "256s": 6,
+          "shake-128f": 7, "shake-192f": 8, "shake-256f": 9, "shake-128s": 10, "shake-192s": 11, "shake-256s": 12}
 N_BYTES = {"128f": 16, "192f": 24, "256f": 32, "toy": 16, "128s": 16, "192s": 24, "256s": 32}
-NUM_PARAMS = 7
+N_BYTES.update({"shake-" + k: v for k, v in list(N_BYTES.items()) if k != "toy"})
+NUM_PARAMS = 13
+_N_BY_ID = [16, 24, 32, 16, 16, 24, 32, 16, 24, 32, 16, 24, 32]
 STATUS = {0: "HS_OK", 1: "HS_EINVAL", 2: "HS_ENOMEM", 3: "HS_ECUDA", 4: "HS_ETIMEOUT", 5: "HS_EKEY",
           6: "HS_ECANCELED"}
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libhs.so")
@@ -144,7 +147,7 @@ def sig_bytes(params):
 
 def hs_keygen(params, seeds, pk=None, sk=None, stream=None):
     """(pk, sk) for each 3n-byte seed row of ``seeds`` (uint8 [count, 3n])."""
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
+    n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     count = seeds.shape[0] if seeds.ndim == 2 else seeds.shape[0] // (3 * n)
     pk = _like(seeds, count * 2 * n, np.uint8, "uint8") if pk is None else pk
     sk = _like(seeds, count * 4 * n, np.uint8, "uint8") if sk is None else sk
@@ -155,7 +158,7 @@ def hs_keygen(params, seeds, pk=None, sk=None, stream=None):
 def hs_sign_batch(params, sk, msgs, lens, key_idx=None, sigs=None, num_keys=None, stream=None):
     """Signatures (uint8 [count, SIG]) of the packed messages ``msgs`` with lengths ``lens``."""
     count = int(lens.shape[0])
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
+    n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     if num_keys is None:
         num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
     S = sig_bytes(params)
@@ -181,7 +184,7 @@ def hs_slh_sign_batch(params, sk, msgs, lens, ctx=b"", key_idx=None, sigs=None, 
     """FIPS 205 SLH-DSA signatures (deterministic) of every message under one
     context string; ctx=None signs the messages as given (internal function)."""
     count = int(lens.shape[0])
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
+    n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     if num_keys is None:
         num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
     S = sig_bytes(params)
@@ -196,7 +199,7 @@ def hs_slh_sign_batch(params, sk, msgs, lens, ctx=b"", key_idx=None, sigs=None, 
 def hs_slh_verify_batch(params, pk, msgs, lens, sigs, ctx=b"", key_idx=None, ok=None, num_keys=None, stream=None):
     """1/0 per FIPS 205 signature under one context string."""
     count = int(lens.shape[0])
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
+    n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     if num_keys is None:
         num_keys = (pk.shape[0] if pk.ndim == 2 else pk.shape[0] // (2 * n))
     ok = _like(lens, count, np.uint8, "uint8") if ok is None else ok
@@ -214,7 +217,7 @@ class KeySet:
 
     def __init__(self, params, sk, cache_layers=0, stream=None):
         L = load()
-        n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
+        n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
         self.params = params
         self.num_keys = int(sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
         h = C.c_void_p()
@@ -257,7 +260,7 @@ class KeySet:
 def hs_verify_batch(params, pk, msgs, lens, sigs, key_idx=None, ok=None, num_keys=None, stream=None):
     """1/0 per signature (uint8 [count])."""
     count = int(lens.shape[0])
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
+    n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     if num_keys is None:
         num_keys = (pk.shape[0] if pk.ndim == 2 else pk.shape[0] // (2 * n))
     ok = _like(lens, count, np.uint8, "uint8") if ok is None else ok
@@ -302,7 +305,7 @@ def hs_sign_batch_noalloc(params, sk, msgs, lens, sigs, key_idx=None, num_keys=N
     all buffers (including the output ``sigs``) are caller-provided device
     tensors, and the library works in its fixed 8 MiB device buffer."""
     count = int(lens.shape[0])
-    n = N_BYTES[params] if isinstance(params, str) else [16, 24, 32, 16, 16, 24, 32][params]
+    n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     if num_keys is None:
         num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
     _check(load().hs_sign_batch_noalloc(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), _ptr(msgs),
@@ -335,7 +338,7 @@ def hs_sign_mixed(jobs, use_graph=True, stream=None):
     arr = (SignJob * len(jobs))()
     for j, jb in enumerate(jobs):
         ps = jb["params"]
-        n = N_BYTES[ps] if isinstance(ps, str) else [16, 24, 32, 16, 16, 24, 32][ps]
+        n = N_BYTES[ps] if isinstance(ps, str) else _N_BY_ID[ps]
         sk = jb["sk"]
         nk = jb.get("num_keys") or (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
         msgs = _nonempty(jb["msgs"], jb["lens"])
@@ -461,7 +464,8 @@ class Server:
             pass
 
 
-SIG_BY_ID = {0: 17088, 1: 35664, 2: 49856, 3: 1456, 4: 7856, 5: 16224, 6: 29792}
+SIG_BY_ID = {0: 17088, 1: 35664, 2: 49856, 3: 1456, 4: 7856, 5: 16224, 6: 29792,
+             7: 17088, 8: 35664, 9: 49856, 10: 7856, 11: 16224, 12: 29792}
 
 
 def hs_set_tree_sharing(on=True):

@@ -15,6 +15,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 N_BYTES = {"128f": 16, "192f": 24, "256f": 32, "toy": 16, "128s": 16, "192s": 24, "256s": 32}
+N_BYTES.update({"shake-" + k: v for k, v in list(N_BYTES.items()) if k != "toy"})
 BASE_SEED = 23969
 
 

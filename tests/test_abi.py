@@ -34,7 +34,9 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_size_queries_match_oracle(lib, O):
-    for pid, ps in enumerate(("128f", "192f", "256f", "toy")):
+    names = ("128f", "192f", "256f", "toy", "128s", "192s", "256s",
+             "shake-128f", "shake-192f", "shake-256f", "shake-128s", "shake-192s", "shake-256s")
+    for pid, ps in enumerate(names):
         P = O.params(ps)
         for fn, want in (("hs_sig_bytes", P.sig_bytes), ("hs_pk_bytes", 2 * P.n),
                          ("hs_sk_bytes", 4 * P.n), ("hs_seed_bytes", 3 * P.n)):
@@ -44,7 +46,7 @@ def test_size_queries_match_oracle(lib, O):
             assert f(pid) == want, (fn, ps)
     lib.hs_sig_bytes.argtypes = [C.c_int]
     lib.hs_sig_bytes.restype = C.c_size_t
-    assert lib.hs_sig_bytes(7) == 0
+    assert lib.hs_sig_bytes(len(names)) == 0 and lib.hs_sig_bytes(-1) == 0
     lib.hs_sign_kernel_count.restype = C.c_int
     assert lib.hs_sign_kernel_count() == 7
 
@@ -53,7 +55,7 @@ def test_count_zero_and_bad_enum_need_no_gpu(lib):
     lib.hs_sign_batch.restype = C.c_int
     lib.hs_sign_batch.argtypes = [C.c_int, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_uint32, C.c_void_p, C.c_void_p]
-    assert lib.hs_sign_batch(9, None, 1, None, None, None, 1, None, None) == 1      # HS_EINVAL
+    assert lib.hs_sign_batch(13, None, 1, None, None, None, 1, None, None) == 1     # HS_EINVAL
     assert lib.hs_sign_batch(0, None, 1, None, None, None, 0, None, None) == 0      # count 0: no-op
     lib.hs_last_error.restype = C.c_char_p
     assert b"parameter set" in lib.hs_last_error()
