@@ -68,12 +68,39 @@ STAGE_WORK = {
 }
 
 
+# The SHAKE instantiation: every hash is Keccak-f[1600] permutations.  ALU
+# work of one permutation on 32-bit lane halves, per round: column parities
+# 20 (2 LOP3 per half), D 20 (rotate-by-1 and XOR), theta's XOR into the
+# 25 lanes 50, rho 48 funnel shifts (lanes rotated by 0 or 32 cost nothing),
+# chi 50 LOP3, iota 2 -> 190 x 24 = 4560.
+ALU_KECCAK = 4560
+
+
+def _keccak_work(n, d, hp, a, k, length):
+    """Permutations per signature of each stage (T_l absorbs n + 32 + l n
+    bytes plus a pad byte at 136 bytes per permutation)."""
+    t_len = -(-(n + 32 + length * n + 1) // 136)
+    t_k = -(-(n + 32 + k * n + 1) // 136)
+    return {"tree": d * (2 ** hp) * (length * 16 + t_len) + d * (2 ** hp - 1),
+            "fors": k * (2 ** a) * 2 + k * (2 ** a - 1) + t_k,
+            "wots": d * length * (1 + 7.5)}
+
+
+KECCAK_WORK = {"shake-128f": _keccak_work(16, 22, 3, 6, 33, 35), "shake-192f": _keccak_work(24, 22, 3, 8, 33, 51),
+               "shake-256f": _keccak_work(32, 17, 4, 9, 35, 67), "shake-128s": _keccak_work(16, 7, 9, 12, 14, 35),
+               "shake-192s": _keccak_work(24, 7, 9, 14, 17, 51), "shake-256s": _keccak_work(32, 8, 8, 14, 22, 67)}
+
+
 def ops_per_sig(ps, stage):
+    if ps in KECCAK_WORK:          # Keccak is all ALU work: the two bases coincide
+        return KECCAK_WORK[ps][stage] * ALU_KECCAK
     c256, c512 = STAGE_WORK[ps][stage]
     return c256 * OPS_C256 + c512 * OPS_C512
 
 
 def alu_ops_per_sig(ps, stage):
+    if ps in KECCAK_WORK:
+        return KECCAK_WORK[ps][stage] * ALU_KECCAK
     c256, c512 = STAGE_WORK[ps][stage]
     return c256 * ALU_C256 + c512 * ALU_C512
 
@@ -252,13 +279,17 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
     res = {}
     dev = lambda x: torch.from_numpy(x).cuda()
     steps, warmup = max(2, args.steps // 2), 3
-    for ps in ("192f", "256f", "128s", "192s", "256s"):
+    # the SHAKE sets on fewer messages (a permutation costs ~4.5 SHA-256 compressions)
+    shake_counts = {"shake-128f": 4096, "shake-192f": 2048, "shake-256f": 2048, "shake-128s": 256,
+                    "shake-192s": 256, "shake-256s": 256}
+    for ps in ("192f", "256f", "128s", "192s", "256s") + tuple(shake_counts):
         log("config %s" % ps)
-        if ps.endswith("f"):
+        if ps in ("192f", "256f"):
             wl = inputs.config(2, ps)
-        else:       # the same shape of workload, 1024 messages, for the small-signature sets
-            wl = inputs.make(ps, 1024, 16, ("uniform", 32, 1024), inputs.BASE_SEED + 3,
-                             "%s-16keys-1024xU[32,1024]B" % ps)
+        else:       # the same shape of workload for the other sets
+            cnt = shake_counts.get(ps, 1024)
+            wl = inputs.make(ps, cnt, 16, ("uniform", 32, 1024), inputs.BASE_SEED + 3,
+                             "%s-16keys-%dxU[32,1024]B" % (ps, cnt))
         pk, sk = hs.hs_keygen(ps, dev(wl.seeds))
         m, l, k = dev(wl.msgs), dev(wl.lens), dev(wl.key_idx)
         sig = torch.empty(wl.count * hs.sig_bytes(ps), dtype=torch.uint8, device="cuda")
@@ -623,8 +654,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=10.0)
-    ap.add_argument("--params", choices=["128f", "192f", "256f"], default="128f",
-                    help="parameter set (the default workload is 128f)")
+    ap.add_argument("--params", default="128f",
+                    choices=["128f", "192f", "256f", "128s", "192s", "256s", "shake-128f", "shake-192f", "shake-256f",
+                             "shake-128s", "shake-192s", "shake-256s"],
+                    help="parameter set (the default workload is 128f; the others serve small profiling cases)")
     ap.add_argument("--no-other-configs", dest="other_configs", action="store_false",
                     help="skip the 192f / 256f / mixed-parameter measurements")
     ap.add_argument("--serving-seconds", type=float, default=3.0,
