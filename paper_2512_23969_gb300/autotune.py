@@ -21,7 +21,18 @@ from . import hs, inputs
 
 KNOBS = {"fors_lanes": 0, "tree_min_blocks": 1, "tree_split_below": 2}
 STAGE_OF_KNOB = {"fors_lanes": "fors", "tree_min_blocks": "tree"}
-DEFAULT_COUNTS = {"128f": 16384, "192f": 8192, "256f": 8192, "toy": 4096}
+DEFAULT_COUNTS = {"128f": 16384, "192f": 8192, "256f": 8192, "toy": 4096, "128s": 512, "192s": 256, "256s": 256,
+                  "shake-128f": 4096, "shake-192f": 2048, "shake-256f": 2048, "shake-128s": 128, "shake-192s": 64,
+                  "shake-256s": 64}
+# batch sizes at which the two TREE_Sign forms are compared, per family
+SPLIT_COUNTS = {"f": (64, 256, 1024, 2048, 4096, 8192), "s": (8, 16, 32, 64, 128, 256),
+                "shake-f": (64, 256, 1024, 2048, 4096, 8192), "shake-s": (4, 8, 16, 32, 64, 128)}
+
+
+def _family(ps):
+    base = ps[len("shake-"):] if ps.startswith("shake-") else ps
+    fam = "s" if base.endswith("s") else "f"
+    return ("shake-" + fam) if ps.startswith("shake-") else fam
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
@@ -83,9 +94,10 @@ def _stage_ms(params, wl, sk, dev, sigs, stage, reps):
     return best
 
 
-def tune_split(ps, counts=(64, 256, 1024, 2048, 4096, 8192), reps=3, verbose=True):
+def tune_split(ps, counts=None, reps=3, verbose=True):
     """Batch size below which the chain-parallel TREE_Sign is faster: time
     the TREE stage in both forms at growing batch sizes."""
+    counts = counts or SPLIT_COUNTS[_family(ps)]
     rows = {}
     below = 0
     for count in counts:
@@ -139,7 +151,7 @@ def save(result, path=CACHE):
     if os.path.exists(path):
         with open(path) as f:
             data = json.load(f)
-    data[device_key()] = result
+    data.setdefault(device_key(), {}).update(result)      # keep the sets not tuned this time
     with open(path, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
 
