@@ -326,6 +326,14 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
                                 "ms_per_step": round(sum(ms) / len(ms), 3),
                                 "stage_ms": {a: round(b, 3) for a, b in prof.items()},
                                 "identical_to_full_work": bool(torch.equal(sig, ref))}
+    # batched GPU verification of the bench workload's signatures
+    log("128f verify")
+    ms = _time_steps(lambda: hs.hs_verify_batch("128f", pk, m, l, sig.view(wl.count, -1), key_idx=k,
+                                                num_keys=wl.num_keys, stream=stream), stream, flush, steps, warmup)
+    ok = hs.hs_verify_batch("128f", pk, m, l, sig.view(wl.count, -1), key_idx=k, num_keys=wl.num_keys)
+    res["128f_verify"] = {"workload": wl.name + ", hs_verify_batch of the batch's signatures",
+                          "value": round(wl.count * len(ms) / (sum(ms) / 1e3), 1), "unit": "verifications/s",
+                          "ms_per_step": round(sum(ms) / len(ms), 3), "accepted": int(ok.sum().item())}
     # the bench workload signed from a keyset with the top 4 layers of each key prebuilt
     log("128f from a keyset with cached top layers")
     sig.zero_()

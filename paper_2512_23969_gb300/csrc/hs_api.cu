@@ -119,7 +119,8 @@ static void scratch_layout(const Batch& b, const SetInfo& s, size_t sz[kRegions]
     sz[i++] = cnt * nw * 4;                                          // pk_fors
     sz[i++] = cnt * s.d * nw * 4;                                    // roots
     sz[i++] = b.ck ? cnt * s.d * s.len * (16 / b.ck) * nw * 4 : 0;   // chk
-    sz[i++] = b.split ? cnt * s.d * s.leaves * s.len * nw * 4 : 0;   // ends
+    sz[i++] = b.verify ? cnt * s.len * nw * 4                        // ends (one layer when verifying)
+                       : (b.split ? cnt * s.d * s.leaves * s.len * nw * 4 : 0);
     const bool sh = b.dedup_layer != 0 && !b.cached;                 // in-batch sharing
     const size_t mj = b.dedup_layer ? cnt * (s.d - b.dedup_layer) : 0;
     const size_t cap = sh ? ((size_t)1 << b.cap_log2) : 0;
@@ -174,7 +175,7 @@ void carve_scratch(Batch& b, void* base) {
     b.pk_fors = reinterpret_cast<uint32_t*>(r[5]);
     b.roots = reinterpret_cast<uint32_t*>(r[6]);
     b.chk = b.ck ? reinterpret_cast<uint32_t*>(r[7]) : nullptr;
-    b.ends = b.split ? reinterpret_cast<uint32_t*>(r[8]) : nullptr;
+    b.ends = (b.split || b.verify) ? reinterpret_cast<uint32_t*>(r[8]) : nullptr;
     b.leafv = s.leaves > 32 ? reinterpret_cast<uint32_t*>(r[16]) : nullptr;
     const bool sh = b.dedup_layer != 0 && !b.cached;
     b.table = sh ? reinterpret_cast<unsigned long long*>(r[9]) : nullptr;
@@ -456,6 +457,7 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
     b.status = d->status;
     b.ck = verify ? 0u : (ks ? ks->ck : g_ck);
     b.split = !verify && tree_split(p, count);
+    b.verify = verify;
     if (ks && ks->layers) {
         b.dedup_layer = ks->first_layer;
         b.cached = true;

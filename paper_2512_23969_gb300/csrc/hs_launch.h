@@ -28,6 +28,7 @@ struct Batch {
     uint32_t count;
     uint8_t* sigs;            // sign: out; verify: in (const)
     uint8_t* ok;              // verify only
+    bool verify;              // a verification call (scratch: chain ends of one layer)
     // scratch
     KeyBlock* keys;           // num_keys
     uint64_t* offsets;        // count + 1

@@ -153,9 +153,26 @@ struct SetImpl {
                                                    b.ck, own_layers(b), b.mj_id, b.chk_u, 1u);
         return cudaGetLastError();
     }
+    // Verification: FORS roots, PK_FORS, then per layer chains and T_len +
+    // climbs (layers are serial), then the comparison with PK.root.  The
+    // layer messages live in pk_fors (layer 0) and roots (layers >= 1).
     static cudaError_t verify(const Batch& b, cudaStream_t s) {
-        const uint32_t G = (b.count + 3) / 4;
-        verify_kernel<P><<<G, 128, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.ok);
+        const uint32_t T = 128;
+        const uint64_t ft = (uint64_t)b.count * P::K;
+        vfors_kernel<P><<<(uint32_t)((ft + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.fors_roots);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = fors_pk(b, s);
+        const uint64_t ct = (uint64_t)b.count * P::LEN;
+        const uint32_t G1 = (b.count + T - 1) / T;
+        for (uint32_t j = 0; j < (uint32_t)P::D && e == cudaSuccess; j++) {
+            vchain_kernel<P, kChainPol><<<(uint32_t)((ct + T - 1) / T), T, 0, s>>>(
+                b.keys, b.infos, b.count, b.sigs, j == 0 ? b.pk_fors : b.roots, b.ends, j, 1u);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            vleaf_kernel<P><<<G1, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.ends, b.roots, j);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return e;
+        vfinal_kernel<P><<<G1, T, 0, s>>>(b.keys, b.infos, b.count, b.roots, b.ok);
         return cudaGetLastError();
     }
     static cudaError_t keygen(const uint8_t* seeds, uint32_t count, uint8_t* pk, uint8_t* sk, cudaStream_t s) {
