@@ -383,6 +383,30 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
         n_ok += int(ok.sum().item())
     out["verified"] = "%d/%d" % (n_ok, total)
     res["mixed"] = out
+    # a small mixed batch, where per-launch overheads weigh most
+    swls = inputs.mixed(count=96, seed=inputs.BASE_SEED + 61, name="mixed-small")
+    sjobs = []
+    for wl in swls:
+        pk, sk = hs.hs_keygen(wl.params, dev(wl.seeds))
+        sjobs.append({"params": wl.params, "sk": sk, "msgs": dev(wl.msgs), "lens": dev(wl.lens),
+                      "key_idx": dev(wl.key_idx), "num_keys": wl.num_keys,
+                      "sigs": torch.empty(wl.count * hs.sig_bytes(wl.params), dtype=torch.uint8, device="cuda")})
+    stotal = sum(wl.count for wl in swls)
+
+    def splain():
+        for j in sjobs:
+            hs.hs_sign_batch(j["params"], j["sk"], j["msgs"], j["lens"], key_idx=j["key_idx"], sigs=j["sigs"],
+                             num_keys=j["num_keys"], stream=stream)
+
+    sout = {"workload": "mixed 96 msgs 50/30/20 128f/192f/256f, log-U[16 B, 64 KB], 64 keys (32/19/13)",
+            "messages": stotal}
+    for name, fn in (("plain_per_set_calls", splain),
+                     ("one_graph_launch", lambda: hs.hs_sign_mixed(sjobs, use_graph=True, stream=stream)),
+                     ("streams_no_graph", lambda: hs.hs_sign_mixed(sjobs, use_graph=False, stream=stream))):
+        ms = _time_steps(fn, stream, flush, max(steps, 5), warmup)
+        sout[name] = {"value": round(stotal * len(ms) / (sum(ms) / 1e3), 1), "unit": "signatures/s",
+                      "ms_per_step": round(sum(ms) / len(ms), 3)}
+    res["mixed_small"] = sout
     return res
 
 
