@@ -82,7 +82,6 @@ void plan_dedup(Batch& b) {
     b.max_uniq = 0;
     SetInfo s;
     if (!g_share || !set_info(b.pset, &s) || b.num_keys > (1u << 20) || b.count == 0) return;
-    if (s.leaves > 32) return;        // wide trees: no sharing
     // Share layers from the top down while the number of distinct trees a
     // layer can hold (keys x 2^bits of its tree index, at most one per
     // message) is at most half the messages, and the tree index fits the
@@ -618,8 +617,6 @@ HS_API hs_status hs_keyset_create(hs_params p, const uint8_t* sk, uint32_t num_k
     if (!sk || !out || num_keys == 0) return fail(HS_EINVAL, "hs_keyset_create: NULL buffer or no keys");
     if (cache_layers > (uint32_t)si.d - 1)
         return fail(HS_EINVAL, "cache_layers %u: at most d - 1 = %d", cache_layers, si.d - 1);
-    if (cache_layers && si.leaves > 32)
-        return fail(HS_EINVAL, "cache_layers: not offered for the s sets (2^h' = %d leaves per tree)", si.leaves);
     if (cache_layers && (uint64_t)(cache_layers - 1) * si.hp > 24)
         return fail(HS_EINVAL, "cache_layers %u: more than 2^24 trees per key", cache_layers);
     uint64_t tpk = 0;

@@ -9,7 +9,11 @@
 // and all jobs fork from, and join back into, the caller's stream.  With
 // use_graph the whole fork/join sequence is stream-captured into one graph
 // and launched once; without it the same launches go out directly (the
-// "plain" per-stage form that the graph form is measured against).
+// "plain" per-stage form that the graph form is measured against).  The
+// instantiated graph is kept per device: a later call whose DAG has the
+// same shape (same sets, batch-size class and options; only pointers and
+// counts differ) updates its kernel arguments in place
+// (cudaGraphExecUpdate) instead of instantiating anew.
 #include <cuda_runtime.h>
 #include <cstdio>
 #include <mutex>
@@ -26,6 +30,9 @@ constexpr int kMaxJobs = 16;
 
 struct MixedDev {
     bool init = false;
+    std::mutex mu;                      // one call at a time per device: shared streams and graph
+    cudaGraphExec_t exec = nullptr;     // last instantiated graph, reused when the DAG shape matches
+    uint64_t instantiations = 0, updates = 0;
     cudaStream_t capture;               // graphs are captured here, launched on the caller's stream
     cudaStream_t side[2 * kMaxJobs];
     cudaEvent_t fork, msg[kMaxJobs], fors[kMaxJobs], done[kMaxJobs];
@@ -153,9 +160,10 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
         bs[j].status = status;
         carve_scratch(bs[j], static_cast<char*>(base) + off[j]);
     }
+    {
+    std::lock_guard<std::mutex> lk(d->mu);
     if (use_graph) {
         cudaGraph_t g = nullptr;
-        cudaGraphExec_t ge = nullptr;
         // Capture on a library stream (the caller's may be the legacy default
         // stream, which cannot be captured); the graph is launched on 'stream'.
         e = cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeThreadLocal);
@@ -164,12 +172,26 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
             e = cudaStreamEndCapture(d->capture, &g);
             if (e2 != cudaSuccess) e = e2;
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
-        if (e == cudaSuccess) e = cudaGraphLaunch(ge, s);
-        if (ge) cudaGraphExecDestroy(ge);
+        if (e == cudaSuccess && d->exec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(d->exec, g, &info) == cudaSuccess) {
+                d->updates++;
+            } else {                    // another DAG shape: instantiate below
+                cudaGetLastError();
+                cudaGraphExecDestroy(d->exec);
+                d->exec = nullptr;
+            }
+        }
+        if (e == cudaSuccess && !d->exec) {
+            e = cudaGraphInstantiate(&d->exec, g, 0);
+            if (e == cudaSuccess) d->instantiations++;
+            else d->exec = nullptr;
+        }
+        if (e == cudaSuccess) e = cudaGraphLaunch(d->exec, s);
         if (g) cudaGraphDestroy(g);
     } else {
         e = enqueue_jobs(*d, bs, s);
+    }
     }
     cudaError_t ef = cudaFreeAsync(base, s);
     if (e == cudaSuccess) e = ef;

@@ -370,7 +370,7 @@ HS_API hs_status hs_server_create(const hs_server_config* cfg, const uint8_t* co
         if (!sks[p]) { ok = false; break; }
         SetShape sh;
         set_shape(p, &sh);
-        const uint32_t layers = sh.leaves > 32 ? 0u : std::min<uint32_t>(cfg->cache_layers, (uint32_t)sh.d - 1);
+        const uint32_t layers = std::min<uint32_t>(cfg->cache_layers, (uint32_t)sh.d - 1);
         ok = hs_keyset_create((hs_params)p, sks[p], nkeys[p], layers, nullptr, &sv.ks[p]) == HS_OK;
     }
     const size_t host_bytes = cfg->pinned_bytes ? cfg->pinned_bytes : cfg->mem_budget_bytes / 2;

@@ -92,9 +92,12 @@ __global__ void __launch_bounds__(128) bleaf_from_ends_kernel(const KeyBlock* __
 // Merge the 2^h' nodes in sh (level 0) up to the root, left in sh[0 .. NW).
 // auth (may be null): the h' auth nodes of leaf sl are stored there.  Every
 // thread of the block calls it.
+// heap (may be null): every node is also stored there, heap-ordered (node
+// (z, i) at (2^h' >> z) + i, NW words each).
 template <class P>
 __device__ __forceinline__ void block_merkle(const uint32_t* ms256, const uint32_t* msT, uint32_t layer,
-                                             uint64_t tree, uint32_t* sh, uint32_t sl, uint8_t* auth) {
+                                             uint64_t tree, uint32_t* sh, uint32_t sl, uint8_t* auth,
+                                             uint32_t* heap = nullptr) {
     constexpr int NW = P::NW, HP = P::HP, LV = P::LEAVES;
     static_assert(LV <= 2 * kMergeThreads, "one node per thread from the first level up");
     const uint32_t t = threadIdx.x;
@@ -113,6 +116,10 @@ __device__ __forceinline__ void block_merkle(const uint32_t* ms256, const uint32
         if (t < cnt) {
 #pragma unroll
             for (int w = 0; w < NW; w++) sh[t * NW + w] = out[w];
+            if (heap != nullptr) {
+#pragma unroll
+                for (int w = 0; w < NW; w++) heap[((size_t)(LV >> z) + t) * NW + w] = out[w];
+            }
         }
         __syncthreads();
     }
@@ -151,6 +158,62 @@ __global__ void __launch_bounds__(kMergeThreads) bmerkle_kernel(const KeyBlock* 
 #pragma unroll
         for (int w = 0; w < NW; w++) rt[w] = sh[w];
     }
+}
+
+// ---------------------------------------------------------------- shared / cached trees
+// Distinct trees (tree sharing within a batch, keyset caches) for wide
+// trees: one thread per (tree, leaf) for the leaves, with the chain
+// checkpoints of every leaf, stored heap-ordered; then one block per tree
+// for the internal nodes.  nuniq (may be null) bounds the live trees.
+template <class P, int POL>
+__global__ void __launch_bounds__(128) wtree_leaf_kernel(const KeyBlock* __restrict__ keys,
+                                                         const DedupDesc* __restrict__ desc,
+                                                         const uint32_t* __restrict__ nuniq, uint32_t max_uniq,
+                                                         uint32_t* __restrict__ nodes, uint32_t* __restrict__ chk_u,
+                                                         uint32_t ck, uint32_t one) {
+    constexpr int NW = P::NW, LV = P::LEAVES;
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t id = gid / LV;
+    const uint32_t l = (uint32_t)(gid % LV);
+    if (id >= max_uniq || (nuniq && id >= *nuniq)) return;
+    const DedupDesc d = desc[id];
+    const KeyBlock& kb = keys[d.key];
+    uint32_t ms256[8], msT[P::BIG ? 16 : 8], skseed[NW];
+#pragma unroll
+    for (int w = 0; w < 8; w++) ms256[w] = kb.ms256[w];
+#pragma unroll
+    for (int w = 0; w < (P::BIG ? 16 : 8); w++) msT[w] = P::BIG ? kb.ms512[w] : kb.ms256[w];
+#pragma unroll
+    for (int w = 0; w < NW; w++) skseed[w] = kb.sk_seed[w];
+    const Pipes<POL> pp(one);
+    uint32_t* mychk = ck ? chk_u + ((size_t)id * LV + l) * (size_t)P::LEN * (16u / ck) * NW : nullptr;
+    uint32_t node[NW];
+    wots_leaf<P, POL>(ms256, msT, skseed, d.layer, d.tree, l, node, mychk, ck, pp);
+    uint32_t* tn = nodes + (size_t)id * 2 * LV * NW;
+#pragma unroll
+    for (int w = 0; w < NW; w++) tn[((size_t)LV + l) * NW + w] = node[w];
+}
+
+template <class P>
+__global__ void __launch_bounds__(kMergeThreads) wtree_merge_kernel(const KeyBlock* __restrict__ keys,
+                                                                    const DedupDesc* __restrict__ desc,
+                                                                    const uint32_t* __restrict__ nuniq,
+                                                                    uint32_t max_uniq, uint32_t* __restrict__ nodes) {
+    constexpr int NW = P::NW, LV = P::LEAVES;
+    __shared__ uint32_t sh[LV * NW];
+    const uint32_t id = blockIdx.x;
+    if (id >= max_uniq || (nuniq && id >= *nuniq)) return;      // block-uniform
+    const DedupDesc d = desc[id];
+    const KeyBlock& kb = keys[d.key];
+    uint32_t ms256[8], msT[P::BIG ? 16 : 8];
+#pragma unroll
+    for (int w = 0; w < 8; w++) ms256[w] = kb.ms256[w];
+#pragma unroll
+    for (int w = 0; w < (P::BIG ? 16 : 8); w++) msT[w] = P::BIG ? kb.ms512[w] : kb.ms256[w];
+    uint32_t* tn = nodes + (size_t)id * 2 * LV * NW;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(LV * NW); i += blockDim.x) sh[i] = tn[LV * NW + i];
+    __syncthreads();
+    block_merkle<P>(ms256, msT, d.layer, d.tree, sh, 0u, nullptr, tn);
 }
 
 // ---------------------------------------------------------------- keygen

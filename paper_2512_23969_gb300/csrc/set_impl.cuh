@@ -17,7 +17,7 @@ namespace hs {
 template <class P>
 struct SetImpl {
     // XMSS trees wider than a warp (s sets) take the two-launch form of
-    // kern_stree.cuh; tree sharing and keyset caches are not offered there.
+    // kern_stree.cuh, also for the shared and cached trees.
     static constexpr bool kWide = P::LEAVES > 32;
 
     // layers each message builds itself: all of them unless the upper
@@ -75,10 +75,26 @@ struct SetImpl {
                                                                      b.roots, L);
         return cudaGetLastError();
     }
-    static cudaError_t tree_dedup(const Batch& b, cudaStream_t s) {
+    // The distinct trees of the shared / cached layers, all nodes and the
+    // checkpoints of every leaf (desc: their (key, layer, tree)).
+    static cudaError_t build_trees(const KeyBlock* keys, const DedupDesc* desc, const uint32_t* nuniq,
+                                   uint32_t max_uniq, uint32_t* nodes, uint32_t* chk, uint32_t ck, cudaStream_t s) {
+        const uint32_t T = 128;
+        const uint64_t th = (uint64_t)max_uniq * P::LEAVES;
+        if (th == 0) return cudaSuccess;
         if constexpr (kWide) {
-            return cudaErrorNotSupported;
+            wtree_leaf_kernel<P, kChainPol><<<(uint32_t)((th + T - 1) / T), T, 0, s>>>(keys, desc, nuniq, max_uniq,
+                                                                                      nodes, chk, ck, 1u);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            wtree_merge_kernel<P><<<max_uniq, kMergeThreads, 0, s>>>(keys, desc, nuniq, max_uniq, nodes);
         } else {
+            utree_kernel<P, kChainPol><<<(uint32_t)((th + T - 1) / T), T, 0, s>>>(keys, desc, nuniq, max_uniq, nodes,
+                                                                                  chk, ck, 1u);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t tree_dedup(const Batch& b, cudaStream_t s) {
         const uint32_t T = 128, L = own_layers(b);
         const uint64_t mj = (uint64_t)b.count * (P::D - L);
         dedup_insert_kernel<P><<<(uint32_t)((mj + T - 1) / T), T, 0, s>>>(b.infos, b.count, L, b.table, b.cap_log2,
@@ -89,14 +105,11 @@ struct SetImpl {
         dedup_compact_kernel<<<(cap + T - 1) / T, T, 0, s>>>(b.table, cap, b.slot_id, b.desc, b.nuniq, b.max_uniq,
                                                              b.status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const uint64_t ut = (uint64_t)b.max_uniq * P::LEAVES;
-        utree_kernel<P, kChainPol><<<(uint32_t)((ut + T - 1) / T), T, 0, s>>>(b.keys, b.desc, b.nuniq, b.max_uniq,
-                                                                              b.nodes_u, b.chk_u, b.ck, 1u);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = build_trees(b.keys, b.desc, b.nuniq, b.max_uniq, b.nodes_u, b.chk_u, b.ck, s)) != cudaSuccess)
+            return e;
         dedup_scatter_kernel<P><<<(uint32_t)((mj + T - 1) / T), T, 0, s>>>(b.infos, b.count, L, b.mj_slot, b.slot_id,
                                                                            b.nodes_u, b.sigs, b.roots, b.mj_id);
         return cudaGetLastError();
-        }
     }
     // Cached top layers (keyset): auth paths, roots and tree ids from the cache.
     static cudaError_t tree_cached(const Batch& b, cudaStream_t s) {
@@ -110,19 +123,13 @@ struct SetImpl {
     // Build every tree of layers L..D-1 of num_keys resident keys.
     static cudaError_t cache_build(const KeyBlock* keys, uint32_t num_keys, uint32_t L, uint32_t tpk,
                                    DedupDesc* desc, uint32_t* nodes, uint32_t* chk, uint32_t ck, cudaStream_t s) {
-        if constexpr (kWide) return cudaErrorNotSupported;
         const uint32_t T = 128;
         const uint64_t trees = (uint64_t)num_keys * tpk;
         if (trees == 0) return cudaSuccess;
         cache_desc_kernel<P><<<(uint32_t)((trees + T - 1) / T), T, 0, s>>>(num_keys, L, tpk, desc);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        const uint64_t th = trees * P::LEAVES;
-        if constexpr (!kWide)
-            utree_kernel<P, kChainPol><<<(uint32_t)((th + T - 1) / T), T, 0, s>>>(keys, desc, nullptr,
-                                                                                  (uint32_t)trees, nodes, chk, ck,
-                                                                                  1u);
-        return cudaGetLastError();
+        return build_trees(keys, desc, nullptr, (uint32_t)trees, nodes, chk, ck, s);
     }
     static cudaError_t tree_split(const Batch& b, cudaStream_t s) {
         const uint32_t T = 128;

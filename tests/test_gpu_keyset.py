@@ -30,6 +30,9 @@ def _batch(hs, ps, count, num_keys, seed, lengths=("uniform", 0, 300)):
     ("128f", 4, 8200, 16),          # per-leaf TREE_Sign (>= the split size)
     ("192f", 2, 500, 4),
     ("256f", 3, 260, 3),
+    ("128s", 1, 70, 3),             # a 512-leaf top tree per key (wide-tree builder)
+    ("256s", 2, 20, 2),             # 1 + 256 wide trees per key
+    ("shake-128f", 2, 300, 4),
 ])
 def test_keyset_equals_sign_batch(hs, O, ps, layers, count, num_keys):
     import torch

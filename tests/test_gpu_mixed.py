@@ -47,3 +47,31 @@ def test_mixed_rejects_host_buffers(hs):
     with pytest.raises(hs.HSError):
         hs.hs_sign_mixed([{"params": "toy", "sk": sk, "msgs": wl.msgs, "lens": wl.lens,
                            "sigs": np.zeros(2 * 1456, np.uint8)}])
+
+
+def test_graph_reuse_across_calls(hs):
+    """The kept graph is updated in place for calls of the same DAG shape and
+    re-instantiated for another shape; every call's bytes stay exact."""
+    import torch
+
+    def jobs_for(shape, seed):
+        jobs, refs = [], []
+        for k, (ps, count) in enumerate(shape):
+            wl = inputs.make(ps, count, num_keys=2, lengths=("uniform", 0, 500), seed=seed + k, key_mode="random")
+            pk, sk = hs.hs_keygen(ps, _dev(wl.seeds))
+            d = {"params": ps, "sk": sk, "msgs": _dev(wl.msgs), "lens": _dev(wl.lens),
+                 "key_idx": _dev(wl.key_idx), "num_keys": 2,
+                 "sigs": torch.zeros(count * hs.sig_bytes(ps), dtype=torch.uint8, device="cuda")}
+            refs.append(hs.hs_sign_batch(ps, sk, d["msgs"], d["lens"], key_idx=d["key_idx"], num_keys=2)
+                        .view(-1).clone())
+            jobs.append(d)
+        return jobs, refs
+
+    a = (("128f", 20), ("192f", 6), ("shake-128f", 4))
+    b = (("256f", 3), ("128s", 2))
+    for shape, seed in ((a, 900), (a, 910), (b, 920), (a, 930), (b, 940), (b, 950)):
+        jobs, refs = jobs_for(shape, seed)
+        hs.hs_sign_mixed(jobs, use_graph=True)
+        torch.cuda.synchronize()
+        for d, ref in zip(jobs, refs):
+            assert torch.equal(d["sigs"], ref), (shape, seed, d["params"])

@@ -15,7 +15,8 @@ def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-@pytest.mark.parametrize("ps,count,keys", [("toy", 200, 3), ("128f", 300, 2), ("192f", 120, 2), ("256f", 150, 2)])
+@pytest.mark.parametrize("ps,count,keys", [("toy", 200, 3), ("128f", 300, 2), ("192f", 120, 2), ("256f", 150, 2),
+                                           ("128s", 40, 2), ("shake-128f", 300, 2)])
 def test_sharing_is_bit_exact(hs, O, ps, count, keys):
     import torch
     from paper_2512_23969_gb300 import autotune
