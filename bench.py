@@ -575,8 +575,11 @@ def run_own(args):
             hs.hs_sign_batch(ps, sk_h, msgs_h, lens_h, key_idx=kidx_h, sigs=sigs_h, num_keys=wl.num_keys)
             e2e_t.append(time.perf_counter() - t0)
         h2d = sk_h.numel() + msgs_h.numel() + lens_h.numel() * 8 + kidx_h.numel() * 4
+        srt = sorted(e2e_t)
         e2e = {"value": round(count / (sum(e2e_t) / len(e2e_t)), 1), "unit": "signatures/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(sigs_h.numel()),
+               "steps": len(e2e_t), "ms_median": round(srt[len(srt) // 2] * 1e3, 3),
+               "ms_max": round(srt[-1] * 1e3, 3),
                "path": "hs_sign_batch with pinned host buffers (staged H2D, kernels, D2H, stream sync)"}
         if not torch.equal(sigs_h, sigs.cpu()):
             e2e["mismatch"] = True
@@ -683,7 +686,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=10.0)
     ap.add_argument("--params", default="128f",
