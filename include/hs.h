@@ -48,9 +48,8 @@ extern "C" {
  * tree of the hypertree can be brute-forced in tests.  HS_128S/192S/256S are
  * the scheme's small-signature sets (a variant the paper does not use):
  * (n, h, d, h', a, k) = (16, 63, 7, 9, 12, 14), (24, 63, 7, 9, 14, 17),
- * (32, 64, 8, 8, 14, 22); 7856 / 16224 / 29792-byte signatures.  Tree
- * sharing and keyset caches are not offered for them.  HS_SHAKE_* are the
- * SHAKE256 instantiations of the six sets (SPHINCS+ SHAKE-simple, FIPS 205
+ * (32, 64, 8, 8, 14, 22); 7856 / 16224 / 29792-byte signatures.
+ * HS_SHAKE_* are the SHAKE256 instantiations of the six sets (SPHINCS+ SHAKE-simple, FIPS 205
  * Sec. 11.1): same sizes and key layout, every hash SHAKE256 with the full
  * 32-byte address; another variant the paper does not use. */
 typedef enum {
@@ -273,8 +272,7 @@ typedef struct {
     uint32_t max_batch;         /* requests per batch */
     uint64_t mem_budget_bytes;  /* device arena for in-flight work (>= 1 MiB) */
     uint64_t pinned_bytes;      /* pinned host staging arena (0 = budget / 2) */
-    uint32_t cache_layers;      /* top hypertree layers prebuilt per key (hs_keyset; 0 = none;
-                                   ignored for the s sets) */
+    uint32_t cache_layers;      /* top hypertree layers prebuilt per key (hs_keyset; 0 = none) */
 } hs_server_config;
 typedef struct {
     uint64_t completed, batches, batched_requests, pending;
