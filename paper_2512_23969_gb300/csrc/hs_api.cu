@@ -106,7 +106,7 @@ void plan_dedup(Batch& b) {
 }
 
 // Every scratch region of a batch, in carve order (256-byte aligned each).
-static constexpr int kRegions = 17;
+static constexpr int kRegions = 18;
 static void scratch_layout(const Batch& b, const SetInfo& s, size_t sz[kRegions], int* n) {
     const size_t nw = (size_t)s.n / 4, cnt = b.count;
     int i = 0;
@@ -133,6 +133,7 @@ static void scratch_layout(const Batch& b, const SetInfo& s, size_t sz[kRegions]
     sz[i++] = mu * 2 * s.leaves * nw * 4 +                           // nodes_u, then chk_u
               (b.ck ? mu * s.leaves * s.len * (16 / b.ck) * nw * 4 : 0);
     sz[i++] = s.leaves > 32 ? cnt * s.d * s.leaves * nw * 4 : 0;     // leafv
+    sz[i++] = b.verify ? 16 * (size_t)s.d * 4 + 2 * cnt * s.len * 4 : 0;   // vcnt, vsitem, vorder
     *n = i;
 }
 
@@ -176,6 +177,9 @@ void carve_scratch(Batch& b, void* base) {
     b.chk = b.ck ? reinterpret_cast<uint32_t*>(r[7]) : nullptr;
     b.ends = (b.split || b.verify) ? reinterpret_cast<uint32_t*>(r[8]) : nullptr;
     b.leafv = s.leaves > 32 ? reinterpret_cast<uint32_t*>(r[16]) : nullptr;
+    b.vcnt = b.verify ? reinterpret_cast<uint32_t*>(r[17]) : nullptr;
+    b.vsitem = b.verify ? b.vcnt + 16 * s.d : nullptr;
+    b.vorder = b.verify ? b.vsitem + (size_t)b.count * s.len : nullptr;
     const bool sh = b.dedup_layer != 0 && !b.cached;
     b.table = sh ? reinterpret_cast<unsigned long long*>(r[9]) : nullptr;
     b.mj_slot = sh ? reinterpret_cast<uint32_t*>(r[10]) : nullptr;
@@ -419,6 +423,8 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
     if (!keys_in || !lens || (!verify && !sigs_out) || (verify && (!sigs_in || !ok)))
         return fail(HS_EINVAL, "NULL buffer");
     if (num_keys == 0) return fail(HS_EINVAL, "num_keys must be > 0");
+    if (verify && (uint64_t)count * si.len >= (1ull << 28))
+        return fail(HS_EINVAL, "verify: at most %llu signatures per call", (unsigned long long)((1ull << 28) / si.len - 1));
     DevState* d;
     hs_status st = dev_state(&d);
     if (st != HS_OK) return st;

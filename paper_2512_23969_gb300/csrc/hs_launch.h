@@ -29,6 +29,9 @@ struct Batch {
     uint8_t* sigs;            // sign: out; verify: in (const)
     uint8_t* ok;              // verify only
     bool verify;              // a verification call (scratch: chain ends of one layer)
+    uint32_t* vcnt;           // verify: 16 chain-length buckets per layer (16 D words)
+    uint32_t* vsitem;         // verify: count * LEN words, steps << 28 | rank
+    uint32_t* vorder;         // verify: count * LEN words, chains sorted by length
     // scratch
     KeyBlock* keys;           // num_keys
     uint64_t* offsets;        // count + 1

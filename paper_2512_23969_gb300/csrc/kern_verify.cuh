@@ -13,8 +13,13 @@
 // (then the signer's T_k kernel for PK_FORS); then for each layer one
 // thread per (message, chain) advancing its chain to the end, and one
 // thread per message for T_len and the h' climbs, which leaves root_j in
-// scratch for the next layer; finally a comparison with PK.root.  2 d + 3
-// launches per batch; every step of every chain runs in its own lane.
+// scratch for the next layer; finally a comparison with PK.root.
+// A chain needs w - 1 - digit steps (0 .. 15), so a warp of chains in
+// message order waits for its longest.  The chains of a layer are
+// therefore bucketed by their step count (the thread that produced msg_j
+// counts its message's digits and takes ranks with 16 atomics), scattered
+// longest first, and the chain kernel runs them in that order: the chains
+// of a warp then have the same length.
 #pragma once
 #include <cuda_runtime.h>
 #include "hs_common.cuh"
@@ -65,36 +70,98 @@ __global__ void __launch_bounds__(128) vfors_kernel(const KeyBlock* __restrict__
     for (int w = 0; w < NW; w++) r[w] = node[w];
 }
 
+// The len base-w digits of an n-byte value (message nibbles, high first,
+// then the 3 checksum digits).
+template <class P>
+__device__ __forceinline__ uint32_t wots_digit(const uint32_t* msg, uint32_t i) {
+    constexpr int NW = P::NW;
+    if (i < (uint32_t)P::LEN1) return (msg[i >> 3] >> (28 - 4 * (i & 7))) & 15u;
+    uint32_t csum = 0;
+#pragma unroll
+    for (int w = 0; w < NW; w++)
+#pragma unroll
+        for (int b = 0; b < 8; b++) csum += 15u - ((msg[w] >> (28 - 4 * b)) & 15u);
+    return ((csum << 4) >> (12 - 4 * (i - P::LEN1))) & 15u;
+}
+
+constexpr uint32_t kRankBits = 28;        // sitem = steps << 28 | rank within the steps bucket
+
+// For message m's layer: each chain's step count, counted into the layer's
+// 16 buckets (one atomic per non-empty bucket), with the chain's rank inside
+// its bucket recorded in sitem.  Messages with an invalid key count as 0 steps.
+template <class P>
+__device__ __forceinline__ void count_steps(const uint32_t* msg, bool valid, uint64_t m, uint32_t* __restrict__ cnt,
+                                            uint32_t* __restrict__ sitem) {
+    constexpr int LEN = P::LEN;
+    uint32_t hist[16];
+#pragma unroll
+    for (int b = 0; b < 16; b++) hist[b] = 0;
+#pragma unroll 1
+    for (uint32_t i = 0; i < (uint32_t)LEN; i++) {
+        const uint32_t st = valid ? 15u - wots_digit<P>(msg, i) : 0u;
+#pragma unroll
+        for (int b = 0; b < 16; b++) hist[b] += (st == (uint32_t)b) ? 1u : 0u;
+    }
+    uint32_t base[16];
+#pragma unroll
+    for (int b = 0; b < 16; b++) base[b] = hist[b] ? atomicAdd(&cnt[b], hist[b]) : 0u;
+#pragma unroll 1
+    for (uint32_t i = 0; i < (uint32_t)LEN; i++) {
+        const uint32_t st = valid ? 15u - wots_digit<P>(msg, i) : 0u;
+        uint32_t r = 0;
+#pragma unroll
+        for (int b = 0; b < 16; b++)
+            if (st == (uint32_t)b) r = base[b]++;
+        sitem[m * LEN + i] = (st << kRankBits) | r;
+    }
+}
+
+// Layer 0: count from PK_FORS.
+template <class P>
+__global__ void __launch_bounds__(128) vcount0_kernel(const MsgInfo* __restrict__ infos, uint32_t count,
+                                                      const uint32_t* __restrict__ pk_fors, uint32_t* __restrict__ cnt,
+                                                      uint32_t* __restrict__ sitem) {
+    const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    uint32_t msg[P::NW];
+#pragma unroll
+    for (int w = 0; w < P::NW; w++) msg[w] = pk_fors[(size_t)m * P::NW + w];
+    count_steps<P>(msg, infos[m].key != KEY_INVALID, m, cnt, sitem);
+}
+
+// Place every chain of the layer at its sorted position (longest first).
+template <class P>
+__global__ void __launch_bounds__(256) vscatter_kernel(uint32_t count, const uint32_t* __restrict__ cnt,
+                                                       const uint32_t* __restrict__ sitem, uint32_t* __restrict__ order) {
+    const uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= (uint64_t)count * P::LEN) return;
+    const uint32_t v = sitem[it];
+    const uint32_t st = v >> kRankBits, r = v & ((1u << kRankBits) - 1u);
+    uint32_t base = 0;
+#pragma unroll
+    for (int b = 15; b >= 0; b--) base += ((uint32_t)b > st) ? cnt[b] : 0u;
+    order[base + r] = (uint32_t)it;
+}
+
 // Layer j, chain i of message m: its digit from msg_j (PK_FORS for j = 0,
 // else root_{j-1} in vroot), then F from the signed position to w - 1.
 template <class P, int POL>
 __global__ void __launch_bounds__(128) vchain_kernel(const KeyBlock* __restrict__ keys,
                                                      const MsgInfo* __restrict__ infos, uint32_t count,
                                                      const uint8_t* __restrict__ sigs,
-                                                     const uint32_t* __restrict__ msgj,
+                                                     const uint32_t* __restrict__ order,
+                                                     const uint32_t* __restrict__ sitem,
                                                      uint32_t* __restrict__ ends, uint32_t j, uint32_t one) {
     constexpr int NW = P::NW, LEN = P::LEN;
-    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t pos = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= (uint64_t)count * LEN) return;
+    const uint64_t gid = order[pos];             // chains in order of decreasing length
     const uint64_t m = gid / LEN;
     const uint32_t i = (uint32_t)(gid % LEN);
-    if (m >= count) return;
     const MsgInfo& info = infos[m];
     if (info.key == KEY_INVALID) return;
     const KeyBlock& kb = keys[info.key];
-    uint32_t msg[NW];
-#pragma unroll
-    for (int w = 0; w < NW; w++) msg[w] = msgj[m * NW + w];
-    uint32_t digit;
-    if (i < (uint32_t)P::LEN1) {
-        digit = (msg[i >> 3] >> (28 - 4 * (i & 7))) & 15u;
-    } else {
-        uint32_t csum = 0;
-#pragma unroll
-        for (int w = 0; w < NW; w++)
-#pragma unroll
-            for (int b = 0; b < 8; b++) csum += 15u - ((msg[w] >> (28 - 4 * b)) & 15u);
-        digit = ((csum << 4) >> (12 - 4 * (i - P::LEN1))) & 15u;
-    }
+    const uint32_t digit = 15u - (sitem[gid] >> kRankBits);
     const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
     const uint32_t kp = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
     uint32_t ms256[8], x[NW];
@@ -126,12 +193,16 @@ template <class P>
 __global__ void __launch_bounds__(128) vleaf_kernel(const KeyBlock* __restrict__ keys,
                                                     const MsgInfo* __restrict__ infos, uint32_t count,
                                                     const uint8_t* __restrict__ sigs, const uint32_t* __restrict__ ends,
-                                                    uint32_t* __restrict__ vroot, uint32_t j) {
+                                                    uint32_t* __restrict__ vroot, uint32_t j,
+                                                    uint32_t* __restrict__ cnt_next, uint32_t* __restrict__ sitem) {
     constexpr int NW = P::NW, LEN = P::LEN, HP = P::HP;
     const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= count) return;
     const MsgInfo& info = infos[m];
-    if (info.key == KEY_INVALID) return;
+    if (info.key == KEY_INVALID) {
+        if (cnt_next) count_steps<P>(vroot + (size_t)m * NW, false, m, cnt_next, sitem);
+        return;
+    }
     const KeyBlock& kb = keys[info.key];
     uint32_t ms256[8], msT[P::BIG ? 16 : 8];
 #pragma unroll
@@ -163,6 +234,7 @@ __global__ void __launch_bounds__(128) vleaf_kernel(const KeyBlock* __restrict__
     }
 #pragma unroll
     for (int w = 0; w < NW; w++) vroot[(size_t)m * NW + w] = node[w];
+    if (cnt_next) count_steps<P>(node, true, m, cnt_next, sitem);   // the next layer's chains
 }
 
 // ok[m] = 1 iff the top root equals PK.root.

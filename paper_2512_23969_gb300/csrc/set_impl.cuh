@@ -163,19 +163,34 @@ struct SetImpl {
     // Verification: FORS roots, PK_FORS, then per layer chains and T_len +
     // climbs (layers are serial), then the comparison with PK.root.  The
     // layer messages live in pk_fors (layer 0) and roots (layers >= 1).
+    // Scratch: fors_roots, pk_fors, roots (root_j of the current layer),
+    // ends (chain ends of one layer), vcnt (16 step buckets per layer),
+    // vsitem / vorder (one word per chain of a layer).
     static cudaError_t verify(const Batch& b, cudaStream_t s) {
         const uint32_t T = 128;
+        cudaError_t e = cudaMemsetAsync(b.vcnt, 0, sizeof(uint32_t) * 16 * P::D, s);
         const uint64_t ft = (uint64_t)b.count * P::K;
-        vfors_kernel<P><<<(uint32_t)((ft + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.fors_roots);
-        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            vfors_kernel<P><<<(uint32_t)((ft + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.sigs,
+                                                                       b.fors_roots);
+            e = cudaGetLastError();
+        }
         if (e == cudaSuccess) e = fors_pk(b, s);
         const uint64_t ct = (uint64_t)b.count * P::LEN;
         const uint32_t G1 = (b.count + T - 1) / T;
+        if (e == cudaSuccess) {
+            vcount0_kernel<P><<<G1, T, 0, s>>>(b.infos, b.count, b.pk_fors, b.vcnt, b.vsitem);
+            e = cudaGetLastError();
+        }
         for (uint32_t j = 0; j < (uint32_t)P::D && e == cudaSuccess; j++) {
-            vchain_kernel<P, kChainPol><<<(uint32_t)((ct + T - 1) / T), T, 0, s>>>(
-                b.keys, b.infos, b.count, b.sigs, j == 0 ? b.pk_fors : b.roots, b.ends, j, 1u);
+            vscatter_kernel<P><<<(uint32_t)((ct + 255) / 256), 256, 0, s>>>(b.count, b.vcnt + 16 * j, b.vsitem,
+                                                                            b.vorder);
             if ((e = cudaGetLastError()) != cudaSuccess) break;
-            vleaf_kernel<P><<<G1, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.ends, b.roots, j);
+            vchain_kernel<P, kChainPol><<<(uint32_t)((ct + T - 1) / T), T, 0, s>>>(
+                b.keys, b.infos, b.count, b.sigs, b.vorder, b.vsitem, b.ends, j, 1u);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            vleaf_kernel<P><<<G1, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.ends, b.roots, j,
+                                             j + 1 < (uint32_t)P::D ? b.vcnt + 16 * (j + 1) : nullptr, b.vsitem);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) return e;
