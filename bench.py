@@ -489,6 +489,34 @@ def measure_serving(hs, inputs, seconds, rhos, burst=60000):
     return out
 
 
+def run_verify_only(args):
+    """Verification of the bench batch: 1 signing call, then 3 timed
+    hs_verify_batch calls (CUDA events); prints one JSON line."""
+    import torch
+    from paper_2512_23969_gb300 import build as hs_build
+    hs_build.build()
+    from paper_2512_23969_gb300 import hs, inputs
+    hs.load()
+    ps = args.params
+    wl = inputs.config(1) if ps == "128f" and args.count == 16384 else \
+        inputs.make(ps, args.count, 16, 32, inputs.BASE_SEED + 1, "%s-16keys-%dx32B" % (ps, args.count))
+    pk, sk = hs.hs_keygen(ps, torch.from_numpy(wl.seeds).cuda())
+    m, l, k = (torch.from_numpy(x).cuda() for x in (wl.msgs, wl.lens, wl.key_idx))
+    sig = hs.hs_sign_batch(ps, sk, m, l, key_idx=k, num_keys=wl.num_keys)
+    ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ok = hs.hs_verify_batch(ps, pk, m, l, sig, key_idx=k, num_keys=wl.num_keys)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"metric": "verifications/s", "value": round(wl.count / (min(ms) / 1e3), 1),
+                      "ms": [round(x, 3) for x in ms], "accepted": int(ok.sum().item()), "count": wl.count,
+                      "params": ps}))
+    return 0
+
+
 def run_own(args):
     import numpy as np
     import torch
@@ -697,6 +725,8 @@ def main():
                     help="skip the 192f / 256f / mixed-parameter measurements")
     ap.add_argument("--serving-seconds", type=float, default=3.0,
                     help="seconds of Poisson load per rate in the serving measurement (0 = skip)")
+    ap.add_argument("--verify-only", action="store_true",
+                    help="sign the batch once, then time hs_verify_batch on it (3 calls) and print one line")
     ap.add_argument("--count", type=int, default=16384,
                     help="messages per step (smaller counts are for profiler captures)")
     args = ap.parse_args()
@@ -704,6 +734,8 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.verify_only:
+        return run_verify_only(args)
     return run_own(args)
 
 

@@ -176,12 +176,17 @@ __global__ void fors_pk_kernel(const KeyBlock* __restrict__ keys, const MsgInfo*
     if (info.key == KEY_INVALID) return;
     const KeyBlock& kb = keys[info.key];
     constexpr int NW = P::NW;
-    TStreamP<P> ts;
-    ts.init(P::BIG ? kb.ms512 : kb.ms256, make_adrs(0, info.idx_tree, T_FORS_ROOTS, info.idx_leaf, 0, 0));
     const uint32_t* r = fors_roots + (size_t)m * P::K * NW;
-    for (int i = 0; i < P::K; i++) ts.template push_n<NW>(r + i * NW);
+    const Adrs a = make_adrs(0, info.idx_tree, T_FORS_ROOTS, info.idx_leaf, 0, 0);
     uint32_t out[NW];
-    ts.template finish<NW>(P::K * P::N, out);
+    if constexpr (P::SHAKE) {
+        TStreamP<P> ts;
+        ts.init(kb.ms256, a);
+        for (int i = 0; i < P::K; i++) ts.template push_n<NW>(r + i * NW);
+        ts.template finish<NW>(P::K * P::N, out);
+    } else {
+        tl_from_mem<P::BIG, P::K * NW, NW>(P::BIG ? kb.ms512 : kb.ms256, a, r, out);
+    }
 #pragma unroll
     for (int w = 0; w < NW; w++) pk_fors[(size_t)m * NW + w] = out[w];
 }

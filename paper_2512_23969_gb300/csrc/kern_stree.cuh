@@ -77,13 +77,18 @@ __global__ void __launch_bounds__(128) bleaf_from_ends_kernel(const KeyBlock* __
     if (info.key == KEY_INVALID) return;
     const KeyBlock& kb = keys[info.key];
     const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
-    TStreamP<P> ts;
-    ts.init(P::BIG ? kb.ms512 : kb.ms256, make_adrs(j, tree, T_WOTS_PK, l, 0, 0));
     const uint32_t* e = ends + (size_t)gid * LEN * NW;
-#pragma unroll 1
-    for (int i = 0; i < LEN; i++) ts.template push_n<NW>(e + i * NW);
     uint32_t node[NW];
-    ts.template finish<NW>(LEN * P::N, node);
+    if constexpr (P::SHAKE) {
+        TStreamP<P> ts;
+        ts.init(kb.ms256, make_adrs(j, tree, T_WOTS_PK, l, 0, 0));
+#pragma unroll 1
+        for (int i = 0; i < LEN; i++) ts.template push_n<NW>(e + i * NW);
+        ts.template finish<NW>(LEN * P::N, node);
+    } else {
+        tl_from_mem<P::BIG, LEN * NW, NW>(P::BIG ? kb.ms512 : kb.ms256, make_adrs(j, tree, T_WOTS_PK, l, 0, 0), e,
+                                          node);
+    }
     uint32_t* out = leafv + (((size_t)m * P::D + j) * LV + l) * NW;
 #pragma unroll
     for (int w = 0; w < NW; w++) out[w] = node[w];

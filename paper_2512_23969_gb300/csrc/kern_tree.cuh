@@ -231,13 +231,17 @@ __global__ void __launch_bounds__(128) leaves_kernel(const KeyBlock* __restrict_
     for (int w = 0; w < (P::BIG ? 16 : 8); w++) msT[w] = P::BIG ? kb.ms512[w] : kb.ms256[w];
     const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
     const uint32_t sl = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
-    TStreamP<P> ts;
-    ts.init(msT, make_adrs(j, tree, T_WOTS_PK, l, 0, 0));
     const uint32_t* e = ends + (size_t)gid * LEN * NW;
-#pragma unroll 1
-    for (int i = 0; i < LEN; i++) ts.template push_n<NW>(e + i * NW);
     uint32_t node[NW];
-    ts.template finish<NW>(LEN * P::N, node);
+    if constexpr (P::SHAKE) {
+        TStreamP<P> ts;
+        ts.init(msT, make_adrs(j, tree, T_WOTS_PK, l, 0, 0));
+#pragma unroll 1
+        for (int i = 0; i < LEN; i++) ts.template push_n<NW>(e + i * NW);
+        ts.template finish<NW>(LEN * P::N, node);
+    } else {
+        tl_from_mem<P::BIG, LEN * NW, NW>(msT, make_adrs(j, tree, T_WOTS_PK, l, 0, 0), e, node);
+    }
     merkle_finish<P>(ms256, msT, gmask, m, j, l, sl, tree, node, sigs, roots);
 }
 

@@ -87,24 +87,44 @@ __device__ __forceinline__ uint32_t wots_digit(const uint32_t* msg, uint32_t i) 
 constexpr uint32_t kRankBits = 28;        // sitem = steps << 28 | rank within the steps bucket
 
 // For message m's layer: each chain's step count, counted into the layer's
-// 16 buckets (one atomic per non-empty bucket), with the chain's rank inside
-// its bucket recorded in sitem.  Messages with an invalid key count as 0 steps.
+// 16 buckets, with the chain's rank inside its bucket recorded in sitem.
+// Called by all 32 lanes of a warp, converged (inactive lanes count
+// nothing): per bucket the warp scans its lanes' counts with shuffles and
+// one lane adds the warp's total with a single atomic, so the 16 counters
+// see one atomic per warp instead of one per thread.  Messages with an
+// invalid key count as 0 steps.
 template <class P>
-__device__ __forceinline__ void count_steps(const uint32_t* msg, bool valid, uint64_t m, uint32_t* __restrict__ cnt,
-                                            uint32_t* __restrict__ sitem) {
+__device__ __forceinline__ void count_steps(const uint32_t* msg, bool active, bool valid, uint64_t m,
+                                            uint32_t* __restrict__ cnt, uint32_t* __restrict__ sitem) {
     constexpr int LEN = P::LEN;
+    const uint32_t lane = threadIdx.x & 31;
     uint32_t hist[16];
 #pragma unroll
     for (int b = 0; b < 16; b++) hist[b] = 0;
+    if (active) {
 #pragma unroll 1
-    for (uint32_t i = 0; i < (uint32_t)LEN; i++) {
-        const uint32_t st = valid ? 15u - wots_digit<P>(msg, i) : 0u;
+        for (uint32_t i = 0; i < (uint32_t)LEN; i++) {
+            const uint32_t st = valid ? 15u - wots_digit<P>(msg, i) : 0u;
 #pragma unroll
-        for (int b = 0; b < 16; b++) hist[b] += (st == (uint32_t)b) ? 1u : 0u;
+            for (int b = 0; b < 16; b++) hist[b] += (st == (uint32_t)b) ? 1u : 0u;
+        }
     }
     uint32_t base[16];
 #pragma unroll
-    for (int b = 0; b < 16; b++) base[b] = hist[b] ? atomicAdd(&cnt[b], hist[b]) : 0u;
+    for (int b = 0; b < 16; b++) {
+        uint32_t x = hist[b];                       // inclusive scan over the lanes
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if (lane >= (uint32_t)off) x += y;
+        }
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
+        uint32_t wbase = 0;
+        if (lane == 31 && total) wbase = atomicAdd(&cnt[b], total);
+        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
+        base[b] = wbase + x - hist[b];
+    }
+    if (!active) return;
 #pragma unroll 1
     for (uint32_t i = 0; i < (uint32_t)LEN; i++) {
         const uint32_t st = valid ? 15u - wots_digit<P>(msg, i) : 0u;
@@ -116,17 +136,18 @@ __device__ __forceinline__ void count_steps(const uint32_t* msg, bool valid, uin
     }
 }
 
-// Layer 0: count from PK_FORS.
+// Layer 0: count from PK_FORS (every lane of every warp takes part).
 template <class P>
 __global__ void __launch_bounds__(128) vcount0_kernel(const MsgInfo* __restrict__ infos, uint32_t count,
                                                       const uint32_t* __restrict__ pk_fors, uint32_t* __restrict__ cnt,
                                                       uint32_t* __restrict__ sitem) {
     const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= count) return;
+    const bool active = m < count;
+    const bool valid = active && infos[m].key != KEY_INVALID;
     uint32_t msg[P::NW];
 #pragma unroll
-    for (int w = 0; w < P::NW; w++) msg[w] = pk_fors[(size_t)m * P::NW + w];
-    count_steps<P>(msg, infos[m].key != KEY_INVALID, m, cnt, sitem);
+    for (int w = 0; w < P::NW; w++) msg[w] = active ? pk_fors[(size_t)m * P::NW + w] : 0u;
+    count_steps<P>(msg, active, valid, m, cnt, sitem);
 }
 
 // Place every chain of the layer at its sorted position (longest first).
@@ -187,22 +208,12 @@ __global__ void __launch_bounds__(128) vchain_kernel(const KeyBlock* __restrict_
     for (int w = 0; w < NW; w++) e[w] = x[w];
 }
 
-// Layer j of message m: T_len over the chain ends, then h' climbs with the
-// auth path; root_j replaces msg_j in vroot.
+// root_j of message m: T_len over its chain ends, h' climbs with the auth path.
 template <class P>
-__global__ void __launch_bounds__(128) vleaf_kernel(const KeyBlock* __restrict__ keys,
-                                                    const MsgInfo* __restrict__ infos, uint32_t count,
-                                                    const uint8_t* __restrict__ sigs, const uint32_t* __restrict__ ends,
-                                                    uint32_t* __restrict__ vroot, uint32_t j,
-                                                    uint32_t* __restrict__ cnt_next, uint32_t* __restrict__ sitem) {
+__device__ __forceinline__ void layer_root(const KeyBlock* __restrict__ keys, const MsgInfo& info,
+                                           const uint8_t* __restrict__ sigs, const uint32_t* __restrict__ ends,
+                                           uint32_t m, uint32_t j, uint32_t* node, uint32_t* __restrict__ vroot) {
     constexpr int NW = P::NW, LEN = P::LEN, HP = P::HP;
-    const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= count) return;
-    const MsgInfo& info = infos[m];
-    if (info.key == KEY_INVALID) {
-        if (cnt_next) count_steps<P>(vroot + (size_t)m * NW, false, m, cnt_next, sitem);
-        return;
-    }
     const KeyBlock& kb = keys[info.key];
     uint32_t ms256[8], msT[P::BIG ? 16 : 8];
 #pragma unroll
@@ -211,13 +222,16 @@ __global__ void __launch_bounds__(128) vleaf_kernel(const KeyBlock* __restrict__
     for (int w = 0; w < (P::BIG ? 16 : 8); w++) msT[w] = P::BIG ? kb.ms512[w] : kb.ms256[w];
     const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
     const uint32_t kp = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
-    TStreamP<P> ts;
-    ts.init(msT, make_adrs(j, tree, T_WOTS_PK, kp, 0, 0));
     const uint32_t* e = ends + (size_t)m * LEN * NW;
+    if constexpr (P::SHAKE) {
+        TStreamP<P> ts;
+        ts.init(msT, make_adrs(j, tree, T_WOTS_PK, kp, 0, 0));
 #pragma unroll 1
-    for (int i = 0; i < LEN; i++) ts.template push_n<NW>(e + i * NW);
-    uint32_t node[NW];
-    ts.template finish<NW>(LEN * P::N, node);
+        for (int i = 0; i < LEN; i++) ts.template push_n<NW>(e + i * NW);
+        ts.template finish<NW>(LEN * P::N, node);
+    } else {
+        tl_from_mem<P::BIG, LEN * NW, NW>(msT, make_adrs(j, tree, T_WOTS_PK, kp, 0, 0), e, node);
+    }
     const uint8_t* auth = sigs + (size_t)m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES +
                           (size_t)LEN * P::N;
 #pragma unroll 1
@@ -234,7 +248,26 @@ __global__ void __launch_bounds__(128) vleaf_kernel(const KeyBlock* __restrict__
     }
 #pragma unroll
     for (int w = 0; w < NW; w++) vroot[(size_t)m * NW + w] = node[w];
-    if (cnt_next) count_steps<P>(node, true, m, cnt_next, sitem);   // the next layer's chains
+}
+
+// Layer j of message m: T_len over the chain ends, then h' climbs with the
+// auth path; root_j replaces msg_j in vroot.
+template <class P>
+__global__ void __launch_bounds__(128) vleaf_kernel(const KeyBlock* __restrict__ keys,
+                                                    const MsgInfo* __restrict__ infos, uint32_t count,
+                                                    const uint8_t* __restrict__ sigs, const uint32_t* __restrict__ ends,
+                                                    uint32_t* __restrict__ vroot, uint32_t j,
+                                                    uint32_t* __restrict__ cnt_next, uint32_t* __restrict__ sitem) {
+    constexpr int NW = P::NW;
+    const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = m < count;
+    const bool valid = active && infos[m].key != KEY_INVALID;
+    uint32_t node[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) node[w] = 0;
+    if (valid) layer_root<P>(keys, infos[m], sigs, ends, m, j, node, vroot);
+    __syncwarp();
+    if (cnt_next) count_steps<P>(node, active, valid, m, cnt_next, sitem);   // the next layer's chains
 }
 
 // ok[m] = 1 iff the top root equals PK.root.
