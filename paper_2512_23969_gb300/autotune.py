@@ -22,8 +22,8 @@ from . import hs, inputs
 KNOBS = {"fors_lanes": 0, "tree_min_blocks": 1, "tree_split_below": 2}
 STAGE_OF_KNOB = {"fors_lanes": "fors", "tree_min_blocks": "tree"}
 DEFAULT_COUNTS = {"128f": 16384, "192f": 8192, "256f": 8192, "toy": 4096, "128s": 512, "192s": 256, "256s": 256,
-                  "shake-128f": 4096, "shake-192f": 2048, "shake-256f": 2048, "shake-128s": 128, "shake-192s": 64,
-                  "shake-256s": 64}
+                  "shake-128f": 4096, "shake-192f": 2048, "shake-256f": 2048, "shake-128s": 256, "shake-192s": 256,
+                  "shake-256s": 256}
 # batch sizes at which the two TREE_Sign forms are compared, per family
 SPLIT_COUNTS = {"f": (64, 256, 1024, 2048, 4096, 8192), "s": (8, 16, 32, 64, 128, 256),
                 "shake-f": (64, 256, 1024, 2048, 4096, 8192), "shake-s": (4, 8, 16, 32, 64, 128)}
