@@ -324,7 +324,7 @@ hs_status hs_set_tree_sharing(int on);
 
 /*
  * FIPS 205 (SLH-DSA) mode -- a variant; the paper signs with SPHINCS+
- * round 3.1.  At the SHA2 128f/192f/256f sets FIPS 205 keeps the keys,
+ * round 3.1.  At every set here (SHA2 and SHAKE) FIPS 205 keeps the keys,
  * tweakable hashes, addresses and sizes and changes two things: the FORS
  * indices are the base-2^a digits of md read most significant bit first
  * (base_2b), and pure signing signs M' = 0x00 || len(ctx) || ctx || M.

@@ -1,4 +1,5 @@
-// hs_common.cuh -- tweakable hashes of SPHINCS+ SHA2-simple on device.
+// hs_common.cuh -- tweakable hashes of SPHINCS+ SHA2-simple on device (the
+// SHAKE instantiation branches to keccak.cuh where a set asks for it).
 //
 // All n-byte values live in registers as n/4 big-endian 32-bit words (the
 // natural SHA-2 word order, so digests chain into the next message block

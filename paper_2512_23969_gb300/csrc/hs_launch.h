@@ -1,7 +1,8 @@
 // hs_launch.h -- host-side launchers of the signer's kernels (library
 // internal; the public surface is include/hs.h).  Each launcher dispatches
-// on the parameter set id (0 128f, 1 192f, 2 256f, 3 toy) to the kernel
-// template instantiated for that set.
+// on the parameter set id (0 128f, 1 192f, 2 256f, 3 toy, 4-6 128s-256s,
+// 7-12 the SHAKE instantiations of 0-2 and 4-6) to the kernel template
+// instantiated for that set.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>

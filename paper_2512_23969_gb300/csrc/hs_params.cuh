@@ -1,5 +1,6 @@
-// hs_params.cuh -- compile-time parameter sets (paper Table 1) and the
-// sizes derived from them.  Every kernel is instantiated once per set.
+// hs_params.cuh -- compile-time parameter sets (paper Table 1, and the s and
+// SHAKE variants) and the sizes derived from them.  Every kernel is
+// instantiated once per set.
 #pragma once
 #include <cstdint>
 
@@ -21,7 +22,7 @@ struct Params {
     static constexpr bool BIG = !SHAKE_ && (N_ > 16);
     static constexpr int NW = N_ / 4;              // n in 32-bit words
     static constexpr int LEN1 = 2 * N_;            // 8n / log2(w)
-    static constexpr int LEN2 = 3;                 // all three sets (and toy)
+    static constexpr int LEN2 = 3;                 // every set here (and toy): n = 16 .. 32 at w = 16
     static constexpr int LEN = LEN1 + LEN2;
     static constexpr int TREE_BITS = H_ - HP;
     static constexpr int MD_BYTES = (K_ * A_ + 7) / 8;
