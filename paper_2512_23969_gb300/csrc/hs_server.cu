@@ -254,11 +254,12 @@ bool admit(ServerImpl& sv, Slot& slot) {
     for (size_t i = 0; i < count; i++) {
         const uint64_t id = sv.pending[p].front();
         sv.pending[p].pop_front();
-        const Request& r = sv.reqs[id];
+        Request& r = sv.reqs[id];
         if (!r.msg.empty()) memcpy(h + mo, r.msg.data(), r.msg.size());
         mo += r.msg.size();
         reinterpret_cast<uint64_t*>(h + o_lens)[i] = r.msg.size();
         reinterpret_cast<uint32_t*>(h + o_kidx)[i] = r.key;
+        std::vector<uint8_t>().swap(r.msg);       // staged: the copy is no longer needed
         slot.ids.push_back(id);
     }
     Batch b{};
@@ -492,25 +493,14 @@ HS_API hs_status hs_server_replay(hs_server* s, uint32_t count, const uint8_t* p
     std::vector<uint64_t> ids(count);
     std::unordered_map<uint64_t, uint32_t> index;
     index.reserve(count * 2 + 16);
-    const uint64_t t0 = now_ns();
-    for (uint32_t i = 0; i < count; i++) {
-        const uint64_t due = t0 + arrival_ns[i];
-        for (uint64_t t = now_ns(); t < due; t = now_ns()) {
-            if (due - t > 200000) std::this_thread::sleep_for(std::chrono::nanoseconds(due - t - 100000));
-        }
-        const uint32_t q = pool_idx[i];
-        // latency is measured from the scheduled arrival, not from the submit
-        hs_status st = submit_at(s, (hs_params)params[i], keys[i], pool_msgs ? pool_msgs + pool_off[q] : nullptr,
-                                 pool_lens[q], sigs ? sigs + sig_offsets[i] : nullptr, &ids[i], due);
-        if (st != HS_OK) return st;
-        index[ids[i]] = i;
-    }
     uint32_t got = 0;
     std::vector<uint64_t> cid(4096), lat(4096);
     std::vector<int32_t> cst(4096);
     hs_status worst = HS_OK;
-    const uint64_t deadline = now_ns() + (uint64_t)timeout_ms * 1000000ull;
-    while (got < count) {
+    // collect finished requests as they come, so the server's request table
+    // stays small during a long run (it is a hash map guarded by the
+    // scheduler's mutex)
+    auto drain = [&]() {
         const int n = hs_server_poll(s, cid.data(), lat.data(), cst.data(), (int)cid.size());
         for (int k = 0; k < n; k++) {
             auto it = index.find(cid[k]);
@@ -520,6 +510,33 @@ HS_API hs_status hs_server_replay(hs_server* s, uint32_t count, const uint8_t* p
                 if (cst[k] != HS_OK && worst == HS_OK) worst = (hs_status)cst[k];
             }
         }
+        return n;
+    };
+    const uint64_t t0 = now_ns();
+    uint64_t last_drain = t0;
+    for (uint32_t i = 0; i < count; i++) {
+        const uint64_t due = t0 + arrival_ns[i];
+        for (uint64_t t = now_ns(); t < due; t = now_ns()) {
+            if (due - t > 200000) {
+                drain();
+                last_drain = now_ns();
+                if (due > last_drain + 100000) std::this_thread::sleep_for(std::chrono::nanoseconds(due - last_drain - 100000));
+            }
+        }
+        const uint32_t q = pool_idx[i];
+        // latency is measured from the scheduled arrival, not from the submit
+        hs_status st = submit_at(s, (hs_params)params[i], keys[i], pool_msgs ? pool_msgs + pool_off[q] : nullptr,
+                                 pool_lens[q], sigs ? sigs + sig_offsets[i] : nullptr, &ids[i], due);
+        if (st != HS_OK) return st;
+        index[ids[i]] = i;
+        if (now_ns() - last_drain > 1000000) {      // at least once a millisecond while submitting
+            drain();
+            last_drain = now_ns();
+        }
+    }
+    const uint64_t deadline = now_ns() + (uint64_t)timeout_ms * 1000000ull;
+    while (got < count) {
+        drain();
         if (got >= count) break;
         if (now_ns() > deadline) return sv_fail(HS_ETIMEOUT, "hs_server_replay: requests still pending at the timeout");
         std::unique_lock<std::mutex> lk(sv.mu);
