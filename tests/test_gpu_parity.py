@@ -211,3 +211,52 @@ def test_invalid_arguments(hs):
     assert L.hs_sign_batch(0, sk.data_ptr(), 1, None, None, lens.data_ptr(), 0, sigs.data_ptr(), None) == 0
     with pytest.raises(HSError):
         hs.hs_sign_batch("128f", sk, None, lens, num_keys=0)
+
+
+@pytest.mark.parametrize("ps", ["192f", "256f"])
+def test_config2_full_size(hs, O, ps):
+    """192f / 256f, 16 keys, 8192 messages of U{32..1024} bytes in one call
+    (the bench's launch shape for these sets): oracle on the seeded
+    32-message subset, GPU verify accepts all."""
+    import torch
+    wl = inputs.config(2, ps)
+    assert wl.count == 8192 and wl.num_keys == 16
+    pk, sk = hs.hs_keygen(ps, _dev(wl.seeds))
+    msgs, lens, kidx = _dev(wl.msgs), _dev(wl.lens), _dev(wl.key_idx)
+    sigs = hs.hs_sign_batch(ps, sk, msgs, lens, key_idx=kidx, num_keys=16)
+    ok = hs.hs_verify_batch(ps, pk, msgs, lens, sigs, key_idx=kidx, num_keys=16)
+    torch.cuda.synchronize()
+    assert int(ok.sum().item()) == wl.count
+    got = sigs.cpu().numpy()
+    _, osk = _oracle_keys(O, ps, wl.seeds)
+    want = _oracle_sign_many(O, ps, osk, wl, list(wl.subset))
+    _compare(O, ps, got, want, list(wl.subset))
+
+
+def test_mixed_full_size_graph(hs, O):
+    """The mixed recipe at full size -- 32768 messages 50/30/20 over
+    128f/192f/256f, log-uniform 16 B - 64 KB, 64 keys -- in one graph launch:
+    GPU verify accepts all, and 4 seeded messages per set equal the oracle."""
+    import numpy as np
+    import torch
+    wls = inputs.mixed()
+    assert sum(wl.count for wl in wls) == 32768
+    jobs, pks = [], []
+    for wl in wls:
+        pk, sk = hs.hs_keygen(wl.params, _dev(wl.seeds))
+        pks.append(pk)
+        jobs.append({"params": wl.params, "sk": sk, "msgs": _dev(wl.msgs), "lens": _dev(wl.lens),
+                     "key_idx": _dev(wl.key_idx), "num_keys": wl.num_keys,
+                     "sigs": torch.empty(wl.count * hs.sig_bytes(wl.params), dtype=torch.uint8, device="cuda")})
+    hs.hs_sign_mixed(jobs, use_graph=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(23969)
+    for wl, j, pk in zip(wls, jobs, pks):
+        sig = j["sigs"].view(wl.count, -1)
+        ok = hs.hs_verify_batch(wl.params, pk, j["msgs"], j["lens"], sig, key_idx=j["key_idx"],
+                                num_keys=wl.num_keys)
+        assert int(ok.sum().item()) == wl.count, wl.params
+        sample = sorted(rng.choice(wl.count, 4, replace=False).tolist())
+        _, osk = _oracle_keys(O, wl.params, wl.seeds)
+        want = _oracle_sign_many(O, wl.params, osk, wl, sample)
+        _compare(O, wl.params, sig.cpu().numpy(), want, sample)
