@@ -35,8 +35,12 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
                                           uint32_t layer, uint64_t tree, uint32_t kp, uint32_t* out,
                                           uint32_t* chk, uint32_t ck, const Pipes<POL>& pp) {
     constexpr int NW = P::NW;
+    // SHA-2: chain ends go to a per-thread array (local memory) and T_len
+    // runs over it afterwards, so no hash state is live across the chain
+    // loop; SHAKE streams them into its own buffer.
+    uint32_t ends[P::SHAKE ? 1 : P::LEN * NW];
     TStreamP<P> ts;
-    ts.init(msT, make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0));
+    if constexpr (P::SHAKE) ts.init(msT, make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0));
     const Adrs aprf = make_adrs(layer, tree, T_WOTS_PRF, kp, 0, 0);
     const Adrs ahash = make_adrs(layer, tree, T_WOTS_HASH, kp, 0, 0);
     const uint32_t per_chain = ck ? 16u / ck : 0u;
@@ -69,9 +73,15 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
                 for (int w = 0; w < NW; w++) d[w] = x[w];
             }
         }
-        ts.template push_n<NW>(x);
+        if constexpr (P::SHAKE) {
+            ts.template push_n<NW>(x);
+        } else {
+#pragma unroll
+            for (int w = 0; w < NW; w++) ends[i * NW + w] = x[w];
+        }
     }
-    ts.template finish<NW>(P::LEN * P::N, out);
+    if constexpr (P::SHAKE) ts.template finish<NW>(P::LEN * P::N, out);
+    else tl_from_mem<P::BIG, P::LEN * NW, NW>(msT, make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0), ends, out);
 }
 
 // Merkle levels of one XMSS tree held by an aligned lane group (one leaf
