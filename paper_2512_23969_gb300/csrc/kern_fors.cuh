@@ -8,8 +8,8 @@
 // GB300 mapping (ours, not the paper's Tree Fusion): a tree is owned by an
 // aligned group of LPT lanes of one warp.  Each lane builds a subtree of
 // height R = a - log2(LPT) over 2^R consecutive leaves with a register
-// treehash (one H call site, left siblings kept in a small select-indexed
-// stack), then the top log2(LPT) levels are merged across the group with
+// treehash (one H call site, left siblings in a small stack, SibStack),
+// then the top log2(LPT) levels are merged across the group with
 // warp shuffles.  Lane subtrees taller than 7 levels (a = 12-14 of the s
 // sets) are built as 2^(R-7) consecutive height-7 subtrees whose roots are
 // merged through a second stack of at most 3 nodes.  No shared memory and no block barriers; the grid is flat
@@ -24,6 +24,70 @@ namespace hs {
 
 template <int L> struct Log2 { static constexpr int v = 1 + Log2<L / 2>::v; };
 template <> struct Log2<1> { static constexpr int v = 0; };
+
+// Left siblings of a lane's treehash: levels 0..RI-1 (inner subtrees) and
+// RI..R-1 (outer merges).  LOCAL: one per-thread array at run-time indices
+// (local memory) -- no registers, no select chains; measured faster for
+// lane subtrees of up to 7 levels.  Otherwise registers read through
+// select chains (faster for the 9-10 level subtrees of the s sets).
+template <int R, int RI, int NW, bool LOCAL>
+struct SibStack;
+
+template <int R, int RI, int NW>
+struct SibStack<R, RI, NW, true> {
+    uint32_t v[R * NW];
+    __device__ __forceinline__ void load(uint32_t z, uint32_t* o) const {
+#pragma unroll
+        for (int w = 0; w < NW; w++) o[w] = v[z * NW + w];
+    }
+    __device__ __forceinline__ void store(uint32_t z, const uint32_t* x) {
+#pragma unroll
+        for (int w = 0; w < NW; w++) v[z * NW + w] = x[w];
+    }
+    __device__ __forceinline__ void load_outer(uint32_t z, uint32_t* o) const { load(z, o); }
+    __device__ __forceinline__ void store_outer(uint32_t z, const uint32_t* x) { store(z, x); }
+};
+
+template <int R, int RI, int NW>
+struct SibStack<R, RI, NW, false> {
+    static constexpr int RO = R - RI;
+    uint32_t in[RI][NW];
+    uint32_t out[RO > 0 ? RO : 1][NW];
+    __device__ __forceinline__ void load(uint32_t z, uint32_t* o) const {
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            uint32_t v = in[0][w];
+#pragma unroll
+            for (int zz = 1; zz < RI; zz++) v = (z == (uint32_t)zz) ? in[zz][w] : v;
+            o[w] = v;
+        }
+    }
+    __device__ __forceinline__ void store(uint32_t z, const uint32_t* x) {
+#pragma unroll
+        for (int zz = 0; zz < RI; zz++)
+            if (z == (uint32_t)zz) {
+#pragma unroll
+                for (int w = 0; w < NW; w++) in[zz][w] = x[w];
+            }
+    }
+    __device__ __forceinline__ void load_outer(uint32_t z, uint32_t* o) const {
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            uint32_t v = out[0][w];
+#pragma unroll
+            for (int zz = 1; zz < RO; zz++) v = (z - RI == (uint32_t)zz) ? out[zz][w] : v;
+            o[w] = v;
+        }
+    }
+    __device__ __forceinline__ void store_outer(uint32_t z, const uint32_t* x) {
+#pragma unroll
+        for (int zz = 0; zz < RO; zz++)
+            if (z - RI == (uint32_t)zz) {
+#pragma unroll
+                for (int w = 0; w < NW; w++) out[zz][w] = x[w];
+            }
+    }
+};
 
 template <class P, int POL, int LPT>
 __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ keys,
@@ -63,8 +127,7 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
     uint8_t* sf = sigs + (size_t)m * P::SIG_BYTES + P::N + (size_t)i * (A + 1) * P::N;
 
     const Pipes<POL> pp(one);
-    uint32_t stk[RI][NW];                          // left siblings, levels 0..RI-1
-    uint32_t ostk[RO > 0 ? RO : 1][NW];            // left siblings, levels RI..R-1
+    SibStack<R, RI, NW, (R <= 7)> stk;                 // left siblings, levels 0..R-1
     uint32_t node[NW];
     const uint32_t base = L << R;                  // first leaf of this lane (within tree)
 #pragma unroll 1
@@ -89,28 +152,16 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
 #pragma unroll 1
             while ((idx & 1u) && z < (uint32_t)RI) {
                 uint32_t lr[2 * NW];
+                stk.load(z, lr);
 #pragma unroll
-                for (int w = 0; w < NW; w++) {
-                    uint32_t v = stk[0][w];
-#pragma unroll
-                    for (int zz = 1; zz < RI; zz++) v = (z == (uint32_t)zz) ? stk[zz][w] : v;
-                    lr[w] = v;
-                    lr[NW + w] = node[w];
-                }
+                for (int w = 0; w < NW; w++) lr[NW + w] = node[w];
                 z++;
                 idx >>= 1;
                 hashH_ms<P>(ms256, ms512,
                             make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node);
                 if (z < (uint32_t)A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
             }
-            if (z < (uint32_t)RI) {
-#pragma unroll
-                for (int zz = 0; zz < RI; zz++)
-                    if (z == (uint32_t)zz) {
-#pragma unroll
-                        for (int w = 0; w < NW; w++) stk[zz][w] = node[w];
-                    }
-            }
+            if (z < (uint32_t)RI) stk.store(z, node);
         }
         if constexpr (RO > 0) {
             // node = root of inner subtree ob (level RI); merge with the outer stack
@@ -118,28 +169,16 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
 #pragma unroll 1
             while ((idx & 1u) && z < (uint32_t)R) {
                 uint32_t lr[2 * NW];
+                stk.load_outer(z, lr);
 #pragma unroll
-                for (int w = 0; w < NW; w++) {
-                    uint32_t v = ostk[0][w];
-#pragma unroll
-                    for (int zz = 1; zz < RO; zz++) v = (z - RI == (uint32_t)zz) ? ostk[zz][w] : v;
-                    lr[w] = v;
-                    lr[NW + w] = node[w];
-                }
+                for (int w = 0; w < NW; w++) lr[NW + w] = node[w];
                 z++;
                 idx >>= 1;
                 hashH_ms<P>(ms256, ms512,
                             make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node);
                 if (z < (uint32_t)A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
             }
-            if (z < (uint32_t)R) {
-#pragma unroll
-                for (int zz = 0; zz < RO; zz++)
-                    if (z - RI == (uint32_t)zz) {
-#pragma unroll
-                        for (int w = 0; w < NW; w++) ostk[zz][w] = node[w];
-                    }
-            }
+            if (z < (uint32_t)R) stk.store_outer(z, node);
         }
     }
     // node = lane subtree root, level R, index L within the tree
