@@ -349,7 +349,8 @@ def keccak_f1600(lanes):
 
 
 def counters(reset=False):
-    """[SHA-256 blocks, SHA-512 blocks, F, PRF, H, T] of the calling thread."""
-    out = (C.c_uint64 * 6)()
+    """[SHA-256 blocks, SHA-512 blocks, F, PRF, H, T, Keccak permutations] of
+    the calling thread."""
+    out = (C.c_uint64 * 7)()
     lib().oracle_counters(out, 1 if reset else 0)
     return list(out)

@@ -217,7 +217,7 @@ static void sha512_block(uint64_t H[8], const uint8_t blk[128])
 
 /* Per-thread call counters (instrumentation for structure-count tests). */
 static _Thread_local uint64_t g_c256_blocks, g_c512_blocks, g_calls_f, g_calls_prf,
-                              g_calls_h, g_calls_t;
+                              g_calls_h, g_calls_t, g_keccak_perms;
 
 /* SHA-256 of a whole message: full blocks straight from the input, then the
  * padded tail (0x80, zeros, 64-bit big-endian bit length; FIPS 180-4 5.1.1). */
@@ -399,6 +399,7 @@ static void keccak_f1600(uint64_t A[25])
                 A[x + 5 * y] = B[x + 5 * y] ^ (~B[(x + 1) % 5 + 5 * y] & B[(x + 2) % 5 + 5 * y]);
         A[0] ^= g_keccak_rc[ir];   /* iota */
     }
+    g_keccak_perms++;
 }
 
 /* SHAKE256(M, 8 outlen): rate 136 bytes, domain bits 1111 then pad10*1. */
@@ -1256,10 +1257,12 @@ SPX_EXPORT int oracle_slh_verify(int pid, const uint8_t *pk, const uint8_t *ctx,
     return rc;
 }
 
-/* Counters: [0] SHA-256 blocks, [1] SHA-512 blocks, [2] F, [3] PRF, [4] H, [5] T. */
+/* Counters: [0] SHA-256 blocks, [1] SHA-512 blocks, [2] F, [3] PRF, [4] H, [5] T,
+ * [6] Keccak-f[1600] permutations. */
 SPX_EXPORT void oracle_counters(uint64_t *out, int reset)
 {
     out[0] = g_c256_blocks; out[1] = g_c512_blocks; out[2] = g_calls_f;
-    out[3] = g_calls_prf; out[4] = g_calls_h; out[5] = g_calls_t;
-    if (reset) g_c256_blocks = g_c512_blocks = g_calls_f = g_calls_prf = g_calls_h = g_calls_t = 0;
+    out[3] = g_calls_prf; out[4] = g_calls_h; out[5] = g_calls_t; out[6] = g_keccak_perms;
+    if (reset)
+        g_c256_blocks = g_c512_blocks = g_calls_f = g_calls_prf = g_calls_h = g_calls_t = g_keccak_perms = 0;
 }
