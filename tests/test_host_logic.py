@@ -1,0 +1,106 @@
+"""Host-side logic that needs no GPU: the seeded workload generators (sizes,
+distributions, determinism), the binding's parameter tables against the C
+header and library, and the tuning cache (merging and applying per device)."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2512_23969_gb300 import autotune, hs, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_config_recipes_sizes_and_determinism():
+    c0 = inputs.config(0)
+    assert (c0.params, c0.count, c0.num_keys) == ("128f", 64, 1) and set(c0.lens.tolist()) == {32}
+    c1 = inputs.config(1)
+    assert (c1.params, c1.count, c1.num_keys) == ("128f", 16384, 16)
+    assert np.array_equal(c1.key_idx, np.arange(16384, dtype=np.uint32) % 16)
+    assert set(c1.lens.tolist()) == {32} and c1.msgs.size == 16384 * 32
+    assert len(set(c1.subset.tolist())) == 256 and c1.subset.max() < 16384
+    again = inputs.config(1)
+    assert np.array_equal(again.msgs, c1.msgs) and np.array_equal(again.seeds, c1.seeds)
+    for ps in ("192f", "256f"):
+        c2 = inputs.config(2, ps)
+        assert (c2.params, c2.count, c2.num_keys) == (ps, 8192, 16)
+        assert c2.lens.min() >= 32 and c2.lens.max() <= 1024 and c2.seeds.shape[1] == 3 * inputs.N_BYTES[ps]
+    assert not np.array_equal(inputs.config(2, "192f").msgs[:64], inputs.config(2, "256f").msgs[:64])
+
+
+def test_log_uniform_lengths():
+    rng = np.random.default_rng(1)
+    L = inputs.log_uniform_lengths(rng, 200000, 16, 65536)
+    assert L.min() >= 16 and L.max() <= 65536
+    # log-uniform: the median sits near the geometric mean of the range
+    assert 0.8 < np.median(L) / np.sqrt(16 * 65537) < 1.25
+    # a quarter of the mass per quarter of the log range
+    q = np.log(L.astype(np.float64) / 16) / np.log(65537 / 16)
+    hist = np.histogram(q, bins=4, range=(0, 1))[0] / L.size
+    assert np.all(np.abs(hist - 0.25) < 0.02)
+
+
+def test_mixed_recipe():
+    wls = inputs.mixed()
+    assert [wl.params for wl in wls] == ["128f", "192f", "256f"]
+    assert sum(wl.count for wl in wls) == 32768
+    frac = np.array([wl.count for wl in wls]) / 32768
+    assert np.all(np.abs(frac - np.array([0.5, 0.3, 0.2])) < 0.02)
+    assert [wl.num_keys for wl in wls] == [32, 19, 13]
+    allidx = np.sort(np.concatenate([wl.subset for wl in wls]))
+    assert np.array_equal(allidx, np.arange(32768))             # every draw lands in exactly one set
+    for wl in wls:
+        assert wl.lens.min() >= 16 and wl.lens.max() <= 65536
+        assert wl.key_idx.max() < wl.num_keys
+
+
+def test_serving_trace():
+    tr = inputs.serving_trace(rate=20000, seconds=2.0, pool=4096, seed=11)
+    n = len(tr["params"])
+    assert abs(n - 40000) < 4 * np.sqrt(40000)                   # Poisson count
+    a = tr["arrival_ns"]
+    assert np.all(np.diff(a.astype(np.int64)) >= 0) and a[-1] < 2.5e9
+    frac = np.bincount(tr["params"], minlength=3) / n
+    assert np.all(np.abs(frac - np.array([0.6, 0.25, 0.15])) < 0.02)
+    for si, ps in enumerate(("128f", "192f", "256f")):
+        sel = tr["params"] == si
+        assert tr["keys"][sel].max() < (614, 256, 154)[si]
+        assert tr["seeds"][ps].shape == ((614, 256, 154)[si], 3 * inputs.N_BYTES[ps])
+    assert tr["pool_lens"].min() >= 16 and tr["pool_lens"].max() <= 4096
+    assert tr["pool_msgs"].size == int(tr["pool_lens"].sum()) and tr["pool_idx"].max() < 4096
+
+
+def test_binding_tables_match_header_and_library():
+    text = open(os.path.join(ROOT, "include", "hs.h")).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"HS_([0-9A-Z_]+) = (\d+)", text) if not k.startswith("E"))
+    assert int(re.search(r"#define HS_NUM_PARAMS (\d+)", text).group(1)) == hs.NUM_PARAMS == len(hs.PARAMS)
+    for name, pid in hs.PARAMS.items():
+        assert enum[name.upper().replace("-", "_")] == pid, name
+        assert hs.sig_bytes(name) == hs.SIG_BY_ID[pid]
+        if name != "toy":
+            assert int(hs.load().hs_sk_bytes(pid)) == 4 * hs.N_BYTES[name]
+
+
+def test_tuning_cache_merges_and_applies(tmp_path, monkeypatch):
+    monkeypatch.setattr(autotune, "device_key", lambda: "TEST-DEVICE|sm103|152SM")
+    path = str(tmp_path / "tuned.json")
+    autotune.save({"128f": {"fors_lanes": {"best": 4}}}, path)
+    autotune.save({"192f": {"tree_min_blocks": {"best": 4}}}, path)       # another set: kept side by side
+    autotune.save({"128f": {"tree_split_below": {"best": 1024}}}, path)   # same set: replaced
+    data = json.load(open(path))["TEST-DEVICE|sm103|152SM"]
+    assert set(data) == {"128f", "192f"} and data["128f"] == {"tree_split_below": {"best": 1024}}
+    before = {(ps, k): autotune.get(ps, k) for ps in ("128f", "192f") for k in autotune.KNOBS}
+    try:
+        autotune.save({"128f": {"fors_lanes": {"best": 8}, "tree_split_below": {"best": 512}},
+                       "192f": {"fors_lanes": {"best": 3}}}, path)          # 3 lanes: not compiled, skipped
+        applied = autotune.apply(path)
+        assert "128f" in applied
+        assert autotune.get("128f", "fors_lanes") == 8 and autotune.get("128f", "tree_split_below") == 512
+        assert autotune.get("192f", "fors_lanes") == before[("192f", "fors_lanes")]
+        with pytest.raises(hs.HSError):
+            autotune.set("128f", "fors_lanes", 3)
+    finally:
+        for (ps, k), v in before.items():
+            autotune.set(ps, k, v)
