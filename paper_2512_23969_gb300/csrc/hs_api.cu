@@ -64,7 +64,7 @@ static bool set_info(int p, SetInfo* s) {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool set_shape(int pset, SetShape* out) {
-    SetInfo s;
+    SetInfo s{};
     if (!set_info(pset, &s)) return false;
     out->n = s.n;
     out->d = s.d;
@@ -80,7 +80,7 @@ void plan_dedup(Batch& b) {
     b.dedup_layer = 0;
     b.cap_log2 = 0;
     b.max_uniq = 0;
-    SetInfo s;
+    SetInfo s{};
     if (!g_share || !set_info(b.pset, &s) || b.num_keys > (1u << 20) || b.count == 0) return;
     // Share layers from the top down while the number of distinct trees a
     // layer can hold (keys x 2^bits of its tree index, at most one per
@@ -138,7 +138,7 @@ static void scratch_layout(const Batch& b, const SetInfo& s, size_t sz[kRegions]
 }
 
 size_t scratch_bytes(const Batch& b) {
-    SetInfo s;
+    SetInfo s{};
     if (!set_info(b.pset, &s)) return 0;
     size_t sz[kRegions], t = 0;
     int n;
@@ -160,7 +160,7 @@ size_t scratch_bytes(int pset, uint32_t num_keys, uint32_t count, uint32_t ck, b
 }
 
 void carve_scratch(Batch& b, void* base) {
-    SetInfo s;
+    SetInfo s{};
     set_info(b.pset, &s);
     size_t sz[kRegions];
     int n;
@@ -231,12 +231,12 @@ static hs_status dev_state(DevState** out) {
 }
 
 uint32_t* device_status_word() {
-    DevState* d;
+    DevState* d = nullptr;
     return dev_state(&d) == HS_OK ? d->status : nullptr;
 }
 
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
-    DevState* d;
+    DevState* d = nullptr;
     if (dev_state(&d) != HS_OK) return cudaErrorUnknown;
     return cudaMallocFromPoolAsync(p, bytes, d->pool, s);
 }
@@ -346,7 +346,7 @@ HS_API int hs_profile_read(float* ms, const char** names, int max) {
 }
 
 HS_API hs_status hs_check_status(void* stream, uint32_t* flags) {
-    DevState* d;
+    DevState* d = nullptr;
     hs_status st = dev_state(&d);
     if (st != HS_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -364,11 +364,11 @@ HS_API hs_status hs_check_status(void* stream, uint32_t* flags) {
 
 HS_API hs_status hs_keygen(hs_params p, const uint8_t* seeds, uint32_t count, uint8_t* pk, uint8_t* sk,
                            void* stream) {
-    SetInfo si;
+    SetInfo si{};
     if (!set_info(p, &si)) return fail(HS_EINVAL, "invalid parameter set %d", (int)p);
     if (count == 0) return HS_OK;
     if (!seeds || !pk || !sk) return fail(HS_EINVAL, "NULL buffer");
-    DevState* d;
+    DevState* d = nullptr;
     hs_status st = dev_state(&d);
     if (st != HS_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -417,7 +417,7 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
                            uint32_t num_keys, const uint32_t* key_idx, const uint8_t* msgs, const uint64_t* lens,
                            const uint8_t* sigs_in, uint8_t* sigs_out, uint32_t count, uint8_t* ok, void* stream,
                            bool fips = false, const uint8_t* prefix = nullptr, uint32_t plen = 0) {
-    SetInfo si;
+    SetInfo si{};
     if (!set_info(p, &si)) return fail(HS_EINVAL, "invalid parameter set %d", (int)p);
     if (count == 0) return HS_OK;
     if (!keys_in || !lens || (!verify && !sigs_out) || (verify && (!sigs_in || !ok)))
@@ -425,7 +425,7 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
     if (num_keys == 0) return fail(HS_EINVAL, "num_keys must be > 0");
     if (verify && (uint64_t)count * si.len >= (1ull << 28))
         return fail(HS_EINVAL, "verify: at most %llu signatures per call", (unsigned long long)((1ull << 28) / si.len - 1));
-    DevState* d;
+    DevState* d = nullptr;
     hs_status st = dev_state(&d);
     if (st != HS_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -618,7 +618,7 @@ static void keyset_free(hs_keyset* ks) {
 
 HS_API hs_status hs_keyset_create(hs_params p, const uint8_t* sk, uint32_t num_keys, uint32_t cache_layers,
                                   void* stream, hs_keyset** out) {
-    SetInfo si;
+    SetInfo si{};
     if (!set_info(p, &si)) return fail(HS_EINVAL, "invalid parameter set %d", (int)p);
     if (!sk || !out || num_keys == 0) return fail(HS_EINVAL, "hs_keyset_create: NULL buffer or no keys");
     if (cache_layers > (uint32_t)si.d - 1)
@@ -629,7 +629,7 @@ HS_API hs_status hs_keyset_create(hs_params p, const uint8_t* sk, uint32_t num_k
     for (uint32_t u = 0; u < cache_layers; u++) tpk += 1ull << (u * si.hp);
     const uint64_t trees = tpk * num_keys;
     if (trees >= (1ull << 32)) return fail(HS_EINVAL, "hs_keyset_create: more than 2^32 cached trees");
-    DevState* d;
+    DevState* d = nullptr;
     hs_status st = dev_state(&d);
     if (st != HS_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(128, MINB) tree_kernel(const KeyBlock* __restr
                                                    uint8_t* __restrict__ sigs, uint32_t* __restrict__ roots,
                                                    uint32_t* __restrict__ chk, uint32_t ck, uint32_t layers,
                                                    uint32_t one) {
-    constexpr int NW = P::NW, HP = P::HP, LV = P::LEAVES;
+    constexpr int NW = P::NW, LV = P::LEAVES;
     const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t per_msg = layers * LV;           // layers 0 .. layers-1 of every message
