@@ -323,6 +323,18 @@ hs_status hs_server_inject_launch_failures(hs_server *s, uint32_t n);
 hs_status hs_set_tree_sharing(int on);
 
 /*
+ * hs_set_host_direct -- process-wide switch (default on) for signing calls
+ * whose signature buffer is page-locked host memory mapped into the device
+ * address space (cudaHostAlloc / cudaMallocHost; every such buffer is mapped
+ * under unified addressing): the kernels then write the signatures into it
+ * directly (on GB300 over the coherent NVLink-C2C link) instead of into a
+ * device staging buffer followed by a device-to-host copy.  The call still
+ * returns after the signatures are complete.  Off: always stage and copy.
+ * Other host memory is always staged.
+ */
+hs_status hs_set_host_direct(int on);
+
+/*
  * FIPS 205 (SLH-DSA) mode -- a variant; the paper signs with SPHINCS+
  * round 3.1.  At every set here (SHA2 and SHAKE) FIPS 205 keeps the keys,
  * tweakable hashes, addresses and sizes and changes two things: the FORS

@@ -244,6 +244,21 @@ cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
 uint32_t chain_checkpoint_stride() { return g_ck; }
 
 // 1 if p is host memory (pageable or pinned), 0 if device or managed.
+// Device-side address of page-locked, mapped host memory (nullptr if p is
+// not such memory).  The kernels can write signatures straight into it:
+// on Grace + GB300 the stores cross NVLink-C2C coherently, so no staging
+// buffer and no device-to-host copy is needed.
+static bool g_direct = true;
+static void* mapped_host_ptr(const void* p) {
+    if (!p || !g_direct) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 static int is_host_ptr(const void* p) {
     if (!p) return 0;
     cudaPointerAttributes a;
@@ -315,6 +330,11 @@ HS_API hs_status hs_tune_set(hs_params p, int knob, int32_t value) {
 }
 
 HS_API int32_t hs_tune_get(hs_params p, int knob) { return tune_get(p, knob); }
+
+HS_API hs_status hs_set_host_direct(int on) {
+    g_direct = on != 0;
+    return HS_OK;
+}
 
 HS_API hs_status hs_set_tree_sharing(int on) {
     g_share = on != 0;
@@ -435,7 +455,9 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
     const size_t sig_total = (size_t)count * si.sig;
     const int h_keys = is_host_ptr(keys_in), h_idx = is_host_ptr(key_idx), h_lens = is_host_ptr(lens);
     const int h_msgs = is_host_ptr(msgs);
-    const int h_sig = verify ? is_host_ptr(sigs_in) : is_host_ptr(sigs_out);
+    // signatures into mapped host memory: written in place by the kernels
+    void* sig_direct = (!verify && is_host_ptr(sigs_out)) ? mapped_host_ptr(sigs_out) : nullptr;
+    const int h_sig = verify ? is_host_ptr(sigs_in) : (is_host_ptr(sigs_out) && !sig_direct);
     const int h_ok = verify ? is_host_ptr(ok) : 0;
     uint64_t msg_total = 0;
     if (h_msgs) {
@@ -505,7 +527,8 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
                        : const_cast<uint8_t*>(sigs_in);
         b.ok = h_ok ? reinterpret_cast<uint8_t*>(sg.take(count)) : ok;
     } else {
-        b.sigs = h_sig ? reinterpret_cast<uint8_t*>(sg.take(sig_total)) : sigs_out;
+        b.sigs = h_sig ? reinterpret_cast<uint8_t*>(sg.take(sig_total))
+                       : (sig_direct ? static_cast<uint8_t*>(sig_direct) : sigs_out);
     }
     b.fips = fips;
     b.prefix_len = plen;
@@ -551,7 +574,7 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
     }
     e = cudaFreeAsync(base, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
-    if (h_keys || h_idx || h_lens || h_msgs || h_sig || h_ok) {
+    if (h_keys || h_idx || h_lens || h_msgs || h_sig || h_ok || sig_direct) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     }

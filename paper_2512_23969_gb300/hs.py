@@ -88,6 +88,8 @@ def load():
         getattr(L, name).restype = C.c_int
     L.hs_set_tree_sharing.argtypes = [C.c_int]
     L.hs_set_tree_sharing.restype = C.c_int
+    L.hs_set_host_direct.argtypes = [C.c_int]
+    L.hs_set_host_direct.restype = C.c_int
     L.hs_set_chain_checkpoint.argtypes = [C.c_uint32]
     L.hs_set_chain_checkpoint.restype = C.c_int
     for name in ("hs_keygen", "hs_sign_batch", "hs_verify_batch", "hs_check_status"):
@@ -466,6 +468,11 @@ class Server:
 
 SIG_BY_ID = {0: 17088, 1: 35664, 2: 49856, 3: 1456, 4: 7856, 5: 16224, 6: 29792,
              7: 17088, 8: 35664, 9: 49856, 10: 7856, 11: 16224, 12: 29792}
+
+
+def hs_set_host_direct(on=True):
+    """Write signatures straight into mapped page-locked host buffers (default on)."""
+    _check(load().hs_set_host_direct(1 if on else 0))
 
 
 def hs_set_tree_sharing(on=True):

@@ -179,6 +179,33 @@ def test_host_buffers_equal_device_path(hs, O):
     assert ok.tolist() == [1] * 9
 
 
+@pytest.mark.parametrize("direct", [True, False])
+def test_pinned_host_signatures(hs, O, direct):
+    """Page-locked host buffers: signatures written straight into the mapped
+    host buffer (direct) or staged and copied back -- the same bytes as the
+    device path, and as the oracle on a sample; sets of every hash family
+    and tree width, ragged messages."""
+    import torch
+    hs.hs_set_host_direct(direct)
+    try:
+        for ps, count in (("128f", 300), ("192f", 40), ("256s", 3), ("shake-128f", 20)):
+            wl = inputs.make(ps, count, num_keys=3, lengths=("uniform", 0, 400), seed=4400 + count,
+                             key_mode="random")
+            pk, sk = hs.hs_keygen(ps, _dev(wl.seeds))
+            dev = _gpu_sign(hs, wl, sk)
+            pinned = torch.zeros(count * hs.sig_bytes(ps), dtype=torch.uint8).pin_memory()
+            out = hs.hs_sign_batch(ps, sk, torch.from_numpy(wl.msgs).pin_memory(),
+                                   torch.from_numpy(wl.lens).pin_memory(),
+                                   key_idx=torch.from_numpy(wl.key_idx).pin_memory(), sigs=pinned, num_keys=3)
+            assert out.numpy().tobytes() == dev.tobytes(), ps
+            i = count - 1
+            osk = O.keygen(ps, bytes(wl.seeds[int(wl.key_idx[i])]))[1]
+            assert pinned.numpy()[i * hs.sig_bytes(ps):(i + 1) * hs.sig_bytes(ps)].tobytes() == \
+                O.sign(ps, osk, wl.message(i))
+    finally:
+        hs.hs_set_host_direct(True)
+
+
 def test_key_index_out_of_range(hs, O):
     import torch
     wl = inputs.make("toy", 4, num_keys=2, lengths=16, seed=45)
