@@ -646,7 +646,11 @@ def run_own(args):
             traffic = json.load(open(prof_file)).get("bytes_per_launch_scaled")
         except (OSError, ValueError):
             traffic = None
+    tree_c = STAGE_WORK[ps]["tree"] if ps in STAGE_WORK else None
     roofline = {"bound": "alu", "kernel": "tree_kernel<%s> (TREE_Sign)" % ps,
+                "compressions_per_s": ({"sha256": round(tree_c[0] * count / (tree_ms / 1e3), 1),
+                                        "sha512": round(tree_c[1] * count / (tree_ms / 1e3), 1)}
+                                       if tree_c and tree_ms > 0 else None),
                 "achieved": round(achieved, 3) if achieved else None, "peak": round(alu_peak, 3),
                 "unit": "Tops/s", "frac": round(achieved / alu_peak, 4) if achieved else None, "traffic": traffic,
                 "peak_basis": "ALU pipe %.1f lane-ops/clk/SM (measured LOP3/SHF rate) x %d SMs x %.0f MHz"
@@ -684,9 +688,16 @@ def run_own(args):
     if rank == 0 and args.cpu_seconds > 0:
         sks = oracle_keys(ps, wl.seeds)
         r, n, cores = oracle_rate(ps, sks, wl, args.cpu_seconds)
+        # and on one host thread, over the first 16 messages
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        for i in range(16):
+            O.sign(ps, sks[int(wl.key_idx[i])], wl.message(i))
+        one = 16 / (time.perf_counter() - t0)
         cpu = {"value": round(r, 3), "unit": "signatures/s", "cores": cores, "kind": "oracle",
                "sample": "%d signatures of this workload (messages i mod 16384) in %.0f s on %d host threads"
-                         % (n, args.cpu_seconds, cores)}
+                         % (n, args.cpu_seconds, cores),
+               "single_thread": {"value": round(one, 3), "sample": "messages 0..15 on one host thread"}}
 
     ms_sorted = sorted(step_ms)
     line = {
