@@ -287,3 +287,23 @@ def test_mixed_full_size_graph(hs, O):
         _, osk = _oracle_keys(O, wl.params, wl.seeds)
         want = _oracle_sign_many(O, wl.params, osk, wl, sample)
         _compare(O, wl.params, sig.cpu().numpy(), want, sample)
+
+
+def test_out_of_memory_is_an_error_status(hs):
+    """A batch whose scratch cannot be allocated (terabytes of chain
+    checkpoints) returns HS_ENOMEM; nothing is launched and the library keeps
+    working."""
+    import torch
+    count = 4 << 20                                    # 4 Mi 256f messages, all empty
+    lens = torch.zeros(count, dtype=torch.uint64, device="cuda")
+    msgs = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    wl = inputs.make("256f", 2, num_keys=1, lengths=8, seed=9)
+    pk, sk = hs.hs_keygen("256f", _dev(wl.seeds))
+    sigs = torch.empty(16, dtype=torch.uint8, device="cuda")   # never written: the call fails first
+    with pytest.raises(hs.HSError) as e:
+        hs.hs_sign_batch("256f", sk, msgs, lens, sigs=sigs, num_keys=1)
+    assert e.value.code == 2                           # HS_ENOMEM
+    torch.cuda.synchronize()
+    ok = hs.hs_verify_batch("256f", pk, _dev(wl.msgs), _dev(wl.lens),
+                            hs.hs_sign_batch("256f", sk, _dev(wl.msgs), _dev(wl.lens), num_keys=1), num_keys=1)
+    assert ok.cpu().numpy().all()
