@@ -35,7 +35,11 @@ static hs_status fail(hs_status st, const char* fmt, ...) {
 
 void set_last_error(const char* msg) { g_err = msg; }
 
+// Reports a CUDA error and consumes it: a non-sticky error (an allocation
+// that failed, a bad launch configuration) must not surface again in the
+// next call's launch checks.
 static hs_status cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();
     return fail(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 

@@ -152,6 +152,7 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
     void* base = nullptr;
     cudaError_t e = pool_alloc(&base, total, s);
     if (e != cudaSuccess) {
+        cudaGetLastError();                  // consumed here: reported by the status below
         char buf[200];
         snprintf(buf, sizeof(buf), "hs_sign_mixed: scratch of %zu bytes: %s", total, cudaGetErrorString(e));
         return mx_fail(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA, buf);
