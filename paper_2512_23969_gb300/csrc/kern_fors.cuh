@@ -127,6 +127,21 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
     uint8_t* sf = sigs + (size_t)m * P::SIG_BYTES + P::N + (size_t)i * (A + 1) * P::N;
 
     const Pipes<POL> pp(one);
+    // Leaf hashes with a chain context: PRF and F of every leaf of this
+    // message share address words 0..4 (layer, tree, type, key pair, height
+    // 0 and the top half of the leaf index, which is 0 while k * 2^a <=
+    // 2^16), so rounds 0..4 of each are computed once here and a leaf hash
+    // runs rounds 5..63 -- the same compression as the chain steps of
+    // TREE_Sign, bit for bit.  The two contexts are read at a run-time
+    // index (local memory): 60 registers instead of 79 for a register
+    // select, and as fast or faster (FORS 128f 6.39 -> 6.19 ms, 256f 45.2
+    // -> 43.6 ms per 16384 / 8192 signatures).
+    constexpr bool kCtx = !P::SHAKE && ((uint64_t)K << A) <= 65536u;
+    ChainCtx cxs[kCtx ? 2 : 1];
+    if constexpr (kCtx) {
+        chain_ctx<POL>(ms256, make_adrs(0, tree, T_FORS_PRF, kp, 0, 0), cxs[0], pp);
+        chain_ctx<POL>(ms256, make_adrs(0, tree, T_FORS_TREE, kp, 0, 0), cxs[1], pp);
+    }
     SibStack<R, RI, NW, (R <= 7)> stk;                 // left siblings, levels 0..R-1
     uint32_t node[NW];
     const uint32_t base = L << R;                  // first leaf of this lane (within tree)
@@ -142,8 +157,12 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
             for (int w = 0; w < NW; w++) node[w] = skseed[w];
 #pragma unroll 1
             for (int s = 0; s < 2; s++) {
-                hashF_p<P, POL>(ms256, make_adrs(0, tree, s == 0 ? T_FORS_PRF : T_FORS_TREE, kp, 0, g), node,
-                                node, pp);
+                if constexpr (kCtx) {
+                    chain_step<POL, NW>(cxs[s], ms256, g, node, node, pp);
+                } else {
+                    hashF_p<P, POL>(ms256, make_adrs(0, tree, s == 0 ? T_FORS_PRF : T_FORS_TREE, kp, 0, g), node,
+                                    node, pp);
+                }
                 if (s == 0 && t == gs) store_be<NW>(sf, node);
             }
             if (t == (gs ^ 1u)) store_be<NW>(sf + P::N, node);
