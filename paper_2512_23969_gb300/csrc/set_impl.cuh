@@ -41,7 +41,7 @@ struct SetImpl {
         const uint64_t threads = (uint64_t)b.count * P::K * LPT;
         const uint32_t T = 256;
         const uint32_t G = (uint32_t)((threads + T - 1) / T);
-        fors_kernel<P, kChainPol, LPT><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.fors_roots, 1u);
+        fors_kernel<P, fors_pol<P>(), LPT><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.fors_roots, 1u);
         return cudaGetLastError();
     }
     static cudaError_t fors_pk(const Batch& b, cudaStream_t s) {
@@ -57,11 +57,11 @@ struct SetImpl {
         const uint32_t G = (uint32_t)((threads + T - 1) / T);
         if (threads == 0) return cudaSuccess;
         if constexpr (kWide) {
-            bleaf_kernel<P, kChainPol, MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.leafv, b.chk, b.ck, L, 1u);
+            bleaf_kernel<P, tree_pol<P>(), MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.leafv, b.chk, b.ck, L, 1u);
             cudaError_t e = cudaGetLastError();
             return e == cudaSuccess ? merge(b, s) : e;
         } else {
-            tree_kernel<P, kChainPol, MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck,
+            tree_kernel<P, tree_pol<P>(), MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck,
                                                              L, 1u);
             return cudaGetLastError();
         }
@@ -83,13 +83,13 @@ struct SetImpl {
         const uint64_t th = (uint64_t)max_uniq * P::LEAVES;
         if (th == 0) return cudaSuccess;
         if constexpr (kWide) {
-            wtree_leaf_kernel<P, kChainPol><<<(uint32_t)((th + T - 1) / T), T, 0, s>>>(keys, desc, nuniq, max_uniq,
+            wtree_leaf_kernel<P, tree_pol<P>()><<<(uint32_t)((th + T - 1) / T), T, 0, s>>>(keys, desc, nuniq, max_uniq,
                                                                                       nodes, chk, ck, 1u);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
             wtree_merge_kernel<P><<<max_uniq, kMergeThreads, 0, s>>>(keys, desc, nuniq, max_uniq, nodes);
         } else {
-            utree_kernel<P, kChainPol><<<(uint32_t)((th + T - 1) / T), T, 0, s>>>(keys, desc, nuniq, max_uniq, nodes,
+            utree_kernel<P, tree_pol<P>()><<<(uint32_t)((th + T - 1) / T), T, 0, s>>>(keys, desc, nuniq, max_uniq, nodes,
                                                                                   chk, ck, 1u);
         }
         return cudaGetLastError();
@@ -136,7 +136,7 @@ struct SetImpl {
         const uint32_t L = own_layers(b);
         const uint64_t chains = (uint64_t)b.count * L * P::LEAVES * P::LEN;
         if (chains == 0) return cudaSuccess;
-        chains_kernel<P, kChainPol><<<(uint32_t)((chains + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.ends,
+        chains_kernel<P, tree_pol<P>()><<<(uint32_t)((chains + T - 1) / T), T, 0, s>>>(b.keys, b.infos, b.count, b.ends,
                                                                                   b.chk, b.ck, L, 1u);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

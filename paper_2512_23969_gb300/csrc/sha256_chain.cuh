@@ -34,7 +34,11 @@ __device__ __forceinline__ uint32_t mad_addi(uint32_t a, uint32_t one) {
 }
 
 // Addition policy: bit 0 = T1 sums on IMAD, bit 1 = e update on IMAD,
-// bit 2 = a update on IMAD.  POL 7 is the measured best for chains.
+// bit 2 = a update on IMAD, bit 3 = message-schedule sums on IMAD.
+// Measured on GB300: POL 7 for the chains at n = 16 (POL 15: TREE_Sign
+// 88.4 -> 97.8 ms at 128f), POL 15 for the tree-building chains at n = 24 /
+// 32, whose kernels also run SHA-512 T_len and H (TREE_Sign 1.5-2.8 %
+// faster at 192f / 256f / 192s / 256s).
 template <int POL>
 struct Pipes {
     uint32_t one;
@@ -43,6 +47,15 @@ struct Pipes {
 
 // Policy used by the signing kernels (all round additions on IMAD).
 constexpr int kChainPol = 7;
+// Policy of the kernels that build XMSS trees (TREE_Sign, the split and
+// wide-tree leaf kernels, shared trees) for a parameter set.
+template <class P>
+constexpr int tree_pol() { return P::BIG ? 15 : kChainPol; }
+// Policy of FORS_Sign: 15 only where its leaves run full compressions
+// (no per-message chain context: k * 2^a > 2^16) at n = 24 / 32; with the
+// context POL 7 measured faster (256f FORS 43.7 vs 44.8 ms).
+template <class P>
+constexpr int fors_pol() { return (P::BIG && ((uint64_t)P::K << P::A) > 65536u) ? 15 : kChainPol; }
 
 namespace detail {
 constexpr uint32_t kK256[64] = {HS_K256_LIST};
@@ -77,7 +90,16 @@ template <int POL, bool PRE, int t0, int t1>
 struct Rounds256 {
     __device__ static __forceinline__ void run(uint32_t v[8], uint32_t W[16], const uint32_t* c, const Pipes<POL>& p) {
         constexpr int t = t0;
-        if constexpr (t >= 16) {
+        if constexpr (t >= 16 && (POL & 8)) {
+            const uint32_t a = mad_add(s1_256(W[(t - 2) & 15]), W[(t - 7) & 15], p.one);
+            if constexpr (PRE && t <= 19) {
+                W[t & 15] = mad_add(a, c[t - 16], p.one);
+            } else if constexpr (PRE && t == 20) {
+                W[t & 15] = mad_add(mad_add(a, s0_256(W[5]), p.one), c[4], p.one);
+            } else {
+                W[t & 15] = mad_add(mad_add(a, s0_256(W[(t - 15) & 15]), p.one), W[t & 15], p.one);
+            }
+        } else if constexpr (t >= 16) {
             if constexpr (PRE && t <= 19) {
                 W[t & 15] = s1_256(W[(t - 2) & 15]) + W[(t - 7) & 15] + c[t - 16];
             } else if constexpr (PRE && t == 20) {
