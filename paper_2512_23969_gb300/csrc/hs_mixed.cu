@@ -192,6 +192,10 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
         if (g) cudaGraphDestroy(g);
     } else {
         e = enqueue_jobs(*d, bs, s);
+        // A failed launch leaves that job's side streams unjoined: wait for
+        // them here so the scratch freed below is not reused under them.
+        if (e != cudaSuccess)
+            for (size_t i = 0; i < 2 * bs.size(); i++) cudaStreamSynchronize(d->side[i]);
     }
     }
     cudaError_t ef = cudaFreeAsync(base, s);
