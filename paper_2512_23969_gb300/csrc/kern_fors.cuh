@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
                 for (int w = 0; w < NW; w++) lr[NW + w] = node[w];
                 z++;
                 idx >>= 1;
-                hashH_ms<P>(ms256, ms512,
-                            make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node);
+                hashH_p<P, POL>(ms256, ms512,
+                                make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node, pp);
                 if (z < (uint32_t)A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
             }
             if (z < (uint32_t)RI) stk.store(z, node);
@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
                 for (int w = 0; w < NW; w++) lr[NW + w] = node[w];
                 z++;
                 idx >>= 1;
-                hashH_ms<P>(ms256, ms512,
-                            make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node);
+                hashH_p<P, POL>(ms256, ms512,
+                                make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node, pp);
                 if (z < (uint32_t)A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
             }
             if (z < (uint32_t)R) stk.store_outer(z, node);
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
 #pragma unroll
             for (int w = 0; w < NW; w++) { lr[w] = node[w]; lr[NW + w] = other[w]; }
             const uint32_t idx = L >> (z - R);
-            hashH_ms<P>(ms256, ms512, make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node);
+            hashH_p<P, POL>(ms256, ms512, make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node, pp);
             if (z < A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
         }
     }

@@ -191,4 +191,60 @@ __device__ __forceinline__ void hashF_p(const uint32_t ms256[8], const Adrs& a, 
     else hashF_fast<POL, P::NW>(ms256, a, x, out, pp);
 }
 
+// The same compression as sha256_compress_rolled (16 rounds unrolled in a
+// loop of 4, K from constant memory: a small code footprint for call sites
+// outside the chain loops) with the round additions on IMAD as in round256.
+template <int POL>
+__device__ __forceinline__ void compress256_rolled_p(uint32_t st[8], uint32_t W[16], const Pipes<POL>& p) {
+    uint32_t v[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = st[i];
+#pragma unroll 1
+    for (int t0 = 0; t0 < 64; t0 += 16) {
+        if (t0 > 0) {
+#pragma unroll
+            for (int i = 0; i < 16; i++)
+                W[i] += s1_256(W[(i + 14) & 15]) + W[(i + 9) & 15] + s0_256(W[(i + 1) & 15]);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            uint32_t& a = v[(8 - (j & 7)) & 7];
+            uint32_t& b = v[(9 - (j & 7)) & 7];
+            uint32_t& c = v[(10 - (j & 7)) & 7];
+            uint32_t& d = v[(11 - (j & 7)) & 7];
+            uint32_t& e = v[(12 - (j & 7)) & 7];
+            uint32_t& f = v[(13 - (j & 7)) & 7];
+            uint32_t& g = v[(14 - (j & 7)) & 7];
+            uint32_t& h = v[(15 - (j & 7)) & 7];
+            const uint32_t ch = (e & f) ^ (~e & g);
+            const uint32_t mj = (a & b) | (c & (a | b));
+            const uint32_t t1 =
+                mad_add(mad_add(mad_add(mad_add(h, c_K256[t0 + j], p.one), W[j], p.one), S1_256(e), p.one), ch, p.one);
+            d = mad_add(d, t1, p.one);
+            h = mad_add(mad_add(t1, S0_256(a), p.one), mj, p.one);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) st[i] += v[i];
+}
+
+// H of a parameter set through the rolled IMAD-addition compression where
+// it is one SHA-256 block (n = 16); SHA-512 (n > 16) and SHAKE as hashH_ms.
+template <class P, int POL>
+__device__ __forceinline__ void hashH_p(const uint32_t* ms256, const uint32_t* ms512, const Adrs& a,
+                                        const uint32_t* lr, uint32_t* out, const Pipes<POL>& pp) {
+    if constexpr (P::SHAKE || P::BIG) {
+        hashH_ms<P>(ms256, ms512, a, lr, out);
+    } else {
+        uint32_t W[16], st[8];
+        fill_block<16, 2 * P::NW>(W, a, lr);
+        W[15] = (64 + 22 + 8 * P::NW) * 8;
+#pragma unroll
+        for (int i = 0; i < 8; i++) st[i] = ms256[i];
+        compress256_rolled_p<POL>(st, W, pp);
+#pragma unroll
+        for (int i = 0; i < P::NW; i++) out[i] = st[i];
+    }
+}
+
 }  // namespace hs
