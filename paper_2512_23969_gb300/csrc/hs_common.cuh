@@ -148,37 +148,47 @@ struct TStream {
     }
 };
 
-// T_l over PW payload words already in memory (chain ends, FORS roots):
-// Trunc_n(SHA-x(midstate; ADRSc || payload)), each compression block
-// assembled straight from memory -- word positions inside a block are
-// compile-time constants, the block index is a loop counter -- so nothing
-// is buffered in registers with run-time indices (which would live in
-// local memory).  Same value as the streaming form above.
-template <bool BIG, int PW, int NW>
-__device__ __forceinline__ void tl_from_mem(const uint32_t* ms, const Adrs& a, const uint32_t* p, uint32_t* out) {
+// Block b of a T_l call over PW payload words in memory (chain ends, FORS
+// roots): ADRSc || payload || pad || bit length after the midstate.  Word
+// positions inside a block are compile-time constants and b is a loop
+// counter, so nothing is buffered in registers with run-time indices (which
+// would live in local memory).
+template <bool BIG, int PW>
+__device__ __forceinline__ void tl_block(const Adrs& a, const uint32_t* p, int b, uint32_t* W) {
     constexpr int BW = BIG ? 32 : 16;            // words per block
     constexpr int LW = BIG ? 4 : 2;              // length words
     constexpr int TW = 5 + PW + 1;               // ADRSc words, payload at a 2-byte offset, pad word
     constexpr int NB = (TW + LW + BW - 1) / BW;
     constexpr uint32_t BITS = ((BIG ? 128u : 64u) + 22u + 4u * PW) * 8u;
+#pragma unroll
+    for (int k = 0; k < BW; k++) {
+        const int j = b * BW + k;
+        uint32_t v;
+        if (j < 5) v = j == 0 ? a.w0 : j == 1 ? a.w1 : j == 2 ? a.w2 : j == 3 ? a.w3 : a.w4;
+        else if (j == 5) v = mid16(a.half, p[0]);
+        else if (j < 5 + PW) v = mid16(p[j - 6], p[j - 5]);
+        else if (j == 5 + PW) v = (p[PW - 1] << 16) | 0x8000u;
+        else v = 0u;
+        if (b == NB - 1 && k == BW - 1) v = BITS;
+        W[k] = v;
+    }
+}
+template <bool BIG, int PW>
+__host__ __device__ constexpr int tl_blocks() {
+    return (5 + PW + 1 + (BIG ? 4 : 2) + (BIG ? 32 : 16) - 1) / (BIG ? 32 : 16);
+}
+
+// T_l over PW payload words in memory: Trunc_n(SHA-x(midstate; ADRSc ||
+// payload)), block by block as above.  Same value as the streaming form.
+template <bool BIG, int PW, int NW>
+__device__ __forceinline__ void tl_from_mem(const uint32_t* ms, const Adrs& a, const uint32_t* p, uint32_t* out) {
     uint32_t st[BIG ? 16 : 8];
 #pragma unroll
     for (int i = 0; i < (BIG ? 16 : 8); i++) st[i] = ms[i];
 #pragma unroll 1
-    for (int b = 0; b < NB; b++) {
-        uint32_t W[BW];
-#pragma unroll
-        for (int k = 0; k < BW; k++) {
-            const int j = b * BW + k;
-            uint32_t v;
-            if (j < 5) v = j == 0 ? a.w0 : j == 1 ? a.w1 : j == 2 ? a.w2 : j == 3 ? a.w3 : a.w4;
-            else if (j == 5) v = mid16(a.half, p[0]);
-            else if (j < 5 + PW) v = mid16(p[j - 6], p[j - 5]);
-            else if (j == 5 + PW) v = (p[PW - 1] << 16) | 0x8000u;
-            else v = 0u;
-            if (b == NB - 1 && k == BW - 1) v = BITS;
-            W[k] = v;
-        }
+    for (int b = 0; b < tl_blocks<BIG, PW>(); b++) {
+        uint32_t W[BIG ? 32 : 16];
+        tl_block<BIG, PW>(a, p, b, W);
         if constexpr (BIG) {
             uint64_t s64[8];
 #pragma unroll

@@ -81,7 +81,7 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
         }
     }
     if constexpr (P::SHAKE) ts.template finish<NW>(P::LEN * P::N, out);
-    else tl_from_mem<P::BIG, P::LEN * NW, NW>(msT, make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0), ends, out);
+    else tl_from_mem_p<P::BIG, P::LEN * NW, NW, POL>(msT, make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0), ends, out, pp);
 }
 
 // Merkle levels of one XMSS tree held by an aligned lane group (one leaf

@@ -228,6 +228,28 @@ __device__ __forceinline__ void compress256_rolled_p(uint32_t st[8], uint32_t W[
     for (int i = 0; i < 8; i++) st[i] += v[i];
 }
 
+// T_l over PW payload words in memory through the rolled IMAD-addition
+// compression (SHA-256); the SHA-512 form is tl_from_mem's.
+template <bool BIG, int PW, int NW, int POL>
+__device__ __forceinline__ void tl_from_mem_p(const uint32_t* ms, const Adrs& a, const uint32_t* p, uint32_t* out,
+                                              const Pipes<POL>& pp) {
+    if constexpr (BIG) {
+        tl_from_mem<BIG, PW, NW>(ms, a, p, out);
+    } else {
+        uint32_t st[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) st[i] = ms[i];
+#pragma unroll 1
+        for (int b = 0; b < tl_blocks<false, PW>(); b++) {
+            uint32_t W[16];
+            tl_block<false, PW>(a, p, b, W);
+            compress256_rolled_p<POL>(st, W, pp);
+        }
+#pragma unroll
+        for (int i = 0; i < NW; i++) out[i] = st[i];
+    }
+}
+
 // H of a parameter set through the rolled IMAD-addition compression where
 // it is one SHA-256 block (n = 16); SHA-512 (n > 16) and SHAKE as hashH_ms.
 template <class P, int POL>
