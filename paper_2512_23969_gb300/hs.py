@@ -120,6 +120,41 @@ def _ptr(x):
     return x.data_ptr() if x.numel() else None
 
 
+def _numel(x):
+    return int(x.size) if isinstance(x, np.ndarray) else int(x.numel())
+
+
+def _buf(x, name, itemsize, min_elems=0):
+    """Check a buffer before its address goes to the C ABI: the element size
+    the library reads (1 for bytes, 4 for key indices, 8 for lengths) and at
+    least min_elems elements, so that a wrong dtype or a short buffer raises
+    here instead of being read past its end.  None passes (NULL)."""
+    if x is None:
+        return None
+    isz = int(x.itemsize) if isinstance(x, np.ndarray) else int(x.element_size())
+    if isz != itemsize:
+        raise ValueError("%s: elements of %d bytes expected, got %d" % (name, itemsize, isz))
+    if _numel(x) < min_elems:
+        raise ValueError("%s: at least %d elements needed, got %d" % (name, min_elems, _numel(x)))
+    return x
+
+
+def _msgs_lens(msgs, lens, key_idx=None):
+    """Checks shared by the signing and verification calls: lens (8-byte
+    lengths, one per message), key_idx (4-byte, one per message), msgs
+    (bytes; covering the lengths when they are on the host)."""
+    count = int(lens.shape[0])
+    _buf(lens, "lens", 8)
+    _buf(key_idx, "key_idx", 4, count)
+    if msgs is not None:
+        _buf(msgs, "msgs", 1)
+        if isinstance(lens, np.ndarray) and count:
+            need = int(lens.astype(np.uint64).sum())
+            if _numel(msgs) < need:
+                raise ValueError("msgs: the lengths add up to %d bytes, the buffer has %d" % (need, _numel(msgs)))
+    return count
+
+
 def _stream(stream):
     if stream is not None:
         return stream if isinstance(stream, int) else stream.cuda_stream
@@ -151,20 +186,22 @@ def hs_keygen(params, seeds, pk=None, sk=None, stream=None):
     """(pk, sk) for each 3n-byte seed row of ``seeds`` (uint8 [count, 3n])."""
     n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     count = seeds.shape[0] if seeds.ndim == 2 else seeds.shape[0] // (3 * n)
-    pk = _like(seeds, count * 2 * n, np.uint8, "uint8") if pk is None else pk
-    sk = _like(seeds, count * 4 * n, np.uint8, "uint8") if sk is None else sk
+    _buf(seeds, "seeds", 1, count * 3 * n)
+    pk = _like(seeds, count * 2 * n, np.uint8, "uint8") if pk is None else _buf(pk, "pk", 1, count * 2 * n)
+    sk = _like(seeds, count * 4 * n, np.uint8, "uint8") if sk is None else _buf(sk, "sk", 1, count * 4 * n)
     _check(load().hs_keygen(_pid(params), _ptr(seeds), count, _ptr(pk), _ptr(sk), _stream(stream)))
     return pk.reshape(count, 2 * n), sk.reshape(count, 4 * n)
 
 
 def hs_sign_batch(params, sk, msgs, lens, key_idx=None, sigs=None, num_keys=None, stream=None):
     """Signatures (uint8 [count, SIG]) of the packed messages ``msgs`` with lengths ``lens``."""
-    count = int(lens.shape[0])
+    count = _msgs_lens(msgs, lens, key_idx)
     n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     if num_keys is None:
         num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
+    _buf(sk, "sk", 1, int(num_keys) * 4 * n)
     S = sig_bytes(params)
-    sigs = _like(lens, count * S, np.uint8, "uint8") if sigs is None else sigs
+    sigs = _like(lens, count * S, np.uint8, "uint8") if sigs is None else _buf(sigs, "sigs", 1, count * S)
     msgs = _nonempty(msgs, lens)
     _check(load().hs_sign_batch(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), _ptr(msgs), _ptr(lens),
                                 count, _ptr(sigs), _stream(stream)))
@@ -185,12 +222,13 @@ def _ctx(ctx):
 def hs_slh_sign_batch(params, sk, msgs, lens, ctx=b"", key_idx=None, sigs=None, num_keys=None, stream=None):
     """FIPS 205 SLH-DSA signatures (deterministic) of every message under one
     context string; ctx=None signs the messages as given (internal function)."""
-    count = int(lens.shape[0])
+    count = _msgs_lens(msgs, lens, key_idx)
     n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     if num_keys is None:
         num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
+    _buf(sk, "sk", 1, int(num_keys) * 4 * n)
     S = sig_bytes(params)
-    sigs = _like(lens, count * S, np.uint8, "uint8") if sigs is None else sigs
+    sigs = _like(lens, count * S, np.uint8, "uint8") if sigs is None else _buf(sigs, "sigs", 1, count * S)
     msgs = _nonempty(msgs, lens)
     cbuf, clen = _ctx(ctx)
     _check(load().hs_slh_sign_batch(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), cbuf, clen, _ptr(msgs),
@@ -200,11 +238,13 @@ def hs_slh_sign_batch(params, sk, msgs, lens, ctx=b"", key_idx=None, sigs=None, 
 
 def hs_slh_verify_batch(params, pk, msgs, lens, sigs, ctx=b"", key_idx=None, ok=None, num_keys=None, stream=None):
     """1/0 per FIPS 205 signature under one context string."""
-    count = int(lens.shape[0])
+    count = _msgs_lens(msgs, lens, key_idx)
     n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     if num_keys is None:
         num_keys = (pk.shape[0] if pk.ndim == 2 else pk.shape[0] // (2 * n))
-    ok = _like(lens, count, np.uint8, "uint8") if ok is None else ok
+    _buf(pk, "pk", 1, int(num_keys) * 2 * n)
+    _buf(sigs, "sigs", 1, count * sig_bytes(params))
+    ok = _like(lens, count, np.uint8, "uint8") if ok is None else _buf(ok, "ok", 1, count)
     msgs = _nonempty(msgs, lens)
     cbuf, clen = _ctx(ctx)
     _check(load().hs_slh_verify_batch(_pid(params), _ptr(pk), int(num_keys), _ptr(key_idx), cbuf, clen, _ptr(msgs),
@@ -222,6 +262,7 @@ class KeySet:
         n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
         self.params = params
         self.num_keys = int(sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
+        _buf(sk, "sk", 1, self.num_keys * 4 * n)
         h = C.c_void_p()
         _check(L.hs_keyset_create(_pid(params), _ptr(sk), self.num_keys, int(cache_layers), _stream(stream),
                                   C.byref(h)))
@@ -233,9 +274,9 @@ class KeySet:
         return int(load().hs_keyset_bytes(self._h))
 
     def sign(self, msgs, lens, key_idx=None, sigs=None, stream=None):
-        count = int(lens.shape[0])
+        count = _msgs_lens(msgs, lens, key_idx)
         S = sig_bytes(self.params)
-        sigs = _like(lens, count * S, np.uint8, "uint8") if sigs is None else sigs
+        sigs = _like(lens, count * S, np.uint8, "uint8") if sigs is None else _buf(sigs, "sigs", 1, count * S)
         msgs = _nonempty(msgs, lens)
         _check(load().hs_sign_keyset(self._h, _ptr(key_idx), _ptr(msgs), _ptr(lens), count, _ptr(sigs),
                                      _stream(stream)))
@@ -261,11 +302,13 @@ class KeySet:
 
 def hs_verify_batch(params, pk, msgs, lens, sigs, key_idx=None, ok=None, num_keys=None, stream=None):
     """1/0 per signature (uint8 [count])."""
-    count = int(lens.shape[0])
+    count = _msgs_lens(msgs, lens, key_idx)
     n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     if num_keys is None:
         num_keys = (pk.shape[0] if pk.ndim == 2 else pk.shape[0] // (2 * n))
-    ok = _like(lens, count, np.uint8, "uint8") if ok is None else ok
+    _buf(pk, "pk", 1, int(num_keys) * 2 * n)
+    _buf(sigs, "sigs", 1, count * sig_bytes(params))
+    ok = _like(lens, count, np.uint8, "uint8") if ok is None else _buf(ok, "ok", 1, count)
     msgs = _nonempty(msgs, lens)
     _check(load().hs_verify_batch(_pid(params), _ptr(pk), int(num_keys), _ptr(key_idx), _ptr(msgs), _ptr(lens),
                                   _ptr(sigs), count, _ptr(ok), _stream(stream)))
@@ -306,10 +349,12 @@ def hs_sign_batch_noalloc(params, sk, msgs, lens, sigs, key_idx=None, num_keys=N
     """Like hs_sign_batch, for callers that cannot allocate device memory:
     all buffers (including the output ``sigs``) are caller-provided device
     tensors, and the library works in its fixed 8 MiB device buffer."""
-    count = int(lens.shape[0])
+    count = _msgs_lens(msgs, lens, key_idx)
     n = N_BYTES[params] if isinstance(params, str) else _N_BY_ID[params]
     if num_keys is None:
         num_keys = (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
+    _buf(sk, "sk", 1, int(num_keys) * 4 * n)
+    _buf(sigs, "sigs", 1, count * sig_bytes(params))
     _check(load().hs_sign_batch_noalloc(_pid(params), _ptr(sk), int(num_keys), _ptr(key_idx), _ptr(msgs),
                                         _ptr(lens), count, _ptr(sigs), _stream(stream)))
     return sigs
@@ -343,6 +388,9 @@ def hs_sign_mixed(jobs, use_graph=True, stream=None):
         n = N_BYTES[ps] if isinstance(ps, str) else _N_BY_ID[ps]
         sk = jb["sk"]
         nk = jb.get("num_keys") or (sk.shape[0] if sk.ndim == 2 else sk.shape[0] // (4 * n))
+        cnt = _msgs_lens(jb["msgs"], jb["lens"], jb.get("key_idx"))
+        _buf(sk, "sk", 1, int(nk) * 4 * n)
+        _buf(jb["sigs"], "sigs", 1, cnt * sig_bytes(ps))
         msgs = _nonempty(jb["msgs"], jb["lens"])
         arr[j] = SignJob(_pid(ps), _ptr(sk), int(nk), _ptr(jb.get("key_idx")), _ptr(msgs), _ptr(jb["lens"]),
                          int(jb["lens"].shape[0]), _ptr(jb["sigs"]))

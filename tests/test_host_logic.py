@@ -104,3 +104,38 @@ def test_tuning_cache_merges_and_applies(tmp_path, monkeypatch):
     finally:
         for (ps, k), v in before.items():
             autotune.set(ps, k, v)
+
+
+def test_binding_rejects_wrong_element_sizes_and_short_buffers():
+    """The binding checks element sizes and buffer lengths before an address
+    reaches the C ABI (a wrong dtype would otherwise be read past its end);
+    every case below raises before any CUDA call, so it runs on the CPU."""
+    import torch
+    S, n = hs.sig_bytes("128f"), 16
+    sk = np.zeros((2, 4 * n), np.uint8)
+    pk = np.zeros((2, 2 * n), np.uint8)
+    msgs = np.zeros(64, np.uint8)
+    lens = np.full(2, 32, np.uint64)
+    kidx = np.zeros(2, np.uint32)
+    cases = [
+        lambda: hs.hs_sign_batch("128f", sk, msgs, lens.astype(np.int32)),               # 4-byte lengths
+        lambda: hs.hs_sign_batch("128f", sk, msgs, lens, key_idx=kidx.astype(np.int64)),  # 8-byte key indices
+        lambda: hs.hs_sign_batch("128f", sk, msgs, lens, key_idx=kidx[:1]),               # one index short
+        lambda: hs.hs_sign_batch("128f", sk, msgs[:63], lens),                            # lengths add to 64
+        lambda: hs.hs_sign_batch("128f", sk, msgs, lens, sigs=np.zeros(2 * S - 1, np.uint8)),
+        lambda: hs.hs_sign_batch("128f", sk.reshape(-1)[:100], msgs, lens, num_keys=2),    # 2 keys need 128 B
+        lambda: hs.hs_sign_batch("128f", torch.zeros(2, 64, dtype=torch.int32), msgs, lens),
+        lambda: hs.hs_verify_batch("128f", pk.reshape(-1)[:63], msgs, lens, np.zeros(2 * S, np.uint8), num_keys=2),
+        lambda: hs.hs_verify_batch("128f", pk, msgs, lens, np.zeros(2 * S - 16, np.uint8)),
+        lambda: hs.hs_verify_batch("128f", pk, msgs, lens, np.zeros(2 * S, np.uint8), ok=np.zeros(1, np.uint8)),
+        lambda: hs.hs_keygen("128f", np.zeros((2, 3 * n), np.uint8), pk=np.zeros(63, np.uint8)),
+        lambda: hs.hs_keygen("128f", np.zeros((2, 3 * n), np.uint16)),
+        lambda: hs.hs_slh_sign_batch("128f", sk, msgs, torch.full((2,), 32, dtype=torch.int32)),
+        lambda: hs.hs_sign_batch_noalloc("128f", sk, msgs, lens, np.zeros(S, np.uint8)),
+        lambda: hs.hs_sign_mixed([{"params": "128f", "sk": sk, "msgs": msgs, "lens": lens,
+                                   "sigs": np.zeros(S, np.uint8)}]),
+    ]
+    for i, call in enumerate(cases):
+        with pytest.raises(ValueError):
+            call()
+            pytest.fail("case %d passed the checks" % i)
