@@ -48,7 +48,8 @@ def test_served_equals_alone(hs, O, budget_mb, inflight):
         m = trace["pool_msgs"][offs[q]:offs[q + 1]]
         alone = hs.hs_sign_batch(ps, keys[ps], _dev(m if m.size else np.zeros(1, np.uint8)),
                                  _dev(np.array([m.size], np.uint64)),
-                                 key_idx=_dev(np.array([trace["keys"][i]], np.uint32)), num_keys=6)
+                                 key_idx=_dev(np.array([trace["keys"][i]], np.uint32)),
+                                 num_keys=int(keys[ps].shape[0]))       # 6 / 4 / 3 keys per set
         assert alone.cpu().numpy().tobytes() == sigs[i], i
         if i % 50 == 0:   # and the oracle on a sample
             osk = O.keygen(ps, bytes(trace["seeds"][ps][int(trace["keys"][i])]))[1]
