@@ -436,6 +436,10 @@ class Server:
         msg = bytes(msg)
         if out is None:
             out = np.empty(sig_bytes(params), dtype=np.uint8)
+        else:                        # the server copies the signature into it from the host
+            if not isinstance(out, np.ndarray) and out.is_cuda:
+                raise ValueError("out: host memory expected (the server writes it on the host)")
+            _buf(out, "out", 1, sig_bytes(params))
         rid = C.c_uint64()
         buf = C.create_string_buffer(msg, len(msg)) if msg else None
         _check(load().hs_server_submit(self._h, _pid(params), int(key), buf, len(msg), _ptr(out), C.byref(rid)))
@@ -471,6 +475,15 @@ class Server:
         pool_lens = np.ascontiguousarray(pool_lens, dtype=np.uint64)
         arrival_ns = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
         n = int(params.shape[0])
+        for name, a in (("keys", keys), ("pool_idx", pool_idx), ("arrival_ns", arrival_ns)):
+            if a.shape[0] != n:
+                raise ValueError("%s: %d entries for %d requests" % (name, a.shape[0], n))
+        if pool_msgs is not None:
+            pool_msgs = np.ascontiguousarray(pool_msgs, dtype=np.uint8)
+        need = int(pool_lens.sum())
+        if need and (pool_msgs is None or pool_msgs.size < need):
+            raise ValueError("pool_msgs: the pool lengths add up to %d bytes, the buffer has %d"
+                             % (need, 0 if pool_msgs is None else pool_msgs.size))
         lat = np.zeros(n, dtype=np.uint64)
         sigs = offs = None
         if keep_signatures:

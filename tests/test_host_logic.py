@@ -139,3 +139,21 @@ def test_binding_rejects_wrong_element_sizes_and_short_buffers():
         with pytest.raises(ValueError):
             call()
             pytest.fail("case %d passed the checks" % i)
+
+
+def test_server_binding_checks_without_a_server():
+    """Replay's per-request arrays and message pool, and submit's output
+    buffer, are checked in the binding before the C ABI sees them (the
+    checks run before the server handle is used, so a bare object works)."""
+    srv = hs.Server.__new__(hs.Server)
+    srv._h = None
+    z8, z32, z64 = np.zeros(4, np.uint8), np.zeros(4, np.uint32), np.zeros(4, np.uint64)
+    lens = np.full(2, 10, np.uint64)
+    with pytest.raises(ValueError):
+        srv.replay(z8, z32[:3], z32, np.zeros(20, np.uint8), lens, z64)          # 3 keys for 4 requests
+    with pytest.raises(ValueError):
+        srv.replay(z8, z32, z32, np.zeros(20, np.uint8), lens, z64[:2])          # 2 arrival times
+    with pytest.raises(ValueError):
+        srv.replay(z8, z32, z32, np.zeros(19, np.uint8), lens, z64)              # pool lengths add to 20
+    with pytest.raises(ValueError):
+        srv.submit("128f", 0, b"m", out=np.zeros(hs.sig_bytes("128f") - 1, np.uint8))
