@@ -1,0 +1,38 @@
+"""bench.py's reference arm (the CPU oracle timed on the host cores) prints
+exactly one JSON line carrying the keys of the bench contract, and under a
+multi-rank launch only rank 0 prints; the GPU arm's line is checked on the
+GPU by the driver's own run."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ARGS = [sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+        "--ref-step-seconds", "1"]
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run(ARGS, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.strip()]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    need = {"impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+            "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"}
+    assert need <= set(d), need - set(d)
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["unit"] == "signatures/s" and d["steps"] == 1 and d["vs_baseline"] is None
+    assert d["config"]["workload"] and d["config"]["params"] == "128f"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run(ARGS, cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""
