@@ -66,6 +66,17 @@ MUTANTS = [
      "idx[i] = (uint32_t)(acc & (((uint64_t)1 << p->a) - 1)); acc >>= p->a;", False),
     ("FIPS prefix domain byte", "w[0] = 0;", "w[0] = 1;", False),
     ("FIPS context length byte dropped", "w[1] = (uint8_t)ctxlen;", "w[1] = 0;", False),
+    ("hmac ipad", "buf[i] = kpad[i] ^ 0x36;", "buf[i] = kpad[i] ^ 0x5c;", False),
+    ("mgf1 counter starts at 1", "uint32_t c = 0;\n    uint8_t buf[256], dig[64];",
+     "uint32_t c = 1;\n    uint8_t buf[256], dig[64];", False),
+    ("WOTS and FORS PRF address types swapped", "ADDR_WOTS_PRF = 5, ADDR_FORS_PRF = 6",
+     "ADDR_WOTS_PRF = 6, ADDR_FORS_PRF = 5", False),
+    ("FORS roots in reverse order", "fors_node(c, idx_tree, idx_leaf, (uint32_t)i, a, roots + (size_t)i * n);",
+     "fors_node(c, idx_tree, idx_leaf, (uint32_t)i, a, roots + (size_t)(c->p.k - 1 - i) * n);", False),
+    ("FORS auth path in reverse height order",
+     "fors_node(c, idx_tree, idx_leaf, (g >> z) ^ 1u, z, s + (size_t)(z + 1) * n);",
+     "fors_node(c, idx_tree, idx_leaf, (g >> z) ^ 1u, z, s + (size_t)(a - z) * n);", False),
+    ("checksum sums the digits", "csum += (uint32_t)(p->w - 1 - digits[i]);", "csum += (uint32_t)digits[i];", False),
     ("Keccak rho offset walk", "int nx = y, ny = (2 * x + 3 * y) % 5;", "int nx = y, ny = (3 * x + 2 * y) % 5;", False),
     ("Keccak pi source lane", "int sx = (x + 3 * y) % 5, sy = x;", "int sx = (3 * x + y) % 5, sy = x;", False),
     ("Keccak chi operand order", "B[x + 5 * y] ^ (~B[(x + 1) % 5 + 5 * y] & B[(x + 2) % 5 + 5 * y])",
