@@ -77,6 +77,12 @@ MUTANTS = [
      "fors_node(c, idx_tree, idx_leaf, (g >> z) ^ 1u, z, s + (size_t)(z + 1) * n);",
      "fors_node(c, idx_tree, idx_leaf, (g >> z) ^ 1u, z, s + (size_t)(a - z) * n);", False),
     ("checksum sums the digits", "csum += (uint32_t)(p->w - 1 - digits[i]);", "csum += (uint32_t)digits[i];", False),
+    ("WOTS secret without the chain index", "adrs_set_keypair(&A, kp);\n    adrs_set_chain(&A, (uint32_t)i);\n    adrs_set_hash(&A, 0);",
+     "adrs_set_keypair(&A, kp);\n    adrs_set_chain(&A, 0);\n    adrs_set_hash(&A, 0);", False),
+    ("WOTS chain address off by one", "adrs_set_keypair(A, kp);\n    adrs_set_chain(A, (uint32_t)i);",
+     "adrs_set_keypair(A, kp);\n    adrs_set_chain(A, (uint32_t)i + 1);", False),
+    ("XMSS node height off by one", "adrs_set_height(&A, (uint32_t)z);\n    adrs_set_index(&A, i);\n    hash_H(c, &A, l, r, out);",
+     "adrs_set_height(&A, (uint32_t)z - 1);\n    adrs_set_index(&A, i);\n    hash_H(c, &A, l, r, out);", False),
     ("Keccak rho offset walk", "int nx = y, ny = (2 * x + 3 * y) % 5;", "int nx = y, ny = (3 * x + 2 * y) % 5;", False),
     ("Keccak pi source lane", "int sx = (x + 3 * y) % 5, sy = x;", "int sx = (3 * x + y) % 5, sy = x;", False),
     ("Keccak chi operand order", "B[x + 5 * y] ^ (~B[(x + 1) % 5 + 5 * y] & B[(x + 2) % 5 + 5 * y])",
