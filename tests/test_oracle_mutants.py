@@ -83,6 +83,8 @@ MUTANTS = [
      "adrs_set_keypair(A, kp);\n    adrs_set_chain(A, (uint32_t)i + 1);", False),
     ("XMSS node height off by one", "adrs_set_height(&A, (uint32_t)z);\n    adrs_set_index(&A, i);\n    hash_H(c, &A, l, r, out);",
      "adrs_set_height(&A, (uint32_t)z - 1);\n    adrs_set_index(&A, i);\n    hash_H(c, &A, l, r, out);", False),
+    ("verify FORS climb children swapped", "if ((gz & 1) == 0) hash_H(c, &A, node, au, node);",
+     "if ((gz & 1) == 1) hash_H(c, &A, node, au, node);", False),
     ("Keccak rho offset walk", "int nx = y, ny = (2 * x + 3 * y) % 5;", "int nx = y, ny = (3 * x + 2 * y) % 5;", False),
     ("Keccak pi source lane", "int sx = (x + 3 * y) % 5, sy = x;", "int sx = (3 * x + y) % 5, sy = x;", False),
     ("Keccak chi operand order", "B[x + 5 * y] ^ (~B[(x + 1) % 5 + 5 * y] & B[(x + 2) % 5 + 5 * y])",
