@@ -117,6 +117,7 @@ HS_API hs_status hs_sign_batch_noalloc(hs_params p, const uint8_t* sk, uint32_t 
     if (e != cudaSuccess) {
         char buf[256];
         snprintf(buf, sizeof(buf), "hs_sign_batch_noalloc: launch failed: %s", cudaGetErrorString(e));
+        cudaGetLastError();            // consumed here: reported by the status below
         return na_fail(HS_ECUDA, buf);
     }
     return HS_OK;
