@@ -91,6 +91,49 @@ KECCAK_WORK = {"shake-128f": _keccak_work(16, 22, 3, 6, 33, 35), "shake-192f": _
                "shake-192s": _keccak_work(24, 7, 9, 14, 17, 51), "shake-256s": _keccak_work(32, 8, 8, 14, 22, 67)}
 
 
+# The same ALU work as the kernels execute it.  The basis above prices
+# every compression in full; the signing kernels skip part of it, bit for
+# bit the same result:
+#  * a WOTS+ chain step (and a FORS leaf PRF / F where k 2^a <= 2^16) takes
+#    its state after rounds 0..4 and sigma0 of message words 1..4 from a
+#    context computed once per chain (per hash type), and runs rounds 5..63;
+#  * its message words 6 + n/4 .. 14 are zero and word 15 is a constant, so
+#    their sigma0 / sigma1 terms fold away in the unrolled schedule.
+# So one such step costs 59 x 10 + 4 x (46 sigma1 + 34 + n/4 sigma0) ALU
+# ops, and a chain 2 contexts (5 x 10 + 4 x 4 each) plus 16 steps.  T_l, H
+# and T_k run the rolled compression in full (1024 / 2624 per block).
+SET_SHAPE = {  # n, d, h', a, k, len
+    "128f": (16, 22, 3, 6, 33, 35), "192f": (24, 22, 3, 8, 33, 51), "256f": (32, 17, 4, 9, 35, 67),
+    "128s": (16, 7, 9, 12, 14, 35), "192s": (24, 7, 9, 14, 17, 51), "256s": (32, 8, 8, 14, 22, 67)}
+
+
+def _step_alu(nw, ctx=True):
+    """ALU ops of one one-block F / PRF compression over nw payload words."""
+    s1 = 48 - 2
+    s0 = 48 - (9 - nw) - 1 - (4 if ctx else 0)
+    return (59 if ctx else 64) * 10 + 4 * (s1 + s0)
+
+
+def exec_alu_per_sig(ps, stage):
+    """ALU-pipe ops per signature of a stage as the kernels execute them
+    (the roofline's work basis); the SHAKE sets execute the full basis."""
+    if ps in KECCAK_WORK:
+        return alu_ops_per_sig(ps, stage)
+    n, d, hp, a, k, length = SET_SHAPE[ps]
+    nw, big = n // 4, n > 16
+    c_blk = ALU_C512 if big else ALU_C256
+    if stage == "tree":
+        chain = 2 * (5 * 10 + 4 * 4) + 16 * _step_alu(nw)
+        tl_blocks = -(-(22 + length * n + (17 if big else 9)) // (128 if big else 64))
+        leaves = d * (1 << hp)
+        return leaves * (length * chain + tl_blocks * c_blk) + d * ((1 << hp) - 1) * c_blk
+    if stage == "fors":
+        ctx = (k << a) <= 65536
+        tk_blocks = -(-(22 + k * n + (17 if big else 9)) // (128 if big else 64))
+        return k * (1 << a) * 2 * _step_alu(nw, ctx) + (k * ((1 << a) - 1) + tk_blocks) * c_blk
+    return alu_ops_per_sig(ps, stage)
+
+
 def ops_per_sig(ps, stage):
     if ps in KECCAK_WORK:          # Keccak is all ALU work: the two bases coincide
         return KECCAK_WORK[ps][stage] * ALU_KECCAK
@@ -302,8 +345,11 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
         res[ps] = {"workload": wl.name, "value": round(wl.count * len(ms) / (sum(ms) / 1e3), 1),
                    "unit": "signatures/s", "ms_per_step": round(sum(ms) / len(ms), 3),
                    "stage_ms": {a: round(b, 3) for a, b in prof.items()},
-                   "alu_frac": {st: round(alu_ops_per_sig(ps, st) * wl.count / (prof[st] / 1e3) / 1e12 / alu_peak, 4)
+                   "alu_frac": {st: round(exec_alu_per_sig(ps, st) * wl.count / (prof[st] / 1e3) / 1e12 / alu_peak, 4)
                                 for st in ("tree", "fors") if prof.get(st, 0) > 0},
+                   "alu_frac_full_compression": {
+                       st: round(alu_ops_per_sig(ps, st) * wl.count / (prof[st] / 1e3) / 1e12 / alu_peak, 4)
+                       for st in ("tree", "fors") if prof.get(st, 0) > 0},
                    "verified": int(ok.sum().item()) == wl.count}
     # the bench workload again with tree sharing on (same signatures, less work)
     log("128f with tree sharing")
@@ -406,17 +452,69 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
         ms = _time_steps(fn, stream, flush, max(steps, 5), warmup)
         sout[name] = {"value": round(stotal * len(ms) / (sum(ms) / 1e3), 1), "unit": "signatures/s",
                       "ms_per_step": round(sum(ms) / len(ms), 3)}
+    sout["stage_ms_per_set"] = stage_breakdown(hs, sjobs, stream, flush)
     res["mixed_small"] = sout
+    # a batch of the serving run's mean size (~78 requests of one set, log-U[16 B, 4 KB])
+    bjobs = []
+    for i, ps in enumerate(("128f", "192f", "256f")):
+        wl = inputs.make(ps, 78, 16, ("loguniform", 16, 4096), inputs.BASE_SEED + 70 + i, "%s-78-serving" % ps)
+        _, sk = hs.hs_keygen(ps, dev(wl.seeds))
+        bjobs.append({"params": ps, "sk": sk, "msgs": dev(wl.msgs), "lens": dev(wl.lens),
+                      "key_idx": dev(wl.key_idx), "num_keys": wl.num_keys,
+                      "sigs": torch.empty(wl.count * hs.sig_bytes(ps), dtype=torch.uint8, device="cuda")})
+    res["serving_batch"] = {"workload": "78 requests of one set, log-U[16 B, 4 KB], 16 keys (the serving run's "
+                                        "mean batch)", "stage_ms_per_set": stage_breakdown(hs, bjobs, stream, flush)}
     return res
 
 
-def measure_serving(hs, inputs, seconds, rhos, burst=60000):
-    """Config-5 style serving run: 1024 resident keys (614/256/154), mix
-    60/25/15 of 128f/192f/256f, log-uniform 16 B - 4 KB messages, an 8 GiB
-    device-memory admission budget.  First a saturating burst (all requests
-    at t = 0) measures the peak rate of this mix; then Poisson arrivals at
-    rho x peak for 'seconds' each, reporting achieved rate and p50/p99
-    latency from arrival to host-observed completion."""
+def stage_breakdown(hs, jobs, stream, flush, reps=5):
+    """Per-stage CUDA-event times (median of reps) of each job signed alone."""
+    out = {}
+    for j in jobs:
+        runs = []
+        for r in range(reps + 1):
+            flush.fill_(r & 0xFF)
+            hs.hs_profile_enable(True)
+            hs.hs_sign_batch(j["params"], j["sk"], j["msgs"], j["lens"], key_idx=j["key_idx"], sigs=j["sigs"],
+                             num_keys=j["num_keys"], stream=stream)
+            prof = hs.hs_profile_read()
+            hs.hs_profile_enable(False)
+            if r:                          # the first is a warm-up
+                runs.append(prof)
+        med = {k: round(sorted(p[k] for p in runs)[len(runs) // 2], 3) for k in runs[0]}
+        med["total"] = round(sum(v for k, v in med.items()), 3)
+        med["messages"] = int(j["lens"].numel())
+        med["max_msg_bytes"] = int(j["lens"].max().item())
+        out[j["params"]] = med
+    return out
+
+
+def _replay_point(srv, inputs, np, rate, seconds, seed):
+    """Poisson arrivals at 'rate' for 'seconds'; achieved rate and latency."""
+    tr = inputs.serving_trace(rate=rate, seconds=seconds, seed=seed)
+    n = len(tr["params"])
+    st0 = srv.stats()
+    lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
+                        tr["arrival_ns"], timeout_ms=int(seconds * 1000) + 120000)
+    st1 = srv.stats()
+    finish = (tr["arrival_ns"].astype(np.float64) + lat.astype(np.float64)).max() / 1e9
+    nb = st1["batches"] - st0["batches"]
+    return {"offered": round(rate, 1), "seconds": seconds, "requests": n, "value": round(n / finish, 1),
+            "unit": "signatures/s", "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
+            "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3), "max_ms": round(float(lat.max()) / 1e6, 3),
+            "batches": nb, "mean_batch": round((st1["batched_requests"] - st0["batched_requests"]) / max(1, nb), 1)}
+
+
+def measure_serving(hs, inputs, seconds, rhos, search_steps, p99_bound_ms, burst=60000):
+    """Serving run: 1024 resident keys (614/256/154), mix 60/25/15 of
+    128f/192f/256f, log-uniform 16 B - 4 KB messages, an 8 GiB device-memory
+    admission budget.  A saturating burst (all requests at t = 0) measures
+    the peak rate of this mix; then Poisson arrivals at rho x peak for
+    'seconds' each, reporting achieved rate and p50/p99 latency from arrival
+    to host-observed completion; then the sustained capacity: the highest
+    offered rate whose p99 stays within p99_bound_ms over 'seconds', found by
+    bisection ('search_steps' runs) between the highest rho that held and
+    1.05 x the burst peak."""
     import numpy as np
     import torch
     budget, max_batch, inflight = 8 << 30, 2048, 4
@@ -425,7 +523,8 @@ def measure_serving(hs, inputs, seconds, rhos, burst=60000):
     for ps in ("128f", "192f", "256f"):
         keys[ps] = hs.hs_keygen(ps, torch.from_numpy(base["seeds"][ps]).cuda())[1]
     out = {"workload": "serving: 1024 keys (614/256/154), mix 60/25/15 128f/192f/256f, log-U[16 B, 4 KB]",
-           "mem_budget_bytes": budget, "max_batch": max_batch, "max_inflight": inflight}
+           "mem_budget_bytes": budget, "max_batch": max_batch, "max_inflight": inflight,
+           "p99_bound_ms": p99_bound_ms}
     with hs.Server(keys, max_inflight=inflight, max_batch=max_batch, mem_budget=budget) as srv:
         tr = inputs.serving_trace(rate=1e6, seconds=burst / 1e6, seed=inputs.BASE_SEED + 40)
         tr["arrival_ns"][:] = 0
@@ -443,50 +542,87 @@ def measure_serving(hs, inputs, seconds, rhos, burst=60000):
         out["burst"] = {"requests": n, "value": round(peak, 1), "unit": "signatures/s",
                         "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
                         "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3)}
+        held = 0.0
         for rho in rhos:
-            tr = inputs.serving_trace(rate=rho * peak, seconds=seconds, seed=inputs.BASE_SEED + 41 + int(rho * 100))
-            n = len(tr["params"])
-            log("serving: rho %.2f, %d requests" % (rho, n))
-            try:
-                lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
-                                    tr["arrival_ns"], timeout_ms=int(seconds * 1000) + 60000)
-            except hs.HSError:
-                log("serving: replay timed out; server stats %s" % srv.stats())
-                raise
-            finish = (tr["arrival_ns"].astype(np.float64) + lat.astype(np.float64)).max() / 1e9
-            st = srv.stats()
-            out["rho_%.2f" % rho] = {"offered": round(rho * peak, 1), "requests": n,
-                                     "value": round(n / finish, 1), "unit": "signatures/s",
-                                     "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
-                                     "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3),
-                                     "max_ms": round(float(lat.max()) / 1e6, 3)}
+            log("serving: rho %.2f for %.0f s" % (rho, seconds))
+            pt = _replay_point(srv, inputs, np, rho * peak, seconds, inputs.BASE_SEED + 41 + int(rho * 100))
+            out["rho_%.2f" % rho] = pt
+            if pt["p99_ms"] <= p99_bound_ms:
+                held = max(held, rho)
+        # sustained capacity: bisection on rho for p99 <= bound
+        lo, hi, best = held, 1.05, None
+        if held > 0:
+            best = dict(out["rho_%.2f" % held], rho=held)
+        search = []
+        for k in range(search_steps):
+            mid = round((lo + hi) / 2, 4)
+            log("serving: capacity search rho %.4f for %.0f s" % (mid, seconds))
+            pt = _replay_point(srv, inputs, np, mid * peak, seconds, inputs.BASE_SEED + 300 + k)
+            pt["rho"] = mid
+            search.append(pt)
+            if pt["p99_ms"] <= p99_bound_ms:
+                lo, best = mid, pt
+            else:
+                hi = mid
+        out["capacity_search"] = search
+        out["sustained"] = best
         st = srv.stats()
         out["batches"] = st["batches"]
         out["mean_batch"] = round(st["batched_requests"] / max(1, st["batches"]), 1)
         out["max_inflight_batches"] = st["max_inflight_batches"]
         out["max_device_bytes_in_use"] = st["max_device_bytes_in_use"]
     # the same keys as keysets with their top 2 layers prebuilt: the same
-    # saturating burst and the load of the uncached peak rate
+    # saturating burst, and the load of the uncached sustained capacity
     with hs.Server(keys, max_inflight=inflight, max_batch=max_batch, mem_budget=budget, cache_layers=2) as srv:
         cached = {"cache_layers": 2}
-        for name, rate in (("burst", None), ("rho_1.00_of_uncached_peak", peak)):
-            if rate is None:
-                tr = inputs.serving_trace(rate=1e6, seconds=burst / 1e6, seed=inputs.BASE_SEED + 40)
-                tr["arrival_ns"][:] = 0
-            else:
-                tr = inputs.serving_trace(rate=rate, seconds=seconds, seed=inputs.BASE_SEED + 141)
-            n = len(tr["params"])
-            log("serving with cached top layers: %s, %d requests" % (name, n))
-            t0 = time.perf_counter()
-            lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
-                                tr["arrival_ns"], timeout_ms=int(seconds * 1000) + 120000)
-            wall = time.perf_counter() - t0
-            finish = (tr["arrival_ns"].astype(np.float64) + lat.astype(np.float64)).max() / 1e9
-            cached[name] = {"requests": n, "value": round(n / (wall if rate is None else finish), 1),
-                            "unit": "signatures/s", "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
-                            "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3)}
+        tr = inputs.serving_trace(rate=1e6, seconds=burst / 1e6, seed=inputs.BASE_SEED + 40)
+        tr["arrival_ns"][:] = 0
+        n = len(tr["params"])
+        log("serving with cached top layers: burst of %d" % n)
+        t0 = time.perf_counter()
+        lat, _ = srv.replay(tr["params"], tr["keys"], tr["pool_idx"], tr["pool_msgs"], tr["pool_lens"],
+                            tr["arrival_ns"], timeout_ms=120000)
+        cached["burst"] = {"requests": n, "value": round(n / (time.perf_counter() - t0), 1),
+                           "unit": "signatures/s", "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
+                           "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3)}
+        if best is not None:
+            sec = min(seconds, 20.0)
+            log("serving with cached top layers: at the uncached sustained rate for %.0f s" % sec)
+            cached["at_uncached_sustained"] = _replay_point(srv, inputs, np, best["offered"], sec,
+                                                            inputs.BASE_SEED + 141)
         out["cached_top_layers"] = cached
     return out
+
+
+def summarize(line):
+    """The figures a reader looks for first, as a short object at the end of
+    the JSON line."""
+    r = line.get("roofline") or {}
+    sm = {"sig_per_s": line.get("value"), "e2e_sig_per_s": (line.get("e2e") or {}).get("value"),
+          "alu_frac_executed": r.get("frac"), "alu_frac_full_compression": r.get("frac_full_compression"),
+          "issue_frac": r.get("issue_frac")}
+    p = line.get("plain_per_stage") or {}
+    sm["plain_per_stage_sig_per_s"] = p.get("value")
+    sv = line.get("serving") or {}
+    for key in ("rho_0.50", "rho_0.75"):
+        if isinstance(sv.get(key), dict):
+            sm["serving_" + key] = {k: sv[key].get(k) for k in ("seconds", "value", "p50_ms", "p99_ms")}
+    if isinstance(sv.get("sustained"), dict):
+        b = sv["sustained"]
+        sm["serving_sustained"] = {"rho": b.get("rho"), "offered": b.get("offered"), "value": b.get("value"),
+                                   "p50_ms": b.get("p50_ms"), "p99_ms": b.get("p99_ms"),
+                                   "p99_bound_ms": sv.get("p99_bound_ms"), "seconds": b.get("seconds")}
+    if isinstance(sv.get("burst"), dict):
+        sm["serving_burst_sig_per_s"] = sv["burst"].get("value")
+    oc = line.get("other_configs") or {}
+    for key in ("mixed_small", "mixed"):
+        if isinstance(oc.get(key), dict):
+            sm[key + "_ms"] = {k: v.get("ms_per_step") for k, v in oc[key].items() if isinstance(v, dict)
+                               and "ms_per_step" in v}
+    for ps in ("192f", "256f"):
+        if isinstance(oc.get(ps), dict):
+            sm[ps + "_sig_per_s"] = oc[ps].get("value")
+    return sm
 
 
 def run_verify_only(args):
@@ -635,8 +771,10 @@ def run_own(args):
     stage_avg = {k: round(sum(v) / len(v), 3) for k, v in stage_ms.items()}
     sm_mhz_peak = 2070.0
     alu_peak = sm_count * alu_rate * sm_mhz_peak * 1e6 / 1e12
-    alu_work = alu_ops_per_sig(ps, "tree") * count
+    alu_work = exec_alu_per_sig(ps, "tree") * count
+    alu_work_full = alu_ops_per_sig(ps, "tree") * count
     achieved = alu_work / (tree_ms / 1e3) / 1e12 if tree_ms > 0 else None
+    achieved_full = alu_work_full / (tree_ms / 1e3) / 1e12 if tree_ms > 0 else None
     issue_peak = int_peak_tops(sm_count, sm_mhz_peak)
     issue_achieved = ops_per_sig(ps, "tree") * count / (tree_ms / 1e3) / 1e12 if tree_ms > 0 else None
     traffic = None
@@ -653,10 +791,15 @@ def run_own(args):
                                        if tree_c and tree_ms > 0 else None),
                 "achieved": round(achieved, 3) if achieved else None, "peak": round(alu_peak, 3),
                 "unit": "Tops/s", "frac": round(achieved / alu_peak, 4) if achieved else None, "traffic": traffic,
+                "frac_full_compression": round(achieved_full / alu_peak, 4) if achieved_full else None,
+                "issue_frac": round(issue_achieved / issue_peak, 4) if issue_achieved else None,
                 "peak_basis": "ALU pipe %.1f lane-ops/clk/SM (measured LOP3/SHF rate) x %d SMs x %.0f MHz"
                               % (alu_rate, sm_count, sm_mhz_peak),
-                "work_basis": "%d ALU-pipe ops per SHA-256 compression, %d per SHA-512; %.4g per launch"
-                              % (ALU_C256, ALU_C512, alu_work),
+                "work_basis": "ALU-pipe ops as executed: chain steps run rounds 5..63 with sigma terms of "
+                              "constant words folded (%d per 128f step), T_len / H in full (%d per SHA-256 "
+                              "block, %d per SHA-512); %.4g per launch; frac_full_compression prices every "
+                              "compression in full (%.4g per launch)"
+                              % (_step_alu(4), ALU_C256, ALU_C512, alu_work, alu_work_full),
                 "issue": {"achieved": round(issue_achieved, 3) if issue_achieved else None,
                           "peak": round(issue_peak, 3),
                           "frac": round(issue_achieved / issue_peak, 4) if issue_achieved else None,
@@ -665,6 +808,23 @@ def run_own(args):
                 "measured_pipes_lane_ops_per_clk_per_sm": pipes}
     if clk.get("sm_mhz") and achieved:
         roofline["frac_at_sampled_clock"] = round(achieved / (sm_count * alu_rate * clk["sm_mhz"] * 1e6 / 1e12), 4)
+
+    # the same workload through the plain per-stage kernels: no chain
+    # checkpoints, so WOTS+_Sign recomputes every chain from its secret
+    plain = None
+    if rank == 0:
+        hs.hs_set_chain_checkpoint(0)
+        try:
+            hs.hs_profile_enable(True)
+            pms = _time_steps(step, stream, flush, max(3, args.steps // 2), 3)
+            pprof = hs.hs_profile_read()
+            hs.hs_profile_enable(False)
+        finally:
+            hs.hs_set_chain_checkpoint(2)
+        plain = {"value": round(count * len(pms) / (sum(pms) / 1e3), 1), "unit": "signatures/s",
+                 "ms_per_step": round(sum(pms) / len(pms), 3), "checkpoint_stride": 0,
+                 "stage_ms": {a: round(b, 3) for a, b in pprof.items()},
+                 "what": "the line's workload with WOTS+_Sign recomputing its chains (no TREE_Sign checkpoints)"}
 
     # the other workloads of the signer's specification, measured with the
     # same events: 192f / 256f batches, and the mixed-parameter batch in one
@@ -679,7 +839,8 @@ def run_own(args):
     serving = None
     if args.serving_seconds > 0 and rank == 0:
         try:
-            serving = measure_serving(hs, inputs, args.serving_seconds, (0.5, 0.75, 1.0))
+            serving = measure_serving(hs, inputs, args.serving_seconds, (0.5, 0.75), args.serving_search,
+                                      args.p99_bound_ms)
         except Exception as exc:
             serving = {"error": repr(exc)[:300]}
 
@@ -721,7 +882,9 @@ def run_own(args):
         "wall_s": round(wall, 3),
         "device": props.name, "sm_count": sm_count,
         "tuning": {k: autotune.get(ps, k) for k in autotune.KNOBS} | {"from_cache": bool(tuned)},
+        "plain_per_stage": plain,
     }
+    line["summary"] = summarize(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     replicas.barrier()
@@ -748,8 +911,12 @@ def main():
                     help="parameter set (the default workload is 128f; the others serve small profiling cases)")
     ap.add_argument("--no-other-configs", dest="other_configs", action="store_false",
                     help="skip the 192f / 256f / mixed-parameter measurements")
-    ap.add_argument("--serving-seconds", type=float, default=3.0,
+    ap.add_argument("--serving-seconds", type=float, default=60.0,
                     help="seconds of Poisson load per rate in the serving measurement (0 = skip)")
+    ap.add_argument("--serving-search", type=int, default=3,
+                    help="bisection steps of the sustained-capacity search (runs of --serving-seconds each)")
+    ap.add_argument("--p99-bound-ms", type=float, default=25.0,
+                    help="p99 latency bound that defines the sustained serving capacity")
     ap.add_argument("--verify-only", action="store_true",
                     help="sign the batch once, then time hs_verify_batch on it (3 calls) and print one line")
     ap.add_argument("--count", type=int, default=16384,

@@ -67,7 +67,8 @@ typedef enum {
     HS_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
     HS_ETIMEOUT = 4, /* a bounded wait ran out */
     HS_EKEY = 5,     /* a key index was >= the number of keys */
-    HS_ECANCELED = 6 /* a server request was cancelled before it ran */
+    HS_ECANCELED = 6,/* a server request was cancelled before it ran */
+    HS_EBUDGET = 7   /* a server request can never fit the server's memory budget */
 } hs_status;
 
 /* Sizes in bytes for a parameter set; 0 for an invalid enum.
@@ -160,8 +161,16 @@ hs_status hs_verify_batch(hs_params p, const uint8_t *pk, uint32_t num_keys,
  */
 hs_status hs_check_status(void *stream, uint32_t *flags);
 
-/* Text of the most recent host-side error of the calling thread. */
+/* Text of the most recent error of the calling thread: argument and launch
+ * errors found on the host, and the key-index error hs_check_status reports
+ * for the kernels.  The text stays until the thread's next error (calls that
+ * succeed do not clear it).  hs_last_error returns a pointer that stays
+ * valid until that next error; hs_last_error_copy copies the text into the
+ * caller's buffer of 'len' bytes, truncated to len - 1 bytes and always
+ * NUL-terminated, and returns HS_EINVAL (copying nothing) if buf is NULL or
+ * len is 0. */
 const char *hs_last_error(void);
+hs_status hs_last_error_copy(char *buf, size_t len);
 
 /*
  * Per-stage timing for measurement.  While enabled, every hs_sign_batch call
@@ -244,7 +253,11 @@ int32_t hs_tune_get(hs_params p, int knob);
  *   device; nkeys[p] = 0 disables set p).  The current device is used.
  * hs_server_submit: copies the message; the signature is written to sig_out
  *   (host memory, hs_sig_bytes(p) bytes, valid until completion; NULL =
- *   compute and discard, for load tests).  HS_EKEY for a key index >= nkeys.
+ *   compute and discard, for load tests).  HS_EKEY for a key index >= nkeys;
+ *   HS_EBUDGET for a request that alone needs more device or pinned memory
+ *   than the server reserved (it could never be admitted); HS_EINVAL for
+ *   malformed arguments (NULL server, bad set, NULL message of nonzero
+ *   length).
  * hs_server_wait: blocks up to timeout_ms; HS_ETIMEOUT if still pending.
  * hs_server_poll: hands out each finished request once (id, latency from
  *   arrival to host-observed completion in ns, and its hs_status: HS_OK,
@@ -407,19 +420,33 @@ hs_status hs_keyset_destroy(hs_keyset *ks);
  * HS_NOALLOC_SCRATCH_BYTES (8 MiB) that every GPU which loads this library
  * holds until the process exits.  Arguments and outputs are those of
  * hs_sign_batch, with these differences:
- *  - every buffer (sk, key_idx, msgs, lens, sigs) must be device memory;
- *    host pointers are rejected with HS_EINVAL (staging them would allocate);
- *    msgs may not be NULL;
+ *  - every buffer (sk, key_idx, msgs, lens, sigs) must be device memory of
+ *    the current device: host pointers (staging them would allocate) and
+ *    buffers of another GPU are rejected with HS_EINVAL; msgs may not be
+ *    NULL;
  *  - a batch whose scratch does not fit the array is rejected with HS_EINVAL
  *    and hs_last_error() states the bytes needed and available.  The need is
- *    256 + 256 * num_keys + about 1.0 KB (128f), 1.4 KB (192f) or 1.8 KB
- *    (256f) per message, so about 8000 / 5800 / 4600 messages fit;
+ *    about 512 + 256 * num_keys bytes plus, per message, 1.0 KB (128f),
+ *    1.4 KB (192f) or 1.8 KB (256f), so about 8000 / 5800 / 4600 messages
+ *    fit.  The small-signature sets keep every leaf of their 512- or
+ *    256-leaf trees in scratch: 57 KB (128s), 85 KB (192s) or 65 KB (256s)
+ *    per message, so only about 140 / 95 / 125 messages fit.  The SHAKE sets
+ *    need what their SHA2 counterparts need;
+ *  - TREE_Sign runs chain-parallel (as hs_sign_batch does for small batches)
+ *    only when its chain ends also fit the array -- 96 KB (128f), 210 KB
+ *    (192f), 570 KB (256f) more per message, so up to about 80 / 38 / 14
+ *    messages -- and one thread per leaf otherwise; the bytes are the same;
  *  - WOTS+_Sign recomputes its chains (no chain checkpoints are kept);
  *  - a key_idx entry >= num_keys gives an all-zero signature for that
- *    message; it is not reported through hs_check_status.
+ *    message.  It is reported through hs_check_status once the library has
+ *    set up the current device (hs_keygen, hs_sign_batch or hs_check_status
+ *    has run on it); before that, it is not reported.
  * Set-up: the first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, and caches it; make that
- * first call before any stream capture on the device.
+ * first call before any stream capture on the device.  The cached address
+ * belongs to the device's current context: after cudaDeviceReset this entry
+ * point (like the rest of the library) must not be used again in the
+ * process.
  * All calls on a device share the one array, and it keeps the previous
  * call's contents (the call clears the words that must start at zero).
  * Calls whose work overlaps on the GPU race on the array: issue them on one

@@ -17,8 +17,8 @@
  *   F, PRF               : SHA-256 always
  *   H, T_l, H_msg, PRF_msg: SHA-256 at n = 16, SHA-512 at n = 24 / 32
  *   deterministic signing: opt_rand = PK.seed
- * Readings of points the paper leaves open are listed in the design doc and are
- * marked "READING" below.
+ * Each point the paper leaves open is decided where it is used, in a comment
+ * marked "READING" that states the reading taken.
  *
  * Style.  Every function follows its definition directly: whole SHA-2 over a
  * fully assembled input (no midstates), recursive Merkle node() with no

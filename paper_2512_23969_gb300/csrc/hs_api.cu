@@ -239,6 +239,16 @@ uint32_t* device_status_word() {
     return dev_state(&d) == HS_OK ? d->status : nullptr;
 }
 
+uint32_t* device_status_word_if_ready() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_dev[dev].init ? g_dev[dev].status : nullptr;
+}
+
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
     DevState* d = nullptr;
     if (dev_state(&d) != HS_OK) return cudaErrorUnknown;
@@ -308,6 +318,13 @@ HS_API size_t hs_pk_bytes(hs_params p) { SetInfo s; return set_info(p, &s) ? (si
 HS_API size_t hs_sk_bytes(hs_params p) { SetInfo s; return set_info(p, &s) ? (size_t)4 * s.n : 0; }
 HS_API size_t hs_seed_bytes(hs_params p) { SetInfo s; return set_info(p, &s) ? (size_t)3 * s.n : 0; }
 HS_API const char* hs_last_error(void) { return g_err.c_str(); }
+HS_API hs_status hs_last_error_copy(char* buf, size_t len) {
+    if (!buf || len == 0) return HS_EINVAL;      // the error text itself is kept
+    const size_t n = std::min(len - 1, g_err.size());
+    memcpy(buf, g_err.data(), n);
+    buf[n] = '\0';
+    return HS_OK;
+}
 HS_API int hs_sign_kernel_count(void) { return 7; }
 
 HS_API int hs_tune_options(hs_params p, int knob, int32_t* values, int max) {

@@ -77,6 +77,9 @@ void set_last_error(const char* msg);
 // word (nullptr if the device state could not be set up), a stream-ordered
 // allocation from the library's pool, and the chain checkpoint stride.
 uint32_t* device_status_word();
+// The same word if the library has already set up the current device, else
+// nullptr; never allocates.
+uint32_t* device_status_word_if_ready();
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
 uint32_t chain_checkpoint_stride();
 

@@ -72,13 +72,15 @@ hs_status mixed_dev(MixedDev** out) {
     return HS_OK;
 }
 
-bool is_dev(const void* p) {
+// Device memory of the current device 'dev' (or managed memory); memory of
+// another GPU is refused, since the kernels would reach it without peer access.
+bool is_dev(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
 }
 
 // Enqueue every job's stage DAG (fork from / join into 'origin').
@@ -118,15 +120,20 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
     std::vector<Batch> bs;
     std::vector<size_t> off;
     size_t total = 0;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return mx_fail(HS_ECUDA, "hs_sign_mixed: no usable current device");
+    }
     for (uint32_t j = 0; j < njobs; j++) {
         const hs_sign_job& jb = jobs[j];
         if ((int)jb.params < 0 || (int)jb.params >= kNumSets) return mx_fail(HS_EINVAL, "hs_sign_mixed: invalid parameter set");
         if (jb.count == 0) continue;
         if (!jb.sk || !jb.msgs || !jb.lens || !jb.sigs || jb.num_keys == 0)
             return mx_fail(HS_EINVAL, "hs_sign_mixed: NULL buffer or num_keys == 0");
-        if (!is_dev(jb.sk) || !is_dev(jb.msgs) || !is_dev(jb.lens) || !is_dev(jb.sigs) ||
-            (jb.key_idx && !is_dev(jb.key_idx)))
-            return mx_fail(HS_EINVAL, "hs_sign_mixed: every buffer must be device memory");
+        if (!is_dev(jb.sk, dev) || !is_dev(jb.msgs, dev) || !is_dev(jb.lens, dev) || !is_dev(jb.sigs, dev) ||
+            (jb.key_idx && !is_dev(jb.key_idx, dev)))
+            return mx_fail(HS_EINVAL, "hs_sign_mixed: every buffer must be memory of the current device");
         Batch b{};
         b.pset = jb.params;
         b.keys_in = jb.sk;

@@ -3,12 +3,15 @@
 // library and forbid it its own allocations (see include/hs.h).
 //
 // The scratch of a batch (key blocks, message offsets, digest fields, FORS
-// roots, PK_FORS, layer roots and the status word) lives in one file-scope
-// device array.  Host code cannot use the array's name as a device address,
+// roots, PK_FORS, layer roots, the chain ends of the chain-parallel
+// TREE_Sign form, the leaves of wide trees) lives in one file-scope device
+// array.  Host code cannot use the array's name as a device address,
 // so the first call on each device looks the address up with
 // cudaGetSymbolAddress (that device current) and caches it per device.  The
 // kernels are the same ones hs_sign_batch launches, in the same order, with
-// chain checkpoints off so that the scratch stays small.
+// chain checkpoints off so that the scratch stays small.  The cached address
+// belongs to the device's current context: it does not survive
+// cudaDeviceReset (nor does the rest of the library's per-device state).
 #include <cuda_runtime.h>
 #include <cstdio>
 #include <mutex>
@@ -32,13 +35,15 @@ hs_status na_fail(hs_status st, const char* msg) {
     return st;
 }
 
-bool is_device_ptr(const void* p) {
+// Device memory of the current device 'dev' (or managed memory).  Memory of
+// another GPU is refused: the kernels would reach it without peer access.
+bool is_device_ptr(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
 }
 
 // Device address of the array on the current device (looked up once).
@@ -77,10 +82,23 @@ HS_API hs_status hs_sign_batch_noalloc(hs_params p, const uint8_t* sk, uint32_t 
     if (count == 0) return HS_OK;
     if (!sk || !msgs || !lens || !sigs) return na_fail(HS_EINVAL, "hs_sign_batch_noalloc: NULL buffer");
     if (num_keys == 0) return na_fail(HS_EINVAL, "hs_sign_batch_noalloc: num_keys must be > 0");
-    if (!is_device_ptr(sk) || !is_device_ptr(msgs) || !is_device_ptr(lens) || !is_device_ptr(sigs) ||
-        (key_idx && !is_device_ptr(key_idx)))
-        return na_fail(HS_EINVAL, "hs_sign_batch_noalloc: every buffer must be device memory");
-    const size_t need = kStatusBytes + scratch_bytes(p, num_keys, count, 0);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return na_fail(HS_ECUDA, "hs_sign_batch_noalloc: no usable current device");
+    }
+    if (!is_device_ptr(sk, dev) || !is_device_ptr(msgs, dev) || !is_device_ptr(lens, dev) ||
+        !is_device_ptr(sigs, dev) || (key_idx && !is_device_ptr(key_idx, dev)))
+        return na_fail(HS_EINVAL, "hs_sign_batch_noalloc: every buffer must be memory of the current device");
+    // TREE_Sign's form: chain-parallel where hs_sign_batch would use it and
+    // its chain-end region fits the array, otherwise one thread per leaf
+    // (the same bytes either way).
+    bool split = tree_split(p, count);
+    size_t need = kStatusBytes + scratch_bytes(p, num_keys, count, 0, split);
+    if (split && need > HS_NOALLOC_SCRATCH_BYTES) {
+        split = false;
+        need = kStatusBytes + scratch_bytes(p, num_keys, count, 0, false);
+    }
     if (need > HS_NOALLOC_SCRATCH_BYTES) {
         char buf[256];
         snprintf(buf, sizeof(buf),
@@ -103,10 +121,15 @@ HS_API hs_status hs_sign_batch_noalloc(hs_params p, const uint8_t* sk, uint32_t 
     b.count = count;
     b.sigs = sigs;
     b.ck = 0;
-    b.status = static_cast<uint32_t*>(base);
+    b.split = split;
+    // Key-index errors go to the status word hs_check_status reads when the
+    // library has already set it up on this device (by any earlier call);
+    // otherwise to a word at the start of the array, which nothing reads.
+    uint32_t* shared_status = device_status_word_if_ready();
+    b.status = shared_status ? shared_status : static_cast<uint32_t*>(base);
     carve_scratch(b, static_cast<char*>(base) + kStatusBytes);
 
-    cudaError_t e = cudaMemsetAsync(b.status, 0, sizeof(uint32_t), s);
+    cudaError_t e = shared_status ? cudaSuccess : cudaMemsetAsync(b.status, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess) e = launch_keyprep(b, false, s);
     if (e == cudaSuccess) e = launch_offsets(b, s);
     if (e == cudaSuccess) e = launch_message(b, false, s);

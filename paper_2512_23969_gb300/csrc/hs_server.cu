@@ -409,7 +409,7 @@ static hs_status submit_at(hs_server* s, hs_params p, uint32_t key, const uint8_
     r.t_arrive = t_arrive;
     const Need one = batch_need(p, 1, len, sv.ks[p]);
     if (one.dev > sv.dev_arena.cap() || one.host > sv.host_arena.cap())
-        return sv_fail(HS_EINVAL, "hs_server_submit: request larger than the memory budget");
+        return sv_fail(HS_EBUDGET, "hs_server_submit: request larger than the memory budget");
     uint64_t rid;
     {
         std::lock_guard<std::mutex> lk(sv.mu);

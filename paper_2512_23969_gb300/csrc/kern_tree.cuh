@@ -11,10 +11,11 @@
 // GB300 mapping: one thread per leaf, the 2^h' leaves of a tree in an
 // aligned lane group of one warp, so the Merkle levels are merged with warp
 // shuffles (no shared memory, no barriers).  Each thread runs its len
-// chains back to back and streams every chain end straight into the T_len
-// hash, so only one chain value plus the running T_len state are live.  The
-// PRF and the 15 F steps of a chain share one call site of the fully
-// unrolled SHA-256 compression (all known-zero message words folded).
+// chains back to back and stores every chain end in a per-thread array
+// (len * n bytes, local memory); T_len then runs over that array block by
+// block, so no T_len hash state is live across the chain loop.  The PRF and
+// the 15 F steps of a chain share one call site of the fully unrolled
+// SHA-256 compression (all known-zero message words folded).
 // All d layers of all messages form one flat grid: the layers of a
 // signature are independent given the digest (paper Fig. 2).
 #pragma once

@@ -17,7 +17,7 @@ N_BYTES.update({"shake-" + k: v for k, v in list(N_BYTES.items()) if k != "toy"}
 NUM_PARAMS = 13
 _N_BY_ID = [16, 24, 32, 16, 16, 24, 32, 16, 24, 32, 16, 24, 32]
 STATUS = {0: "HS_OK", 1: "HS_EINVAL", 2: "HS_ENOMEM", 3: "HS_ECUDA", 4: "HS_ETIMEOUT", 5: "HS_EKEY",
-          6: "HS_ECANCELED"}
+          6: "HS_ECANCELED", 7: "HS_EBUDGET"}
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libhs.so")
 
 _lib = None
@@ -46,6 +46,8 @@ def load():
     L.hs_verify_batch.argtypes = [C.c_int, vp, u32, vp, vp, u64p, vp, u32, vp, vp]
     L.hs_check_status.argtypes = [vp, C.POINTER(C.c_uint32)]
     L.hs_last_error.restype = C.c_char_p
+    L.hs_last_error_copy.argtypes = [C.c_char_p, C.c_size_t]
+    L.hs_last_error_copy.restype = C.c_int
     L.hs_profile_enable.argtypes = [C.c_int]
     L.hs_profile_read.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_char_p), C.c_int]
     L.hs_profile_read.restype = C.c_int
@@ -102,9 +104,16 @@ def _pid(params):
     return PARAMS[params] if isinstance(params, str) else int(params)
 
 
+def last_error(maxlen=512):
+    """The calling thread's most recent error text (hs_last_error_copy)."""
+    buf = C.create_string_buffer(maxlen)
+    load().hs_last_error_copy(buf, maxlen)
+    return buf.value.decode(errors="replace")
+
+
 def _check(rc):
     if rc != 0:
-        raise HSError(rc, load().hs_last_error().decode(errors="replace"))
+        raise HSError(rc, last_error())
 
 
 def _ptr(x):

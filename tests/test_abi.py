@@ -69,3 +69,26 @@ def test_product_never_imports_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
                 assert "spx_oracle" not in text, f
+
+
+def test_last_error_copy_fills_caller_buffer(lib):
+    """hs_last_error_copy: the thread's last error text into the caller's
+    buffer, truncated and NUL-terminated; NULL or empty buffers are refused."""
+    lib.hs_set_chain_checkpoint.argtypes = [C.c_uint32]
+    lib.hs_set_chain_checkpoint.restype = C.c_int
+    lib.hs_last_error.restype = C.c_char_p
+    lib.hs_last_error_copy.argtypes = [C.c_char_p, C.c_size_t]
+    lib.hs_last_error_copy.restype = C.c_int
+    assert lib.hs_set_chain_checkpoint(3) == 1                  # HS_EINVAL, sets the text
+    full = lib.hs_last_error()
+    assert b"stride" in full
+    buf = C.create_string_buffer(b"\xff" * 256, 256)
+    assert lib.hs_last_error_copy(buf, 256) == 0
+    assert buf.value == full
+    small = C.create_string_buffer(b"\xff" * 8, 8)
+    assert lib.hs_last_error_copy(small, 8) == 0
+    assert small.raw == full[:7] + b"\0"                        # 7 bytes and the terminator
+    assert lib.hs_last_error_copy(None, 16) == 1
+    assert lib.hs_last_error_copy(small, 0) == 1
+    assert lib.hs_last_error() == full                          # a refused copy keeps the text
+    assert lib.hs_set_chain_checkpoint(2) == 0                  # the default again

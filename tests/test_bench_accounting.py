@@ -75,3 +75,52 @@ def test_per_call_blocks(O):
         assert _blocks(O, ps, O.THASH_H) == ((0, 1, 0) if P.big else (1, 0, 0))
         assert _blocks(O, "shake-" + ps, O.THASH_F) == (0, 0, 1)
         assert _blocks(O, "shake-" + ps, O.THASH_H) == (0, 0, 1)
+
+
+def _enumerated_step_alu(nw, ctx):
+    """ALU ops of one one-block SHA-256 F / PRF call, enumerated round by
+    round and word by word: message words 0..4 are the address (their
+    rounds and sigma0 terms come from a per-chain context when ctx), words
+    5 .. 5 + nw carry data, words 6 + nw .. 14 are zero, word 15 is the
+    constant bit length.  Sigma / sigma terms of a known word cost nothing."""
+    known = set(range(6 + nw, 15)) | {15}
+    hoisted = {1, 2, 3, 4} if ctx else set()
+    rounds = range(5, 64) if ctx else range(64)
+    ops = 10 * len(rounds)                         # Sigma0, Sigma1 (4 each), Ch, Maj
+    for t in range(16, 64):
+        if (t - 2) not in known:
+            ops += 4                               # sigma1(W[t-2])
+        if (t - 15) not in known and (t - 15) not in hoisted:
+            ops += 4                               # sigma0(W[t-15])
+    return ops
+
+
+@pytest.mark.parametrize("nw", [4, 6, 8])
+def test_executed_alu_model(nw):
+    assert bench._step_alu(nw, True) == _enumerated_step_alu(nw, True)
+    assert bench._step_alu(nw, False) == _enumerated_step_alu(nw, False)
+    assert bench._step_alu(nw, False) <= bench.ALU_C256
+
+
+def test_executed_alu_never_exceeds_full_basis():
+    for ps in SHA:
+        for st in ("tree", "fors"):
+            e, f = bench.exec_alu_per_sig(ps, st), bench.alu_ops_per_sig(ps, st)
+            assert 0.9 * f < e <= f, (ps, st)
+    # 128f TREE: 176 leaves x (35 chains x (2 x 66 + 16 x 926) + 10 x 1024) + 154 x 1024
+    assert bench.exec_alu_per_sig("128f", "tree") == 176 * (35 * (2 * 66 + 16 * 926) + 10 * 1024) + 154 * 1024
+
+
+def test_summary_lists_headline_figures():
+    line = {"value": 1.0, "e2e": {"value": 2.0}, "roofline": {"frac": 0.9, "frac_full_compression": 0.95,
+                                                               "issue_frac": 0.6},
+            "plain_per_stage": {"value": 0.8},
+            "serving": {"rho_0.75": {"seconds": 60, "value": 3, "p50_ms": 1, "p99_ms": 2},
+                        "sustained": {"rho": 0.9, "offered": 9, "value": 8, "p50_ms": 3, "p99_ms": 20,
+                                      "seconds": 60}, "p99_bound_ms": 25, "burst": {"value": 10}},
+            "other_configs": {"mixed_small": {"plain_per_set_calls": {"ms_per_step": 1.5}, "messages": 96}}}
+    sm = bench.summarize(line)
+    assert sm["alu_frac_executed"] == 0.9 and sm["issue_frac"] == 0.6
+    assert sm["plain_per_stage_sig_per_s"] == 0.8
+    assert sm["serving_rho_0.75"]["p99_ms"] == 2 and sm["serving_sustained"]["rho"] == 0.9
+    assert sm["mixed_small_ms"] == {"plain_per_set_calls": 1.5}

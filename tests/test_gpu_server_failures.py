@@ -9,7 +9,7 @@ from paper_2512_23969_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-HS_ECUDA, HS_ECANCELED = 3, 6
+HS_EINVAL, HS_ECUDA, HS_ECANCELED, HS_EBUDGET = 1, 3, 6, 7
 
 
 def _dev(x):
@@ -100,3 +100,20 @@ def test_cancel_pending_requests(hs):
         assert sorted(r for r, _, c in done if c == HS_ECANCELED) == sorted(reqs[i][0] for i in cancelled)
         with pytest.raises(hs.HSError):
             srv.cancel(reqs[0][0])                          # finished and collected: unknown
+
+
+def test_request_beyond_budget_is_ebudget(hs):
+    """A request that alone needs more memory than the server reserved can
+    never be admitted: HS_EBUDGET, distinct from HS_EINVAL for malformed
+    arguments; the server keeps serving."""
+    wl, sk, ref = _setup(hs, "toy", 4, 1, 74)
+    with hs.Server({"toy": sk}, max_inflight=1, max_batch=4, mem_budget=1 << 20, pinned=1 << 20) as srv:
+        with pytest.raises(hs.HSError) as e:
+            srv.submit("toy", 0, bytes(2 << 20))               # 2 MiB message, 1 MiB budget
+        assert e.value.code == HS_EBUDGET
+        assert "budget" in hs.last_error()
+        L = hs.load()
+        assert L.hs_server_submit(srv._h, 99, 0, None, 0, None, None) == HS_EINVAL     # no such set
+        rid, out = srv.submit("toy", int(wl.key_idx[0]), wl.message(0))
+        srv.wait(rid, timeout_ms=60000)
+        assert out.tobytes() == ref[0].tobytes()
