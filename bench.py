@@ -435,7 +435,7 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
     for wl in swls:
         pk, sk = hs.hs_keygen(wl.params, dev(wl.seeds))
         sjobs.append({"params": wl.params, "sk": sk, "msgs": dev(wl.msgs), "lens": dev(wl.lens),
-                      "key_idx": dev(wl.key_idx), "num_keys": wl.num_keys,
+                      "key_idx": dev(wl.key_idx), "num_keys": wl.num_keys, "max_len": int(wl.lens.max()),
                       "sigs": torch.empty(wl.count * hs.sig_bytes(wl.params), dtype=torch.uint8, device="cuda")})
     stotal = sum(wl.count for wl in swls)
 
@@ -452,7 +452,10 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
         ms = _time_steps(fn, stream, flush, max(steps, 5), warmup)
         sout[name] = {"value": round(stotal * len(ms) / (sum(ms) / 1e3), 1), "unit": "signatures/s",
                       "ms_per_step": round(sum(ms) / len(ms), 3)}
-    sout["stage_ms_per_set"] = stage_breakdown(hs, sjobs, stream, flush)
+    try:
+        sout["stage_ms_per_set"] = stage_breakdown(hs, sjobs, stream, flush)
+    except Exception as exc:
+        sout["stage_ms_per_set"] = {"error": repr(exc)[:200]}
     res["mixed_small"] = sout
     # a batch of the serving run's mean size (~78 requests of one set, log-U[16 B, 4 KB])
     bjobs = []
@@ -460,10 +463,14 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
         wl = inputs.make(ps, 78, 16, ("loguniform", 16, 4096), inputs.BASE_SEED + 70 + i, "%s-78-serving" % ps)
         _, sk = hs.hs_keygen(ps, dev(wl.seeds))
         bjobs.append({"params": ps, "sk": sk, "msgs": dev(wl.msgs), "lens": dev(wl.lens),
-                      "key_idx": dev(wl.key_idx), "num_keys": wl.num_keys,
+                      "key_idx": dev(wl.key_idx), "num_keys": wl.num_keys, "max_len": int(wl.lens.max()),
                       "sigs": torch.empty(wl.count * hs.sig_bytes(ps), dtype=torch.uint8, device="cuda")})
+    try:
+        bd = stage_breakdown(hs, bjobs, stream, flush)
+    except Exception as exc:
+        bd = {"error": repr(exc)[:200]}
     res["serving_batch"] = {"workload": "78 requests of one set, log-U[16 B, 4 KB], 16 keys (the serving run's "
-                                        "mean batch)", "stage_ms_per_set": stage_breakdown(hs, bjobs, stream, flush)}
+                                        "mean batch)", "stage_ms_per_set": bd}
     return res
 
 
@@ -484,7 +491,7 @@ def stage_breakdown(hs, jobs, stream, flush, reps=5):
         med = {k: round(sorted(p[k] for p in runs)[len(runs) // 2], 3) for k in runs[0]}
         med["total"] = round(sum(v for k, v in med.items()), 3)
         med["messages"] = int(j["lens"].numel())
-        med["max_msg_bytes"] = int(j["lens"].max().item())
+        med["max_msg_bytes"] = int(j["max_len"])
         out[j["params"]] = med
     return out
 

@@ -217,7 +217,9 @@ hs_status hs_set_chain_checkpoint(uint32_t stride);
  * identical for every setting; only speed changes.  Knobs:
  *   HS_TUNE_FORS_LANES      lanes of a warp that share one FORS tree
  *                           (each lane builds a subtree of 2^a / lanes
- *                           leaves, the rest merges by shuffles)
+ *                           leaves, the rest merges by shuffles); a batch
+ *                           too small to give FORS_Sign about 1024 threads
+ *                           per SM takes the next wider compiled value
  *   HS_TUNE_TREE_MIN_BLOCKS minimum resident 128-thread blocks per SM that
  *                           TREE_Sign is compiled for (0 = compiler's choice)
  *   HS_TUNE_TREE_SPLIT_BELOW batches of fewer messages than this run

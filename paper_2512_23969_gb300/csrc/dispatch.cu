@@ -52,6 +52,27 @@ bool tree_split(int pset, uint32_t count) {
     return below > 0 && count < (uint32_t)below;
 }
 
+int fors_lanes(int pset, uint32_t count) {
+    const SetOps* o = set_ops(pset);
+    SetShape sh{};
+    if (!o || !set_shape(pset, &sh)) return -1;
+    int lpt = tune_get(pset, 0);
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    const uint64_t want = (uint64_t)sms * 1024;
+    while ((uint64_t)count * sh.k * lpt < want) {
+        int wider = 0;                    // smallest compiled value above lpt
+        for (int i = 0; i < o->n_fors_lpt; i++)
+            if (o->fors_lpt[i] > lpt && (wider == 0 || o->fors_lpt[i] < wider)) wider = o->fors_lpt[i];
+        if (wider == 0) break;
+        lpt = wider;
+    }
+    return lpt;
+}
+
 bool tune_set(int pset, int knob, int value) {
     const SetOps* o = set_ops(pset);
     if (!o || knob < 0 || knob > 2) return false;
@@ -80,7 +101,7 @@ cudaError_t launch_message(const Batch& b, bool verify, cudaStream_t s) {
 }
 cudaError_t launch_fors(const Batch& b, cudaStream_t s) {
     const SetOps* o = set_ops(b.pset);
-    return o ? o->fors(b, tune_get(b.pset, 0), s) : cudaErrorInvalidValue;
+    return o ? o->fors(b, fors_lanes(b.pset, b.count), s) : cudaErrorInvalidValue;
 }
 cudaError_t launch_fors_pk(const Batch& b, cudaStream_t s) {
     const SetOps* o = set_ops(b.pset);

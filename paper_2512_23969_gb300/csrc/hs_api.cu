@@ -74,6 +74,7 @@ bool set_shape(int pset, SetShape* out) {
     out->d = s.d;
     out->sig = s.sig;
     out->leaves = s.leaves;
+    out->k = s.k;
     return true;
 }
 

@@ -126,7 +126,7 @@ extern const SetOps kOps_K128F, kOps_K192F, kOps_K256F, kOps_K128S, kOps_K192S, 
 constexpr int kNumSets = 13;
 
 // Shape of a parameter set for host code (false for an unknown id).
-struct SetShape { int n, d, sig, leaves; };
+struct SetShape { int n, d, sig, leaves, k; };
 bool set_shape(int pset, SetShape* out);
 const SetOps* set_ops(int pset);
 
@@ -135,6 +135,10 @@ const SetOps* set_ops(int pset);
 int tune_get(int pset, int knob);
 bool tune_set(int pset, int knob, int value);
 bool tree_split(int pset, uint32_t count);
+// Lanes per FORS tree for a batch of 'count' messages: the tuned value, or
+// for a batch too small to give the launch about 1024 threads per SM, the
+// next wider compiled lane groups (fewer leaves per lane, same bytes).
+int fors_lanes(int pset, uint32_t count);
 
 cudaError_t launch_keyprep(const Batch& b, bool from_pk, cudaStream_t s);
 cudaError_t launch_offsets(const Batch& b, cudaStream_t s);

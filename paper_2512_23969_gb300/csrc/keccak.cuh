@@ -249,33 +249,90 @@ struct ByteShake {
             fill = 0;
         }
     }
-    __device__ void words(const uint32_t* w, int nbytes) {   // big-endian words
-        for (int i = 0; i < nbytes; i++) byte(w[i >> 2] >> (24 - 8 * (i & 3)));
+    // Append the low nb (1..4) bytes of the little-endian word w at any byte
+    // offset; the caller keeps fill + nb <= 136 and absorbs a full block.
+    __device__ __forceinline__ void put(uint32_t w, uint32_t nb) {
+        if (nb < 4) w &= (1u << (8 * nb)) - 1u;
+        const uint32_t s = 8 * (fill & 3), j = fill >> 2;
+        blk[j] |= w << s;
+        if (s + 8 * nb > 32) blk[j + 1] |= w >> (32 - s);
+        fill += nb;
     }
-    __device__ void mem(const uint8_t* p, uint64_t len) {
-        uint64_t i = 0;
-        while (i < len && fill != 0) { byte(p[i]); i++; }
-        for (; len - i >= 136; i += 136) {
-            // one block at any alignment: aligned loads, one prmt per word
-            const uintptr_t addr = reinterpret_cast<uintptr_t>(p + i);
-            const uint32_t* a = reinterpret_cast<const uint32_t*>(addr & ~(uintptr_t)3);
-            const uint32_t sh = (uint32_t)(addr & 3);
+    __device__ void flush_if_full() {
+        if (fill == 136) {
+            absorb_block(blk);
+            for (int i = 0; i < kRateWords; i++) blk[i] = 0;
+            fill = 0;
+        }
+    }
+    __device__ void words(const uint32_t* w, int nbytes) {   // big-endian words
+#pragma unroll 1
+        for (int i = 0; i < nbytes; i += 4) {
+            const uint32_t avail = nbytes - i < 4 ? (uint32_t)(nbytes - i) : 4u;
+            const uint32_t room = 136u - fill;
+            const uint32_t le = bswap32(w[i >> 2]);
+            if (avail <= room) {
+                put(le, avail);
+            } else {                                  // the word straddles the block end
+                put(le, room);
+                flush_if_full();
+                put(le >> (8 * room), avail - room);
+            }
+            flush_if_full();
+        }
+    }
+    // r < 136 message bytes at q without crossing the end of the open block,
+    // through aligned word loads issued together (each holds at least one
+    // byte of q[0, r)).
+    __device__ void append(const uint8_t* q, uint32_t r) {
+        if (r == 0) return;
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(q);
+        const uint32_t* a = reinterpret_cast<const uint32_t*>(addr & ~(uintptr_t)3);
+        const uint32_t sh = (uint32_t)(addr & 3);
+        const uint32_t nl = (sh + r + 3) >> 2;
+        uint32_t raw[kRateWords + 1];
+#pragma unroll
+        for (int k = 0; k < kRateWords + 1; k++) raw[k] = ((uint32_t)k < nl) ? __ldg(a + k) : 0u;
+#pragma unroll
+        for (int k = 0; k < kRateWords; k++)
+            if ((uint32_t)(4 * k) < r) put(__funnelshift_r(raw[k], raw[k + 1], 8 * sh), min(4u, r - 4u * k));
+        flush_if_full();
+    }
+    // Whole blocks at any alignment, the next block's loads in flight during
+    // this permutation.
+    __device__ void blocks(const uint8_t* q, uint64_t nb) {
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(q);
+        const uint32_t* a = reinterpret_cast<const uint32_t*>(addr & ~(uintptr_t)3);
+        const uint32_t sh = (uint32_t)(addr & 3);
+        uint32_t raw[kRateWords + 1];
+#pragma unroll
+        for (int k = 0; k < kRateWords; k++) raw[k] = __ldg(a + k);
+        raw[kRateWords] = sh ? __ldg(a + kRateWords) : 0u;
+        for (uint64_t b = 0; b < nb; b++) {
             uint32_t w[kRateWords];
-            if (sh == 0) {
 #pragma unroll
-                for (int k = 0; k < kRateWords; k++) w[k] = __ldg(a + k);
-            } else {
-                uint32_t w0 = __ldg(a);
+            for (int k = 0; k < kRateWords; k++) w[k] = __funnelshift_r(raw[k], raw[k + 1], 8 * sh);
+            if (b + 1 < nb) {
+                const uint32_t* an = a + (b + 1) * kRateWords;
 #pragma unroll
-                for (int k = 0; k < kRateWords; k++) {
-                    const uint32_t w1 = __ldg(a + k + 1);
-                    w[k] = __funnelshift_r(w0, w1, 8 * sh);
-                    w0 = w1;
-                }
+                for (int k = 0; k < kRateWords; k++) raw[k] = __ldg(an + k);
+                raw[kRateWords] = sh ? __ldg(an + kRateWords) : 0u;
             }
             absorb_block(w);
         }
-        while (i < len) { byte(p[i]); i++; }
+    }
+    __device__ void mem(const uint8_t* p, uint64_t len) {
+        uint64_t i = 0;
+        if (fill != 0 && len != 0) {
+            i = (136u - fill < len) ? 136u - fill : len;
+            append(p, (uint32_t)i);
+        }
+        const uint64_t nb = (len - i) / 136;
+        if (nb) {
+            blocks(p + i, nb);
+            i += nb * 136;
+        }
+        if (i < len) append(p + i, (uint32_t)(len - i));
     }
     // Pad and squeeze nbytes (<= 136) as big-endian words into out.
     __device__ void finish(uint32_t* out, int nbytes) {

@@ -19,8 +19,10 @@ namespace hs {
 
 // ------------------------------------------------------------- byte SHA-x
 // Streaming SHA-256 / SHA-512 over bytes and big-endian words.  Only the
-// message stage uses it: key and prefix bytes go through the byte path,
-// message bodies a whole block at a time (block_from).
+// message stage uses it: key words, pads and digests are appended a word at
+// a time from registers; message bytes arrive through aligned word loads,
+// whole blocks with the next block's loads in flight (blocks()), the partial
+// blocks at either end through one batch of loads each (append()).
 template <bool BIG>
 struct ByteSha {
     static constexpr int B = BIG ? 128 : 64;   // block bytes
@@ -62,32 +64,42 @@ struct ByteSha {
         total++;
         if (fill == B) compress();
     }
-    // nbytes of a big-endian word array
-    __device__ void words(const uint32_t* w, int nbytes) {
-        for (int i = 0; i < nbytes; i++) byte(w[i >> 2] >> (24 - 8 * (i & 3)));
-    }
-    // One whole block straight from memory at any alignment: aligned 32-bit
-    // loads, and one prmt per big-endian word picks its 4 bytes across two
-    // loaded words.  Every word loaded holds at least one byte of the block,
-    // so nothing outside the message is touched.
-    __device__ void block_from(const uint8_t* q) {
-        const uintptr_t addr = reinterpret_cast<uintptr_t>(q);
-        const uint32_t* a = reinterpret_cast<const uint32_t*>(addr & ~(uintptr_t)3);
-        const uint32_t sh = (uint32_t)(addr & 3);
-        uint32_t w[BW];
-        if (sh == 0) {
-#pragma unroll
-            for (int k = 0; k < BW; k++) w[k] = bswap32(__ldg(a + k));
+    // Append the top nb (1..4) bytes of the big-endian word w at any byte
+    // offset; the caller keeps fill + nb <= B and compresses a full block.
+    __device__ __forceinline__ void put(uint32_t w, uint32_t nb) {
+        if (nb < 4) w &= 0xFFFFFFFFu << (32 - 8 * nb);
+        const uint32_t s = 8 * (fill & 3), j = fill >> 2;
+        if (s == 0) {
+            blk[j] = w;
         } else {
-            const uint32_t sel = (sh << 12) | ((sh + 1) << 8) | ((sh + 2) << 4) | (sh + 3);
-            uint32_t w0 = __ldg(a);
-#pragma unroll
-            for (int k = 0; k < BW; k++) {
-                const uint32_t w1 = __ldg(a + k + 1);
-                w[k] = __byte_perm(w0, w1, sel);
-                w0 = w1;
-            }
+            blk[j] |= w >> s;
+            if (s + 8 * nb > 32) blk[j + 1] |= w << (32 - s);
         }
+        fill += nb;
+        total += nb;
+    }
+    // nbytes of a big-endian word array (register data: keys, pads, digests)
+    __device__ void words(const uint32_t* w, int nbytes) {
+#pragma unroll 1
+        for (int i = 0; i < nbytes; i += 4) {
+            const uint32_t avail = nbytes - i < 4 ? (uint32_t)(nbytes - i) : 4u;
+            const uint32_t room = (uint32_t)B - fill;
+            if (avail <= room) {
+                put(w[i >> 2], avail);
+            } else {                                  // the word straddles the block end
+                put(w[i >> 2], room);
+                compress();
+                put(w[i >> 2] << (8 * room), avail - room);
+            }
+            if (fill == (uint32_t)B) compress();
+        }
+    }
+    // The message word selector: big-endian word k of bytes q[4k .. 4k+3]
+    // from the aligned little-endian words around it (q & 3 = sh).
+    static __device__ __forceinline__ uint32_t be_sel(uint32_t sh) {
+        return (sh << 12) | ((sh + 1) << 8) | ((sh + 2) << 4) | (sh + 3);
+    }
+    __device__ __forceinline__ void compress_words(const uint32_t w[BW]) {
         if constexpr (BIG) {
             uint64_t s[8], W[16];
 #pragma unroll
@@ -98,16 +110,69 @@ struct ByteSha {
 #pragma unroll
             for (int i = 0; i < 8; i++) { st[2 * i] = (uint32_t)(s[i] >> 32); st[2 * i + 1] = (uint32_t)s[i]; }
         } else {
-            sha256_compress_full(st, w);
+            uint32_t W[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) W[i] = w[i];
+            sha256_compress_full(st, W);
         }
-        total += B;
     }
-    // raw bytes from global memory at any alignment
+    // Append r < B message bytes at q (any alignment) without crossing the
+    // end of the open block.  The bytes arrive through aligned 32-bit loads
+    // issued together, each holding at least one byte of q[0, r), so nothing
+    // outside the message is read.
+    __device__ void append(const uint8_t* q, uint32_t r) {
+        if (r == 0) return;
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(q);
+        const uint32_t* a = reinterpret_cast<const uint32_t*>(addr & ~(uintptr_t)3);
+        const uint32_t sh = (uint32_t)(addr & 3), sel = be_sel(sh);
+        const uint32_t nl = (sh + r + 3) >> 2;
+        uint32_t raw[BW + 1];
+#pragma unroll
+        for (int k = 0; k < BW + 1; k++) raw[k] = ((uint32_t)k < nl) ? __ldg(a + k) : 0u;
+#pragma unroll
+        for (int k = 0; k < BW; k++)
+            if ((uint32_t)(4 * k) < r) put(__byte_perm(raw[k], raw[k + 1], sel), min(4u, r - 4u * k));
+        if (fill == (uint32_t)B) compress();
+    }
+    // nb whole blocks from q at any alignment: aligned 32-bit loads (every
+    // word holds at least one byte of the blocks), one prmt per big-endian
+    // word, and the next block's loads in flight during this compression.
+    __device__ void blocks(const uint8_t* q, uint64_t nb) {
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(q);
+        const uint32_t* a = reinterpret_cast<const uint32_t*>(addr & ~(uintptr_t)3);
+        const uint32_t sh = (uint32_t)(addr & 3), sel = be_sel(sh);
+        uint32_t raw[BW + 1];
+#pragma unroll
+        for (int k = 0; k < BW; k++) raw[k] = __ldg(a + k);
+        raw[BW] = sh ? __ldg(a + BW) : 0u;
+        for (uint64_t b = 0; b < nb; b++) {
+            uint32_t w[BW];
+#pragma unroll
+            for (int k = 0; k < BW; k++) w[k] = __byte_perm(raw[k], raw[k + 1], sel);
+            if (b + 1 < nb) {
+                const uint32_t* an = a + (b + 1) * BW;
+#pragma unroll
+                for (int k = 0; k < BW; k++) raw[k] = __ldg(an + k);
+                raw[BW] = sh ? __ldg(an + BW) : 0u;
+            }
+            compress_words(w);
+        }
+        total += nb * B;
+    }
+    // raw bytes from global memory at any alignment: the rest of the open
+    // block, whole blocks, then the tail
     __device__ void mem(const uint8_t* p, uint64_t len) {
         uint64_t i = 0;
-        while (i < len && fill != 0) { byte(p[i]); i++; }   // finish the open block
-        for (; len - i >= (uint64_t)B; i += B) block_from(p + i);
-        while (i < len) { byte(p[i]); i++; }
+        if (fill != 0 && len != 0) {
+            i = ((uint64_t)B - fill < len) ? (uint64_t)B - fill : len;
+            append(p, (uint32_t)i);
+        }
+        const uint64_t nb = (len - i) / B;
+        if (nb) {
+            blocks(p + i, nb);
+            i += nb * B;
+        }
+        if (i < len) append(p + i, (uint32_t)(len - i));
     }
     // Pad (0x80, zeros, bit length) and return the digest words (8 or 16).
     __device__ void finish(uint32_t* out) {

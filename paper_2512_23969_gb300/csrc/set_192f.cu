@@ -5,7 +5,7 @@
 namespace hs {
 namespace {
 using P = P192f;
-const int kForsLpt[] = {4, 8, 16};
+const int kForsLpt[] = {4, 8, 16, 32};
 const int kTreeMinb[] = {0, 4};
 
 cudaError_t fors_variant(const Batch& b, int lpt, cudaStream_t s) {
@@ -13,6 +13,7 @@ cudaError_t fors_variant(const Batch& b, int lpt, cudaStream_t s) {
     case 4: return SetImpl<P>::fors<4>(b, s);
     case 8: return SetImpl<P>::fors<8>(b, s);
     case 16: return SetImpl<P>::fors<16>(b, s);
+    case 32: return SetImpl<P>::fors<32>(b, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -30,6 +31,6 @@ extern const SetOps kOps_192F = {
     SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk, tree_variant,
     SetImpl<P>::tree_split, SetImpl<P>::tree_dedup, SetImpl<P>::tree_cached, SetImpl<P>::cache_build,
     SetImpl<P>::wots,       SetImpl<P>::verify,     SetImpl<P>::keygen,
-    kForsLpt, 3, 4, kTreeMinb, 2, 4};
+    kForsLpt, 4, 4, kTreeMinb, 2, 4};
 
 }  // namespace hs

@@ -6,7 +6,7 @@
 namespace hs {
 namespace {
 using P = PK128f;
-const int kForsLpt[] = {2, 4, 8};
+const int kForsLpt[] = {2, 4, 8, 16, 32};
 const int kTreeMinb[] = {0};
 
 cudaError_t fors_variant(const Batch& b, int lpt, cudaStream_t s) {
@@ -14,6 +14,8 @@ cudaError_t fors_variant(const Batch& b, int lpt, cudaStream_t s) {
     case 2: return SetImpl<P>::fors<2>(b, s);
     case 4: return SetImpl<P>::fors<4>(b, s);
     case 8: return SetImpl<P>::fors<8>(b, s);
+    case 16: return SetImpl<P>::fors<16>(b, s);
+    case 32: return SetImpl<P>::fors<32>(b, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -27,6 +29,6 @@ extern const SetOps kOps_K128F = {
     SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk, tree_variant,
     SetImpl<P>::tree_split, SetImpl<P>::tree_dedup, SetImpl<P>::tree_cached, SetImpl<P>::cache_build,
     SetImpl<P>::wots,       SetImpl<P>::verify,     SetImpl<P>::keygen,
-    kForsLpt, 3, 2, kTreeMinb, 1, 0};
+    kForsLpt, 5, 2, kTreeMinb, 1, 0};
 
 }  // namespace hs
