@@ -207,8 +207,9 @@ int hs_sign_kernel_count(void);
  * 16384 128f signatures at s = 2) and WOTS+_Sign finishes each chain in fewer
  * than s steps; s = 0 stores nothing and WOTS+_Sign recomputes each chain
  * from its secret.  Signatures are identical for every setting.  Default 2.
- * Returns HS_EINVAL for any other value.  Not thread-safe against
- * concurrent signing calls.
+ * This sets the stride of every parameter set (hs_tune_set with
+ * HS_TUNE_CHECKPOINT then sets one set's own).  Returns HS_EINVAL for any
+ * other value.  Not thread-safe against concurrent signing calls.
  */
 hs_status hs_set_chain_checkpoint(uint32_t stride);
 
@@ -228,12 +229,29 @@ hs_status hs_set_chain_checkpoint(uint32_t stride);
  *                           Merkle levels); 0 = never.  Any value >= 0 is
  *                           accepted; hs_tune_options lists suggestions.
  *                           Extra scratch: len * n bytes per hypertree leaf.
+ *   HS_TUNE_TREE_POLICY     where TREE_Sign's SHA-256 additions run: 7 =
+ *                           round additions on the FMA pipe (IMAD), 15 =
+ *                           the message-schedule sums too (SHA-2 sets)
+ *   HS_TUNE_TREE_CHAINS     WOTS+ chains a TREE_Sign thread runs at once:
+ *                           1, or 2 interleaved (more independent work per
+ *                           thread, more registers; SHA-2 sets)
+ *   HS_TUNE_CHECKPOINT      this set's chain checkpoint stride (0, 1, 2, 4,
+ *                           8; see hs_set_chain_checkpoint, which sets every
+ *                           set's stride at once)
+ * TREE_Sign's per-leaf kernel is compiled for its default combination of
+ * min blocks, policy and chains per thread, and for each alternative value
+ * of one knob with the other two at their defaults (min blocks 0, the
+ * set's default policy, 1 chain); other combinations are refused.
  * hs_tune_options lists the compiled values (returns their number, or -1);
- * hs_tune_set returns HS_EINVAL for a value that is not compiled in;
- * hs_tune_get returns the current value (-1 for bad arguments).  The
- * package's autotuner measures these and stores the best per device.
+ * hs_tune_set returns HS_EINVAL for a value, or a TREE_Sign combination,
+ * that is not compiled in; hs_tune_get returns the current value (-1 for
+ * bad arguments).  The package's autotuner measures these and stores the
+ * best per device.
  */
-typedef enum { HS_TUNE_FORS_LANES = 0, HS_TUNE_TREE_MIN_BLOCKS = 1, HS_TUNE_TREE_SPLIT_BELOW = 2 } hs_tune_knob;
+typedef enum {
+    HS_TUNE_FORS_LANES = 0, HS_TUNE_TREE_MIN_BLOCKS = 1, HS_TUNE_TREE_SPLIT_BELOW = 2,
+    HS_TUNE_TREE_POLICY = 3, HS_TUNE_TREE_CHAINS = 4, HS_TUNE_CHECKPOINT = 5
+} hs_tune_knob;
 int hs_tune_options(hs_params p, int knob, int32_t *values, int max);
 hs_status hs_tune_set(hs_params p, int knob, int32_t value);
 int32_t hs_tune_get(hs_params p, int knob);

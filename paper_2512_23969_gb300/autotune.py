@@ -1,10 +1,15 @@
 """Measured launch-shape autotuner for the signer's kernels.
 
-The library compiles a few launch-shape variants per parameter set (lanes per
-FORS tree; minimum resident blocks of TREE_Sign) and exposes them through
-``hs_tune_options`` / ``hs_tune_set`` (include/hs.h).  This module times each
-variant on a seeded batch with the library's own per-stage CUDA events and
-keeps the fastest, in a JSON cache keyed by the device (name, SM count,
+The library compiles a few variants per parameter set -- lanes per FORS
+tree; TREE_Sign's addition placement (which pipe runs the SHA-256 sums),
+chains per thread (threads per tree: one thread per leaf running one chain
+at a time, or two interleaved) and minimum resident blocks -- and takes the
+batch size below which TREE_Sign runs a thread per chain and the chain
+checkpoint stride at run time; ``hs_tune_options`` / ``hs_tune_set``
+(include/hs.h) expose them.  This module times each value on a seeded batch
+with the library's own per-stage CUDA events (the stages the knob changes:
+TREE_Sign and WOTS+_Sign together for the checkpoint stride) and keeps the
+fastest, in a JSON cache keyed by the device (name, SM count,
 compute capability, driver) so that a later process can apply it without
 re-measuring.  Signatures are identical for every setting, so the choice is
 purely about speed -- the same idea as the paper's offline tuning followed by
@@ -19,8 +24,13 @@ import numpy as np
 
 from . import hs, inputs
 
-KNOBS = {"fors_lanes": 0, "tree_min_blocks": 1, "tree_split_below": 2}
-STAGE_OF_KNOB = {"fors_lanes": "fors", "tree_min_blocks": "tree"}
+KNOBS = {"fors_lanes": 0, "tree_min_blocks": 1, "tree_split_below": 2, "tree_policy": 3, "tree_chains": 4,
+         "checkpoint": 5}
+# the stages each knob changes, timed together; in tuning order (TREE_Sign's
+# policy and chains per thread before its min blocks: the alternatives of
+# each are compiled only with the other two at their defaults)
+STAGE_OF_KNOB = {"fors_lanes": ("fors",), "tree_policy": ("tree",), "tree_chains": ("tree",),
+                 "tree_min_blocks": ("tree",), "checkpoint": ("tree", "wots")}
 DEFAULT_COUNTS = {"128f": 16384, "192f": 8192, "256f": 8192, "toy": 4096, "128s": 512, "192s": 256, "256s": 256,
                   "shake-128f": 4096, "shake-192f": 2048, "shake-256f": 2048, "shake-128s": 256, "shake-192s": 256,
                   "shake-256s": 256}
@@ -58,7 +68,17 @@ def set(params, knob, value):   # noqa: A001 - mirrors hs_tune_set
     L.hs_tune_set.restype = C.c_int
     rc = L.hs_tune_set(hs.PARAMS[params], KNOBS[knob], int(value))
     if rc != 0:
-        raise hs.HSError(rc, L.hs_last_error().decode())
+        raise hs.HSError(rc, hs.last_error())
+
+
+def try_set(params, knob, value):
+    """set(), returning False where the value (or, for TREE_Sign's knobs,
+    the combination with the other two) is not compiled."""
+    try:
+        set(params, knob, value)
+        return True
+    except hs.HSError:
+        return False
 
 
 def device_key():
@@ -82,14 +102,17 @@ def _batch(params, count, seed=4242):
 
 
 def _stage_ms(params, wl, sk, dev, sigs, stage, reps):
+    """Best-of-reps time of a stage, or of the sum of several stages."""
     import torch
+    stages = (stage,) if isinstance(stage, str) else tuple(stage)
     hs.hs_profile_enable(True)
     best = float("inf")
     for _ in range(reps + 1):                       # first call warms up
         hs.hs_sign_batch(params, sk, dev["msgs"], dev["lens"], key_idx=dev["key_idx"], sigs=sigs,
                          num_keys=wl.num_keys)
         torch.cuda.synchronize()
-        best = min(best, hs.hs_profile_read()[stage])
+        prof = hs.hs_profile_read()
+        best = min(best, sum(prof[st] for st in stages))
     hs.hs_profile_enable(False)
     return best
 
@@ -127,10 +150,13 @@ def tune(params_list=("128f", "192f", "256f"), counts=None, reps=3, verbose=True
         ref = None
         result[ps] = {}
         result[ps]["tree_split_below"] = tune_split(ps, reps=reps, verbose=verbose)
+        for knob in ("tree_min_blocks", "tree_chains"):   # 0 min blocks, 1 chain: every policy is compiled there
+            try_set(ps, knob, options(ps, knob)[0])
         for knob, stage in STAGE_OF_KNOB.items():
             timings = {}
             for v in options(ps, knob):
-                set(ps, knob, v)
+                if not try_set(ps, knob, v):            # not compiled with the other knobs' choice
+                    continue
                 timings[v] = _stage_ms(ps, wl, sk, dev, sigs, stage, reps)
                 cur = sigs.clone()
                 if ref is None:
@@ -138,11 +164,11 @@ def tune(params_list=("128f", "192f", "256f"), counts=None, reps=3, verbose=True
                 elif not torch.equal(ref, cur):
                     raise RuntimeError("tuning %s=%d changed the signatures of %s" % (knob, v, ps))
                 if verbose:
-                    print("tune %s %s=%d: %s %.3f ms" % (ps, knob, v, stage, timings[v]), flush=True)
+                    print("tune %s %s=%d: %s %.3f ms" % (ps, knob, v, "+".join(stage), timings[v]), flush=True)
             best = min(timings, key=timings.get)
             set(ps, knob, best)
             result[ps][knob] = {"best": best, "ms": {str(k): round(t, 4) for k, t in timings.items()},
-                                "count": count}
+                                "count": count, "stages": list(stage)}
     return result
 
 
@@ -163,16 +189,20 @@ def apply(path=CACHE):
     with open(path) as f:
         data = json.load(f)
     entry = data.get(device_key(), {})
+    order = ("tree_split_below", "fors_lanes", "tree_min_blocks", "tree_policy", "tree_chains", "checkpoint")
     for ps, knobs in entry.items():
-        for knob, rec in knobs.items():
-            if knob == "tree_split_below" or rec.get("best") in options(ps, knob):
-                set(ps, knob, rec["best"])
+        if ps not in hs.PARAMS:
+            continue
+        for knob in order:                  # min blocks first: the others' alternatives need its default
+            rec = knobs.get(knob)
+            if rec is not None and (knob == "tree_split_below" or rec.get("best") in options(ps, knob)):
+                try_set(ps, knob, rec["best"])
     return entry
 
 
 if __name__ == "__main__":
     import sys
-    sets = sys.argv[1:] or ["128f", "192f", "256f"]
+    sets = sys.argv[1:] or list(DEFAULT_COUNTS)
     res = tune(sets)
     save(res)
     print(json.dumps(res, indent=1))

@@ -25,9 +25,9 @@ const SetOps* set_ops(int pset) {
 }
 
 namespace {
-// -1 = not set: use the table's default.
+// -1 = not set: use the table's default (knob 5: the process-wide stride).
 struct TuneSlots {
-    std::atomic<int> v[kNumSets][3];
+    std::atomic<int> v[kNumSets][kNumKnobs];
     TuneSlots() {
         for (auto& row : v)
             for (auto& x : row) x.store(-1);
@@ -35,16 +35,53 @@ struct TuneSlots {
 };
 TuneSlots g_slots;
 auto& g_tune = g_slots.v;
+std::atomic<int> g_ck_default{2};
 // Default batch size below which TREE_Sign runs chain-parallel, per set.
 constexpr int kSplitDefault[kNumSets] = {8192, 2048, 4096, 0, 64, 64, 64, 8192, 2048, 4096, 64, 64, 64};
+constexpr int kStrides[] = {0, 1, 2, 4, 8};
 }
 
 int tune_get(int pset, int knob) {
     const SetOps* o = set_ops(pset);
-    if (!o || knob < 0 || knob > 2) return -1;
+    if (!o || knob < 0 || knob >= kNumKnobs) return -1;
     const int v = g_tune[pset][knob].load();
     if (v >= 0) return v;
-    return knob == 0 ? o->fors_lpt_default : (knob == 1 ? o->tree_minb_default : kSplitDefault[pset]);
+    switch (knob) {
+    case 0: return o->fors_lpt_default;
+    case 1: return o->tree_minb_default;
+    case 2: return kSplitDefault[pset];
+    case 3: return o->tree_pol_default;
+    case 4: return 1;
+    default: return g_ck_default.load();
+    }
+}
+
+uint32_t chain_checkpoint_stride(int pset) {
+    const int v = tune_get(pset, 5);
+    return v < 0 ? (uint32_t)g_ck_default.load() : (uint32_t)v;
+}
+
+void set_default_checkpoint(uint32_t stride) {
+    g_ck_default.store((int)stride);
+    for (auto& row : g_tune) row[5].store(-1);       // one stride for every set again
+}
+
+int tune_options(int pset, int knob, int32_t* values, int max) {
+    const SetOps* o = set_ops(pset);
+    if (!o || knob < 0 || knob >= kNumKnobs) return -1;
+    int32_t buf[16];
+    int n = 0;
+    switch (knob) {
+    case 0: for (int i = 0; i < o->n_fors_lpt; i++) buf[n++] = o->fors_lpt[i]; break;
+    case 1: for (int i = 0; i < o->n_tree_minb; i++) buf[n++] = o->tree_minb[i]; break;
+    case 2: for (int v : {0, 256, 512, 1024, 2048, 4096, 8192}) buf[n++] = v; break;   // suggestions: any value works
+    case 3: for (int v : {7, 15}) if (o->tree_has(0, v, 1)) buf[n++] = v; break;
+    case 4: for (int v : {1, 2}) if (o->tree_has(0, o->tree_pol_default, v)) buf[n++] = v; break;
+    default: for (int v : kStrides) buf[n++] = v; break;
+    }
+    for (int i = 0; i < n && i < max; i++)
+        if (values) values[i] = buf[i];
+    return n;
 }
 
 bool tree_split(int pset, uint32_t count) {
@@ -75,14 +112,21 @@ int fors_lanes(int pset, uint32_t count) {
 
 bool tune_set(int pset, int knob, int value) {
     const SetOps* o = set_ops(pset);
-    if (!o || knob < 0 || knob > 2) return false;
+    if (!o || knob < 0 || knob >= kNumKnobs) return false;
     if (knob == 2) {                      // any batch-size threshold
         if (value < 0) return false;
         g_tune[pset][2].store(value);
         return true;
     }
-    const int* opts = knob == 0 ? o->fors_lpt : o->tree_minb;
-    const int n = knob == 0 ? o->n_fors_lpt : o->n_tree_minb;
+    if (knob == 1 || knob == 3 || knob == 4) {   // a compiled TREE_Sign combination
+        int t[3] = {tune_get(pset, 1), tune_get(pset, 3), tune_get(pset, 4)};
+        t[knob == 1 ? 0 : (knob == 3 ? 1 : 2)] = value;
+        if (!o->tree_has(t[0], t[1], t[2])) return false;
+        g_tune[pset][knob].store(value);
+        return true;
+    }
+    int32_t opts[16];
+    const int n = tune_options(pset, knob, opts, 16);
     for (int i = 0; i < n; i++)
         if (opts[i] == value) {
             g_tune[pset][knob].store(value);
@@ -119,7 +163,8 @@ cudaError_t launch_tree(const Batch& b, cudaStream_t s) {
         if (e == cudaSuccess) e = o->tree_dedup(b, s);
         if (e != cudaSuccess) return e;
     }
-    return b.split ? o->tree_split(b, s) : o->tree(b, tune_get(b.pset, 1), s);
+    return b.split ? o->tree_split(b, s)
+                   : o->tree(b, tune_get(b.pset, 1), tune_get(b.pset, 3), tune_get(b.pset, 4), s);
 }
 cudaError_t launch_wots(const Batch& b, cudaStream_t s) {
     const SetOps* o = set_ops(b.pset);

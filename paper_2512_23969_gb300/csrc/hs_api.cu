@@ -19,8 +19,6 @@ namespace hs {
 
 static thread_local std::string g_err;
 
-// Chain checkpoint stride used by signing (see hs_set_chain_checkpoint).
-static uint32_t g_ck = 2;
 
 static hs_status fail(hs_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 static hs_status fail(hs_status st, const char* fmt, ...) {
@@ -256,7 +254,6 @@ cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
     return cudaMallocFromPoolAsync(p, bytes, d->pool, s);
 }
 
-uint32_t chain_checkpoint_stride() { return g_ck; }
 
 // 1 if p is host memory (pageable or pinned), 0 if device or managed.
 // Device-side address of page-locked, mapped host memory (nullptr if p is
@@ -329,20 +326,7 @@ HS_API hs_status hs_last_error_copy(char* buf, size_t len) {
 HS_API int hs_sign_kernel_count(void) { return 7; }
 
 HS_API int hs_tune_options(hs_params p, int knob, int32_t* values, int max) {
-    const SetOps* o = set_ops(p);
-    if (!o || knob < 0 || knob > 2) return -1;
-    if (knob == 2) {                 // any threshold is valid; these are the suggested ones
-        static const int kSplit[] = {0, 256, 512, 1024, 2048, 4096, 8192};
-        const int n = 7;
-        for (int i = 0; i < n && i < max; i++)
-            if (values) values[i] = kSplit[i];
-        return n;
-    }
-    const int* opts = knob == 0 ? o->fors_lpt : o->tree_minb;
-    const int n = knob == 0 ? o->n_fors_lpt : o->n_tree_minb;
-    for (int i = 0; i < n && i < max; i++)
-        if (values) values[i] = opts[i];
-    return n;
+    return tune_options(p, knob, values, max);
 }
 
 HS_API hs_status hs_tune_set(hs_params p, int knob, int32_t value) {
@@ -366,7 +350,7 @@ HS_API hs_status hs_set_tree_sharing(int on) {
 HS_API hs_status hs_set_chain_checkpoint(uint32_t stride) {
     if (stride != 0 && stride != 1 && stride != 2 && stride != 4 && stride != 8)
         return fail(HS_EINVAL, "checkpoint stride must be 0, 1, 2, 4 or 8 (got %u)", stride);
-    g_ck = stride;
+    set_default_checkpoint(stride);
     return HS_OK;
 }
 HS_API void hs_profile_enable(int on) { g_prof = on != 0; g_prof_valid = false; }
@@ -504,7 +488,7 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
     b.num_keys = num_keys;
     b.count = count;
     b.status = d->status;
-    b.ck = verify ? 0u : (ks ? ks->ck : g_ck);
+    b.ck = verify ? 0u : (ks ? ks->ck : chain_checkpoint_stride(p));
     b.split = !verify && tree_split(p, count);
     b.verify = verify;
     if (ks && ks->layers) {
@@ -685,7 +669,7 @@ HS_API hs_status hs_keyset_create(hs_params p, const uint8_t* sk, uint32_t num_k
     ks->layers = cache_layers;
     ks->first_layer = (uint32_t)si.d - cache_layers;
     ks->tpk = (uint32_t)tpk;
-    ks->ck = g_ck;
+    ks->ck = chain_checkpoint_stride(p);
     const size_t nw = (size_t)si.n / 4, sk_bytes = (size_t)num_keys * 4 * si.n;
     const size_t node_bytes = (size_t)trees * 2 * si.leaves * nw * 4;
     const size_t chk_bytes = ks->ck ? (size_t)trees * si.leaves * si.len * (16 / ks->ck) * nw * 4 : 0;

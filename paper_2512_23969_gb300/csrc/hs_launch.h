@@ -81,7 +81,7 @@ uint32_t* device_status_word();
 // nullptr; never allocates.
 uint32_t* device_status_word_if_ready();
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
-uint32_t chain_checkpoint_stride();
+uint32_t chain_checkpoint_stride(int pset);
 
 // Tree sharing plan of a batch: fills dedup_layer, cap_log2 and max_uniq
 // (dedup_layer = 0 when sharing is off or not worth it).
@@ -103,7 +103,10 @@ struct SetOps {
     cudaError_t (*message)(const Batch&, bool, cudaStream_t);
     cudaError_t (*fors)(const Batch&, int, cudaStream_t);
     cudaError_t (*fors_pk)(const Batch&, cudaStream_t);
-    cudaError_t (*tree)(const Batch&, int, cudaStream_t);
+    // TREE_Sign per leaf: (min blocks, addition policy, chains per thread);
+    // tree_has says which combinations are compiled
+    cudaError_t (*tree)(const Batch&, int, int, int, cudaStream_t);
+    bool (*tree_has)(int, int, int);
     cudaError_t (*tree_split)(const Batch&, cudaStream_t);
     cudaError_t (*tree_dedup)(const Batch&, cudaStream_t);
     cudaError_t (*tree_cached)(const Batch&, cudaStream_t);
@@ -118,6 +121,7 @@ struct SetOps {
     const int* tree_minb;
     int n_tree_minb;
     int tree_minb_default;
+    int tree_pol_default;
 };
 extern const SetOps kOps_128F, kOps_192F, kOps_256F, kOps_Toy, kOps_128S, kOps_192S, kOps_256S;
 extern const SetOps kOps_K128F, kOps_K192F, kOps_K256F, kOps_K128S, kOps_K192S, kOps_K256S;
@@ -131,9 +135,16 @@ bool set_shape(int pset, SetShape* out);
 const SetOps* set_ops(int pset);
 
 // Tuned launch shape per set (knob 0 = FORS lanes per tree, 1 = TREE min
-// blocks, 2 = batch size below which TREE_Sign runs chain-parallel).
+// blocks, 2 = batch size below which TREE_Sign runs chain-parallel, 3 =
+// TREE_Sign addition policy, 4 = TREE_Sign chains per thread, 5 = chain
+// checkpoint stride).
+constexpr int kNumKnobs = 6;
 int tune_get(int pset, int knob);
 bool tune_set(int pset, int knob, int value);
+// Compiled values of a knob (returns how many; -1 for bad arguments).
+int tune_options(int pset, int knob, int32_t* values, int max);
+// Process-wide checkpoint stride: the value of every set whose knob 5 is unset.
+void set_default_checkpoint(uint32_t stride);
 bool tree_split(int pset, uint32_t count);
 // Lanes per FORS tree for a batch of 'count' messages: the tuned value, or
 // for a batch too small to give the launch about 1024 threads per SM, the

@@ -143,7 +143,7 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
         b.lens = jb.lens;
         b.count = jb.count;
         b.sigs = jb.sigs;
-        b.ck = chain_checkpoint_stride();
+        b.ck = chain_checkpoint_stride(b.pset);
         b.split = tree_split(b.pset, b.count);
         plan_dedup(b);
         bs.push_back(b);

@@ -23,7 +23,7 @@ namespace hs {
 constexpr int kMergeThreads = 256;
 
 // Leaves of layers 0 .. layers-1 of every message: one thread per leaf.
-template <class P, int POL, int MINB>
+template <class P, int POL, int MINB, int ILP = 1>
 __global__ void __launch_bounds__(128, MINB) bleaf_kernel(const KeyBlock* __restrict__ keys,
                                                           const MsgInfo* __restrict__ infos, uint32_t count,
                                                           uint32_t* __restrict__ leafv, uint32_t* __restrict__ chk,
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(128, MINB) bleaf_kernel(const KeyBlock* __rest
     uint32_t* mychk = (ck != 0 && l == sl)
                           ? chk + ((size_t)m * P::D + j) * (size_t)P::LEN * (16u / ck) * NW : nullptr;
     uint32_t node[NW];
-    wots_leaf<P, POL>(ms256, msT, skseed, j, tree, l, node, mychk, ck, pp);
+    wots_leaf<P, POL, ILP>(ms256, msT, skseed, j, tree, l, node, mychk, ck, pp);
     uint32_t* out = leafv + (((size_t)m * P::D + j) * LV + l) * NW;
 #pragma unroll
     for (int w = 0; w < NW; w++) out[w] = node[w];

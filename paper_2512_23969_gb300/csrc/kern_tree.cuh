@@ -31,11 +31,15 @@ namespace hs {
 // ck-th chain position (0, ck, 2ck, ...) of every chain is stored there,
 // [chain][position / ck][NW words], so that WOTS+_Sign only has to finish
 // at most ck - 1 steps of each chain instead of recomputing it.
-template <class P, int POL>
+// ILP = 2 (SHA-2 only): the thread runs its chains two at a time, the two
+// chains' compressions interleaved (more independent work per thread, more
+// registers); the last chain of an odd len runs alone.  Same bytes.
+template <class P, int POL, int ILP = 1>
 __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t* msT, const uint32_t* skseed,
                                           uint32_t layer, uint64_t tree, uint32_t kp, uint32_t* out,
                                           uint32_t* chk, uint32_t ck, const Pipes<POL>& pp) {
     constexpr int NW = P::NW;
+    static_assert(ILP == 1 || (ILP == 2 && !P::SHAKE), "two chains per thread: SHA-2 sets only");
     // SHA-2: chain ends go to a per-thread array (local memory) and T_len
     // runs over it afterwards, so no hash state is live across the chain
     // loop; SHAKE streams them into its own buffer.
@@ -45,8 +49,45 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
     const Adrs aprf = make_adrs(layer, tree, T_WOTS_PRF, kp, 0, 0);
     const Adrs ahash = make_adrs(layer, tree, T_WOTS_HASH, kp, 0, 0);
     const uint32_t per_chain = ck ? 16u / ck : 0u;
+    auto keep = [&](uint32_t i, uint32_t s, const uint32_t* x) {
+        if (chk != nullptr && (s % ck) == 0) {
+            uint32_t* d = chk + ((size_t)i * per_chain + s / ck) * NW;
+#pragma unroll
+            for (int w = 0; w < NW; w++) d[w] = x[w];
+        }
+    };
+    uint32_t i0 = 0;
+    if constexpr (ILP == 2) {
 #pragma unroll 1
-    for (uint32_t i = 0; i < (uint32_t)P::LEN; i++) {
+        for (; i0 + 1 < (uint32_t)P::LEN; i0 += 2) {
+            uint32_t x0[NW], x1[NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) x0[w] = x1[w] = skseed[w];
+            ChainCtx c0, c1;
+#pragma unroll 1
+            for (uint32_t s = 0; s < 16; s++) {
+                if (s <= 1) {
+                    Adrs a = (s == 0) ? aprf : ahash;
+                    a.w4 = i0 << 16;
+                    chain_ctx<POL>(ms256, a, c0, pp);
+                    a.w4 = (i0 + 1) << 16;
+                    chain_ctx<POL>(ms256, a, c1, pp);
+                }
+                const uint32_t half = s == 0 ? 0u : s - 1u;
+                chain_step<POL, NW>(c0, ms256, half, x0, x0, pp);
+                chain_step<POL, NW>(c1, ms256, half, x1, x1, pp);
+                keep(i0, s, x0);
+                keep(i0 + 1, s, x1);
+            }
+#pragma unroll
+            for (int w = 0; w < NW; w++) {
+                ends[i0 * NW + w] = x0[w];
+                ends[(i0 + 1) * NW + w] = x1[w];
+            }
+        }
+    }
+#pragma unroll 1
+    for (uint32_t i = i0; i < (uint32_t)P::LEN; i++) {
         uint32_t x[NW];
 #pragma unroll
         for (int w = 0; w < NW; w++) x[w] = skseed[w];
@@ -68,11 +109,7 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
                 }
                 chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, x, x, pp);
             }
-            if (chk != nullptr && (s % ck) == 0) {
-                uint32_t* d = chk + ((size_t)i * per_chain + s / ck) * NW;
-#pragma unroll
-                for (int w = 0; w < NW; w++) d[w] = x[w];
-            }
+            keep(i, s, x);
         }
         if constexpr (P::SHAKE) {
             ts.template push_n<NW>(x);
@@ -120,7 +157,7 @@ __device__ __forceinline__ void merkle_finish(const uint32_t* ms256, const uint3
 }
 
 
-template <class P, int POL, int MINB>
+template <class P, int POL, int MINB, int ILP = 1>
 __global__ void __launch_bounds__(128, MINB) tree_kernel(const KeyBlock* __restrict__ keys,
                                                    const MsgInfo* __restrict__ infos, uint32_t count,
                                                    uint8_t* __restrict__ sigs, uint32_t* __restrict__ roots,
@@ -155,7 +192,7 @@ __global__ void __launch_bounds__(128, MINB) tree_kernel(const KeyBlock* __restr
     uint32_t* mychk = (ck != 0 && l == sl)
                           ? chk + ((size_t)m * P::D + j) * (size_t)P::LEN * (16u / ck) * NW : nullptr;
     uint32_t node[NW];
-    wots_leaf<P, POL>(ms256, msT, skseed, j, tree, l, node, mychk, ck, pp);
+    wots_leaf<P, POL, ILP>(ms256, msT, skseed, j, tree, l, node, mychk, ck, pp);
 
     merkle_finish<P>(ms256, msT, gmask, m, j, l, sl, tree, node, sigs, roots);
 }

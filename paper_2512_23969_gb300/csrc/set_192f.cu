@@ -17,20 +17,13 @@ cudaError_t fors_variant(const Batch& b, int lpt, cudaStream_t s) {
     }
     return cudaErrorInvalidValue;
 }
-
-cudaError_t tree_variant(const Batch& b, int minb, cudaStream_t s) {
-    switch (minb) {
-    case 0: return SetImpl<P>::tree<1>(b, s);
-    case 4: return SetImpl<P>::tree<4>(b, s);
-    }
-    return cudaErrorInvalidValue;
-}
 }  // namespace
 
 extern const SetOps kOps_192F = {
-    SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk, tree_variant,
+    SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk,
+    TreeVariants<P, 4>::run, TreeVariants<P, 4>::has,
     SetImpl<P>::tree_split, SetImpl<P>::tree_dedup, SetImpl<P>::tree_cached, SetImpl<P>::cache_build,
     SetImpl<P>::wots,       SetImpl<P>::verify,     SetImpl<P>::keygen,
-    kForsLpt, 4, 4, kTreeMinb, 2, 4};
+    kForsLpt, 4, 4, kTreeMinb, 2, 0, tree_pol<P>()};
 
 }  // namespace hs

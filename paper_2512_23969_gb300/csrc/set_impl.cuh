@@ -49,7 +49,7 @@ struct SetImpl {
         fors_pk_kernel<P><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.fors_roots, b.pk_fors);
         return cudaGetLastError();
     }
-    template <int MINB>
+    template <int MINB, int POL = tree_pol<P>(), int ILP = 1>
     static cudaError_t tree(const Batch& b, cudaStream_t s) {
         const uint32_t L = own_layers(b);
         const uint64_t threads = (uint64_t)b.count * L * P::LEAVES;
@@ -57,12 +57,12 @@ struct SetImpl {
         const uint32_t G = (uint32_t)((threads + T - 1) / T);
         if (threads == 0) return cudaSuccess;
         if constexpr (kWide) {
-            bleaf_kernel<P, tree_pol<P>(), MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.leafv, b.chk, b.ck, L, 1u);
+            bleaf_kernel<P, POL, MINB, ILP><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.leafv, b.chk, b.ck, L, 1u);
             cudaError_t e = cudaGetLastError();
             return e == cudaSuccess ? merge(b, s) : e;
         } else {
-            tree_kernel<P, tree_pol<P>(), MINB><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck,
-                                                             L, 1u);
+            tree_kernel<P, POL, MINB, ILP><<<G, T, 0, s>>>(b.keys, b.infos, b.count, b.sigs, b.roots, b.chk, b.ck,
+                                                        L, 1u);
             return cudaGetLastError();
         }
     }
@@ -225,6 +225,33 @@ struct SetImpl {
             keygen_kernel<P><<<G, T, 0, s>>>(seeds, count, pk, sk, 1u);
             return cudaGetLastError();
         }
+    }
+};
+
+// The compiled variants of TREE_Sign's per-leaf kernel for one set, as
+// (min blocks per SM, addition policy, chains per thread): the default
+// (0, tree_pol<P>(), 1); the other addition policy and two interleaved
+// chains per thread (SHA-2 sets other than toy); and MB_ALT min blocks
+// (0 = none) -- each alternative with the other two at their defaults.
+template <class P, int MB_ALT>
+struct TreeVariants {
+    static constexpr int PD = tree_pol<P>();
+    static constexpr bool kAlts = !P::SHAKE && P::LEAVES >= 8;   // not SHAKE, not the toy set
+    static constexpr int PA = PD == 7 ? 15 : 7;
+    static bool has(int minb, int pol, int ilp) {
+        if (minb == 0 && pol == PD && ilp == 1) return true;
+        if (MB_ALT != 0 && minb == MB_ALT && pol == PD && ilp == 1) return true;
+        return kAlts && minb == 0 && ((pol == PA && ilp == 1) || (pol == PD && ilp == 2));
+    }
+    static cudaError_t run(const Batch& b, int minb, int pol, int ilp, cudaStream_t s) {
+        if (minb == 0 && pol == PD && ilp == 1) return SetImpl<P>::template tree<1, PD, 1>(b, s);
+        if constexpr (MB_ALT != 0)
+            if (minb == MB_ALT && pol == PD && ilp == 1) return SetImpl<P>::template tree<MB_ALT, PD, 1>(b, s);
+        if constexpr (kAlts) {
+            if (minb == 0 && pol == PA && ilp == 1) return SetImpl<P>::template tree<1, PA, 1>(b, s);
+            if (minb == 0 && pol == PD && ilp == 2) return SetImpl<P>::template tree<1, PD, 2>(b, s);
+        }
+        return cudaErrorInvalidValue;
     }
 };
 

@@ -18,16 +18,13 @@ cudaError_t fors_variant(const Batch& b, int lpt, cudaStream_t s) {
     }
     return cudaErrorInvalidValue;
 }
-
-cudaError_t tree_variant(const Batch& b, int minb, cudaStream_t s) {
-    return minb == 0 ? SetImpl<P>::tree<1>(b, s) : cudaErrorInvalidValue;
-}
 }  // namespace
 
 extern const SetOps kOps_K192F = {
-    SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk, tree_variant,
+    SetImpl<P>::keyprep, SetImpl<P>::message, fors_variant, SetImpl<P>::fors_pk,
+    TreeVariants<P, 0>::run, TreeVariants<P, 0>::has,
     SetImpl<P>::tree_split, SetImpl<P>::tree_dedup, SetImpl<P>::tree_cached, SetImpl<P>::cache_build,
     SetImpl<P>::wots,       SetImpl<P>::verify,     SetImpl<P>::keygen,
-    kForsLpt, 4, 4, kTreeMinb, 1, 0};
+    kForsLpt, 4, 4, kTreeMinb, 1, 0, tree_pol<P>()};
 
 }  // namespace hs

@@ -1,7 +1,8 @@
 """Every compiled launch-shape variant gives the same signatures.
 
-The tuning knobs (lanes per FORS tree, TREE_Sign occupancy variant, WOTS+
-chain checkpoint stride) may only change speed.  For each parameter set,
+The tuning knobs (lanes per FORS tree; TREE_Sign's form, addition policy,
+chains per thread and occupancy variant; the WOTS+ chain checkpoint stride,
+for all sets and per set) may only change speed.  For each parameter set,
 each variant signs the same seeded batch; all outputs must be byte-equal to
 the default's, and the default's must equal the oracle on sampled messages.
 """
@@ -13,7 +14,7 @@ from paper_2512_23969_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("ps", ["toy", "128f", "192f", "256f"])
+@pytest.mark.parametrize("ps", ["toy", "128f", "192f", "256f", "128s"])
 def test_variants_identical(hs, O, ps):
     import torch
     from paper_2512_23969_gb300 import autotune
@@ -34,11 +35,23 @@ def test_variants_identical(hs, O, ps):
     for i in (0, 7, 23):
         assert ref[i].numpy().tobytes() == O.sign(ps, osk[wl.key_idx[i]], wl.message(i))
     try:
-        for knob in autotune.KNOBS:
-            for v in autotune.options(ps, knob):
-                autotune.set(ps, knob, v)
-                assert torch.equal(sign(), ref), (knob, v)
-            autotune.set(ps, knob, saved[knob])
+        # every knob's compiled values, with TREE_Sign in both of its forms
+        # (a thread per chain at this batch size by default; per leaf when
+        # the split threshold is 0), each alternative from the defaults
+        for split in (saved["tree_split_below"], 0):
+            autotune.set(ps, "tree_split_below", split)
+            for knob in autotune.KNOBS:
+                if knob == "tree_split_below":
+                    continue
+                for v in autotune.options(ps, knob):
+                    autotune.set(ps, knob, v)
+                    assert torch.equal(sign(), ref), (split, knob, v)
+                autotune.set(ps, knob, saved[knob])
+        autotune.set(ps, "tree_split_below", saved["tree_split_below"])
+        for v in autotune.options(ps, "tree_split_below"):
+            autotune.set(ps, "tree_split_below", v)
+            assert torch.equal(sign(), ref), ("tree_split_below", v)
+        autotune.set(ps, "tree_split_below", saved["tree_split_below"])
         for ck in (0, 1, 2, 4, 8):
             hs.hs_set_chain_checkpoint(ck)
             assert torch.equal(sign(), ref), ("checkpoint", ck)

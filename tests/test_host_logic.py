@@ -157,3 +157,45 @@ def test_server_binding_checks_without_a_server():
         srv.replay(z8, z32, z32, np.zeros(19, np.uint8), lens, z64)              # pool lengths add to 20
     with pytest.raises(ValueError):
         srv.submit("128f", 0, b"m", out=np.zeros(hs.sig_bytes("128f") - 1, np.uint8))
+
+
+def test_tree_knob_combinations_follow_the_compiled_variants():
+    """TREE_Sign's per-leaf kernel is compiled for its default (min blocks
+    0, the set's addition policy, one chain per thread) and for each
+    alternative of one knob with the other two at their defaults; the
+    library refuses other combinations, and the SHAKE sets have no policy
+    or chains-per-thread alternatives.  No CUDA call is made."""
+    assert autotune.options("128f", "tree_policy") == [7, 15]
+    assert autotune.options("192f", "tree_policy") == [7, 15]
+    assert autotune.options("128f", "tree_chains") == [1, 2]
+    assert autotune.options("shake-128f", "tree_policy") == [7]
+    assert autotune.options("shake-128f", "tree_chains") == [1]
+    assert autotune.options("toy", "tree_chains") == [1]
+    assert autotune.options("128f", "checkpoint") == [0, 1, 2, 4, 8]
+    assert autotune.get("128f", "tree_policy") == 7 and autotune.get("256f", "tree_policy") == 15
+    saved = {k: autotune.get("128f", k) for k in autotune.KNOBS}
+    try:
+        autotune.set("128f", "tree_min_blocks", 6)
+        assert not autotune.try_set("128f", "tree_policy", 15)     # (6, 15, 1) is not compiled
+        assert not autotune.try_set("128f", "tree_chains", 2)      # (6, 7, 2) is not compiled
+        autotune.set("128f", "tree_min_blocks", 0)
+        autotune.set("128f", "tree_chains", 2)
+        assert not autotune.try_set("128f", "tree_policy", 15)     # (0, 15, 2) is not compiled
+        assert not autotune.try_set("128f", "tree_min_blocks", 6)
+    finally:
+        autotune.set("128f", "tree_chains", saved["tree_chains"])
+        autotune.set("128f", "tree_min_blocks", saved["tree_min_blocks"])
+        autotune.set("128f", "tree_policy", saved["tree_policy"])
+
+
+def test_checkpoint_stride_per_set_and_process_wide():
+    """hs_set_chain_checkpoint sets every set's stride and drops per-set
+    choices; HS_TUNE_CHECKPOINT sets one set's.  No CUDA call is made."""
+    try:
+        autotune.set("192f", "checkpoint", 4)
+        assert autotune.get("192f", "checkpoint") == 4 and autotune.get("128f", "checkpoint") == 2
+        hs.hs_set_chain_checkpoint(1)
+        assert autotune.get("192f", "checkpoint") == 1 and autotune.get("128f", "checkpoint") == 1
+        assert not autotune.try_set("128f", "checkpoint", 3)
+    finally:
+        hs.hs_set_chain_checkpoint(2)
