@@ -261,7 +261,9 @@ int32_t hs_tune_get(hs_params p, int knob);
  * message) are submitted at any time; a scheduler thread keeps up to
  * max_inflight batches on the GPU, each on its own stream, and launches the
  * next batch -- the oldest pending requests of one parameter set, at most
- * max_batch of them -- as soon as a slot and memory are free, so newly
+ * max_batch of them and at most max(256, all pending / max_inflight), so a
+ * backlog near capacity is spread over the slots rather than formed into
+ * one long batch -- as soon as a slot and memory are free, so newly
  * arrived requests overlap with running ones.  Device memory for messages,
  * signatures and scratch comes from one arena of mem_budget_bytes reserved
  * at creation (admission control: a batch that does not fit waits); host

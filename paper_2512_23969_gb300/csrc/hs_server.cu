@@ -202,6 +202,8 @@ void retire(ServerImpl& sv) {
     }
 }
 
+constexpr size_t kMinShare = 256;
+
 // Form and launch one batch on a free slot (lock held).  Returns false if
 // nothing could be launched (no pending request, or no memory for even one).
 bool admit(ServerImpl& sv, Slot& slot) {
@@ -215,9 +217,17 @@ bool admit(ServerImpl& sv, Slot& slot) {
     if (best < 0) return false;
     const int p = best;
     const hs_keyset* ks = sv.ks[p];
+    // Batch size: up to max_batch, but no more than the backlog's share of
+    // one slot (pending / max_inflight, at least kMinShare): a saturating
+    // backlog still forms full batches, while a transient backlog near
+    // capacity is spread over the slots instead of becoming one long batch
+    // that every request in it waits for.
+    size_t pending_all = 0;
+    for (int q = 0; q < kNumSets; q++) pending_all += sv.pending[q].size();
+    const size_t share = std::max<size_t>(kMinShare, pending_all / sv.cfg.max_inflight);
     // take requests while the cumulative need fits what the arenas could give
     size_t count = 0, msg_bytes = 0;
-    const size_t limit = std::min<size_t>(sv.cfg.max_batch, sv.pending[p].size());
+    const size_t limit = std::min<size_t>(std::min<size_t>(sv.cfg.max_batch, share), sv.pending[p].size());
     const size_t dev_free = sv.dev_arena.cap() - sv.dev_arena.used();
     const size_t host_free = sv.host_arena.cap() - sv.host_arena.used();
     while (count < limit) {

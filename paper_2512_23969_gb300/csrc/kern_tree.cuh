@@ -26,6 +26,28 @@
 
 namespace hs {
 
+// Store n bytes of a chain checkpoint with the evict-first (streaming) hint:
+// WOTS+_Sign reads them in a later kernel, long after they have left L2,
+// and without the hint this 1.6 GB stream (16384 signatures at 128f)
+// pushes the threads' chain-end arrays (local memory, reused by the next
+// thread on the same SM slot) out of L2 and so out to DRAM.  'd' is
+// 4 * NW-byte aligned (checkpoints are NW-word records from a 256-byte
+// aligned base).
+template <int NW>
+__device__ __forceinline__ void store_checkpoint(uint32_t* d, const uint32_t* x) {
+    if constexpr (NW % 4 == 0) {
+#pragma unroll
+        for (int w = 0; w < NW; w += 4)
+            __stcs(reinterpret_cast<uint4*>(d + w), make_uint4(x[w], x[w + 1], x[w + 2], x[w + 3]));
+    } else if constexpr (NW % 2 == 0) {
+#pragma unroll
+        for (int w = 0; w < NW; w += 2) __stcs(reinterpret_cast<uint2*>(d + w), make_uint2(x[w], x[w + 1]));
+    } else {
+#pragma unroll
+        for (int w = 0; w < NW; w++) __stcs(d + w, x[w]);
+    }
+}
+
 // Hypertree leaf = WOTS+ public key of keypair kp in tree (layer, tree).
 // If chk is not null (the thread owns the signing leaf of its tree), every
 // ck-th chain position (0, ck, 2ck, ...) of every chain is stored there,
@@ -48,12 +70,13 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
     if constexpr (P::SHAKE) ts.init(msT, make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0));
     const Adrs aprf = make_adrs(layer, tree, T_WOTS_PRF, kp, 0, 0);
     const Adrs ahash = make_adrs(layer, tree, T_WOTS_HASH, kp, 0, 0);
-    const uint32_t per_chain = ck ? 16u / ck : 0u;
+    // ck is a power of two (1, 2, 4 or 8 when chk is set): test and index
+    // positions with a mask and a shift, not a run-time division per step
+    const uint32_t per_chain = ck ? 16u >> (__ffs(ck) - 1) : 0u;
+    const uint32_t ck_mask = ck ? ck - 1u : 0u, ck_shift = ck ? (uint32_t)(__ffs(ck) - 1) : 0u;
     auto keep = [&](uint32_t i, uint32_t s, const uint32_t* x) {
-        if (chk != nullptr && (s % ck) == 0) {
-            uint32_t* d = chk + ((size_t)i * per_chain + s / ck) * NW;
-#pragma unroll
-            for (int w = 0; w < NW; w++) d[w] = x[w];
+        if (chk != nullptr && (s & ck_mask) == 0) {
+            store_checkpoint<NW>(chk + ((size_t)i * per_chain + (s >> ck_shift)) * NW, x);
         }
     };
     uint32_t i0 = 0;
@@ -229,7 +252,8 @@ __global__ void __launch_bounds__(128) chains_kernel(const KeyBlock* __restrict_
     const uint32_t sl = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
     const Pipes<POL> pp(one);
     uint32_t* mychk = nullptr;
-    const uint32_t per_chain = ck ? 16u / ck : 0u;
+    const uint32_t per_chain = ck ? 16u >> (__ffs(ck) - 1) : 0u;      // ck: a power of two
+    const uint32_t ck_mask = ck ? ck - 1u : 0u, ck_shift = ck ? (uint32_t)(__ffs(ck) - 1) : 0u;
     if (ck != 0 && l == sl) mychk = chk + (((size_t)m * P::D + j) * (size_t)LEN + i) * per_chain * NW;
     ChainCtx cx;
 #pragma unroll 1
@@ -244,10 +268,7 @@ __global__ void __launch_bounds__(128) chains_kernel(const KeyBlock* __restrict_
             }
             chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, x, x, pp);
         }
-        if (mychk != nullptr && (s % ck) == 0) {
-#pragma unroll
-            for (int w = 0; w < NW; w++) mychk[(s / ck) * NW + w] = x[w];
-        }
+        if (mychk != nullptr && (s & ck_mask) == 0) store_checkpoint<NW>(mychk + (s >> ck_shift) * NW, x);
     }
     uint32_t* e = ends + gid * NW;
 #pragma unroll
