@@ -16,6 +16,8 @@ PARAM_IDS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3, "128s": 4, "192s": 5, "2
 # the SHAKE instantiation of each set: id + 32 ("shake-128f", "slh-shake-128f", ...)
 PARAM_IDS.update({"shake-" + k: v + 32 for k, v in list(PARAM_IDS.items()) if not k.startswith("slh-")})
 PARAM_IDS.update({"slh-shake-" + k[4:]: v + 32 for k, v in list(PARAM_IDS.items()) if k.startswith("slh-")})
+# the robust SHA2 instantiation of each round-3.1 set ("robust-128f", ...): id + 64
+PARAM_IDS.update({"robust-" + k: v + 64 for k, v in list(PARAM_IDS.items()) if v < 16})
 
 _lib = None
 

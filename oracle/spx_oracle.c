@@ -32,6 +32,10 @@
  * FIPS 202 Sec. 3: round constants come from its LFSR (Algorithm 5) and the
  * rotation offsets from its (x, y) walk (Algorithm 2), not from tables.
  *
+ * Robust instantiation (parameter id + 64; a variant): SPHINCS+ round 3.1's
+ * robust SHA2 tweakable hashes, which mask the inputs of F, H and T_l with
+ * MGF1 output seeded by PK.seed and the address (thash_masked).
+ *
  * FIPS 205 mode (parameter id + 16): SLH-DSA's two departures from the
  * round-3.1 scheme, stated in FIPS 205 -- the FORS indices are the base-2^a
  * digits of md read most significant bit first (its base_2b), and the pure
@@ -69,19 +73,23 @@ typedef struct {
     int tree_bits, leaf_bits;
     int fips;   /* 1: FORS indices in FIPS 205 order (MSB first)        */
     int shake;  /* 1: SHAKE256 tweakable hashes instead of SHA-2         */
+    int robust; /* 1: robust SHA2 tweakable hashes (inputs masked)       */
     size_t fors_bytes, sig_bytes;
 } spx_params;
 
 /* ids: 0 = 128f, 1 = 192f, 2 = 256f, 3 = toy (n=16,h=4,d=2,h'=2,a=3,k=4),
  * 4 = 128s, 5 = 192s, 6 = 256s (the scheme's small-signature sets, a
  * variant the paper does not use); + 16 = the same set in FIPS 205 mode,
- * + 32 = its SHAKE instantiation */
+ * + 32 = its SHAKE instantiation, + 64 = its robust SHA2 instantiation
+ * (round 3.1 only: not with FIPS 205 mode or SHAKE) */
 static int params_init(int id, spx_params *p)
 {
     memset(p, 0, sizeof(*p));
-    if (id < 0 || id > 63) return -1;
+    if (id < 0 || id > 127) return -1;
     p->fips = (id >> 4) & 1;
     p->shake = (id >> 5) & 1;
+    p->robust = (id >> 6) & 1;
+    if (p->robust && (p->fips || p->shake)) return -1;
     switch (id & 15) {
     case 0: p->n = 16; p->h = 66; p->d = 22; p->a = 6; p->k = 33; break;
     case 1: p->n = 24; p->h = 66; p->d = 22; p->a = 8; p->k = 33; break;
@@ -513,9 +521,34 @@ static void thash(const spx_ctx *c, int big, const adrs_t *A,
     memcpy(out, dig, c->p.n);
 }
 
+/* READING (robust instantiation, a variant; the paper signs with the
+ * simple one): SPHINCS+ round 3.1's robust SHA2 tweakable hashes F, H and
+ * T_l hash M xor MGF1-SHA-x(PK.seed || ADRSc, |M|) in place of M, where
+ * SHA-x is the hash that tweakable hash itself uses (SHA-256 for F; SHA-512
+ * for H and T_l at n = 24 / 32) and the mask seed is PK.seed unpadded,
+ * followed by the 22-byte compressed address.  PRF, PRF_msg and H_msg are
+ * the same as in the simple instantiation. */
+static void thash_masked(const spx_ctx *c, int big, const adrs_t *A,
+                         const uint8_t *in, size_t inlen, uint8_t *out)
+{
+    uint8_t *x, seed[32 + 22];
+    size_t i, n = (size_t)c->p.n;
+    if (!c->p.robust) {
+        thash(c, big, A, in, inlen, out);
+        return;
+    }
+    x = (uint8_t *)malloc(inlen);
+    memcpy(seed, c->pk_seed, n);
+    adrs_compress(A, seed + n);
+    mgf1_shax(big, seed, n + 22, x, inlen);     /* the mask */
+    for (i = 0; i < inlen; i++) x[i] ^= in[i];
+    thash(c, big, A, x, inlen, out);
+    free(x);
+}
+
 /* F: chain step / FORS leaf; always SHA-256, one n-byte block. */
 static void hash_F(const spx_ctx *c, const adrs_t *A, const uint8_t *in, uint8_t *out)
-{ g_calls_f++; thash(c, 0, A, in, c->p.n, out); }
+{ g_calls_f++; thash_masked(c, 0, A, in, c->p.n, out); }
 
 /* H: Merkle parent of two n-byte children; SHA-512 when n > 16. */
 static void hash_H(const spx_ctx *c, const adrs_t *A, const uint8_t *l, const uint8_t *r, uint8_t *out)
@@ -524,12 +557,12 @@ static void hash_H(const spx_ctx *c, const adrs_t *A, const uint8_t *l, const ui
     g_calls_h++;
     memcpy(buf, l, c->p.n);
     memcpy(buf + c->p.n, r, c->p.n);
-    thash(c, c->p.big, A, buf, 2 * (size_t)c->p.n, out);
+    thash_masked(c, c->p.big, A, buf, 2 * (size_t)c->p.n, out);
 }
 
 /* T_l: compress l n-byte values (WOTS public key, FORS roots). */
 static void hash_T(const spx_ctx *c, const adrs_t *A, const uint8_t *in, int l, uint8_t *out)
-{ g_calls_t++; thash(c, c->p.big, A, in, (size_t)l * c->p.n, out); }
+{ g_calls_t++; thash_masked(c, c->p.big, A, in, (size_t)l * c->p.n, out); }
 
 /* PRF: secret value for an address; SHA-256 over SK.seed. */
 static void prf_addr(const spx_ctx *c, const adrs_t *A, uint8_t *out)

@@ -39,7 +39,8 @@ MUTANTS = [
     ("T_len drops the last chain", "hash_T(c, &A, ends, c->p.len, pk);", "hash_T(c, &A, ends, c->p.len - 1, pk);", False),
     ("blockpad always 64 bytes", "size_t B = big ? 128 : 64;\n    if (c->p.shake) {",
      "size_t B = 64;\n    if (c->p.shake) {", False),
-    ("H always SHA-256", "thash(c, c->p.big, A, buf, 2 * (size_t)c->p.n, out);", "thash(c, 0, A, buf, 2 * (size_t)c->p.n, out);", False),
+    ("H always SHA-256", "thash_masked(c, c->p.big, A, buf, 2 * (size_t)c->p.n, out);",
+     "thash_masked(c, 0, A, buf, 2 * (size_t)c->p.n, out);", False),
     ("PRF uses SHA-512 when big", "g_calls_prf++; thash(c, 0, A,", "g_calls_prf++; thash(c, c->p.big, A,", False),
     ("checksum not shifted", "csum <<= (8 - (p->len2 * 4) % 8) % 8;", "", False),
     ("base_w nibble order", "digits[i] = (i % 2 == 0) ? (x[i / 2] >> 4) : (x[i / 2] & 15);",
@@ -95,6 +96,12 @@ MUTANTS = [
      "A[take / 8] ^= (uint64_t)0x06 << (8 * (take % 8));", False),
     ("SHAKE full ADRS word order", "for (i = 0; i < 8; i++) put_be32(out + 4 * i, A->w[i]);",
      "for (i = 0; i < 8; i++) put_be32(out + 4 * i, A->w[7 - i]);", False),
+    ("robust mask always SHA-256", "mgf1_shax(big, seed, n + 22, x, inlen);", "mgf1_shax(0, seed, n + 22, x, inlen);", False),
+    ("robust mask seed without PK.seed", "mgf1_shax(big, seed, n + 22, x, inlen);", "mgf1_shax(big, seed + n, 22, x, inlen);", False),
+    ("robust mask seed one byte short", "mgf1_shax(big, seed, n + 22, x, inlen);", "mgf1_shax(big, seed, n + 21, x, inlen);", False),
+    ("robust PRF masked", "g_calls_prf++; thash(c, 0, A,", "g_calls_prf++; thash_masked(c, 0, A,", False),
+    ("robust T_l unmasked", "g_calls_t++; thash_masked(c, c->p.big, A,", "g_calls_t++; thash(c, c->p.big, A,", False),
+    ("robust F unmasked", "g_calls_f++; thash_masked(c, 0, A,", "g_calls_f++; thash(c, 0, A,", False),
     ("SHAKE PRF_msg operand order", "memcpy(sb, c->sk_prf, n);\n        memcpy(sb + n, opt, n);",
      "memcpy(sb, opt, n);\n        memcpy(sb + n, c->sk_prf, n);", False),
 ]
@@ -161,6 +168,34 @@ def _pins_fail(O):
             sd = R + sk[2 * P.n:3 * P.n] + Hb(R + sk[2 * P.n:] + b"msg").digest()
             if dg != b"".join(Hb(sd + c.to_bytes(4, "big")).digest() for c in range(2))[:P.m]:
                 return "H_msg"
+        for ps in ("128f", "192f"):                 # robust instantiation
+            P = O.params(ps)
+            pk_seed, words = bytes(range(3, 3 + P.n)), [3, 0, 1, 2, 2, 9, 4, 77]
+            ad = bytes([3]) + (1).to_bytes(4, "big") + (2).to_bytes(4, "big") + bytes([2]) + \
+                b"".join(x.to_bytes(4, "big") for x in (9, 4, 77))
+            Hb = hashlib.sha512 if P.n > 16 else hashlib.sha256
+
+            def masked(H, data):
+                mk = b"".join(H(pk_seed + ad + c.to_bytes(4, "big")).digest() for c in range(40))
+                return bytes(a ^ b for a, b in zip(data, mk))
+            pad256, padb = pk_seed + bytes(64 - P.n), pk_seed + bytes((128 if P.n > 16 else 64) - P.n)
+            x1, x2, xl = bytes(range(P.n)), bytes(range(2 * P.n)), bytes(i & 0xFF for i in range(P.len * P.n))
+            if O.thash("robust-" + ps, O.THASH_F, pk_seed, words, x1) != \
+               hashlib.sha256(pad256 + ad + masked(hashlib.sha256, x1)).digest()[:P.n]:
+                return "robust F composition"
+            if O.thash("robust-" + ps, O.THASH_H, pk_seed, words, x2) != Hb(padb + ad + masked(Hb, x2)).digest()[:P.n]:
+                return "robust H composition"
+            if O.thash("robust-" + ps, O.THASH_T, pk_seed, words, xl, l=P.len) != \
+               Hb(padb + ad + masked(Hb, xl)).digest()[:P.n]:
+                return "robust T composition"
+            skseed = bytes(range(7, 7 + P.n))
+            if O.thash("robust-" + ps, O.THASH_PRF, pk_seed, words, sk_seed=skseed) != \
+               hashlib.sha256(pad256 + ad + skseed).digest()[:P.n]:
+                return "robust PRF composition"
+        rtoy = Toy(bytes(range(48)), robust=True)
+        rpk, rsk = O.keygen("robust-toy", bytes(range(48)))
+        if rpk != rtoy.pk_seed + rtoy.pk_root() or O.sign("robust-toy", rsk, b"rm") != rtoy.sign(b"rm"):
+            return "robust toy"
         P = O.params("128f")
         O.counters(reset=True)
         O.wots_pkgen("128f", bytes(64), 1, 2, 3)

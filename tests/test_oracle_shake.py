@@ -24,7 +24,7 @@ class ToyShake(Toy):
     def adrs(layer, tree, typ, kp=0, w6=0, w7=0):
         return adrs32([layer, 0, tree >> 32, tree & 0xFFFFFFFF, typ, kp, w6, w7])
 
-    def th(self, ad, data):
+    def th(self, ad, data, prf=False):
         return hashlib.shake_256(self.pk_seed + ad + data).digest(N)
 
     def sign(self, m):
