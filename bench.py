@@ -324,7 +324,9 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
     steps, warmup = max(2, args.steps // 2), 3
     # the SHAKE sets on fewer messages (a permutation costs ~4.5 SHA-256 compressions)
     shake_counts = {"shake-128f": 4096, "shake-192f": 2048, "shake-256f": 2048, "shake-128s": 256,
-                    "shake-192s": 256, "shake-256s": 256}
+                    "shake-192s": 256, "shake-256s": 256,
+                    # the robust SHA2 instantiation: every F, H and T_l also computes its mask
+                    "robust-128f": 8192, "robust-192f": 4096, "robust-256f": 4096}
     for ps in ("192f", "256f", "128s", "192s", "256s") + tuple(shake_counts):
         log("config %s" % ps)
         if ps in ("192f", "256f"):
@@ -345,11 +347,12 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
         res[ps] = {"workload": wl.name, "value": round(wl.count * len(ms) / (sum(ms) / 1e3), 1),
                    "unit": "signatures/s", "ms_per_step": round(sum(ms) / len(ms), 3),
                    "stage_ms": {a: round(b, 3) for a, b in prof.items()},
-                   "alu_frac": {st: round(exec_alu_per_sig(ps, st) * wl.count / (prof[st] / 1e3) / 1e12 / alu_peak, 4)
-                                for st in ("tree", "fors") if prof.get(st, 0) > 0},
-                   "alu_frac_full_compression": {
+                   "alu_frac": ({st: round(exec_alu_per_sig(ps, st) * wl.count / (prof[st] / 1e3) / 1e12 / alu_peak, 4)
+                                 for st in ("tree", "fors") if prof.get(st, 0) > 0}
+                                if not ps.startswith("robust-") else None),
+                   "alu_frac_full_compression": ({
                        st: round(alu_ops_per_sig(ps, st) * wl.count / (prof[st] / 1e3) / 1e12 / alu_peak, 4)
-                       for st in ("tree", "fors") if prof.get(st, 0) > 0},
+                       for st in ("tree", "fors") if prof.get(st, 0) > 0} if not ps.startswith("robust-") else None),
                    "verified": int(ok.sum().item()) == wl.count}
     # the bench workload again with tree sharing on (same signatures, less work)
     log("128f with tree sharing")

@@ -51,14 +51,22 @@ extern "C" {
  * (32, 64, 8, 8, 14, 22); 7856 / 16224 / 29792-byte signatures.
  * HS_SHAKE_* are the SHAKE256 instantiations of the six sets (SPHINCS+ SHAKE-simple, FIPS 205
  * Sec. 11.1): same sizes and key layout, every hash SHAKE256 with the full
- * 32-byte address; another variant the paper does not use. */
+ * 32-byte address; another variant the paper does not use.
+ * HS_ROBUST_* are the robust SHA2 instantiations of the three f sets
+ * (SPHINCS+ round 3.1 SHA2-robust): F, H and T_l hash their input xor
+ * MGF1-SHA-x(PK.seed || ADRSc, input length), SHA-x being the hash the
+ * tweakable hash itself uses; PRF, PRF_msg and H_msg as in the simple sets.
+ * Same sizes and key layout; keys and signatures differ from the simple
+ * sets'.  A variant the paper does not use; FIPS 205 has no robust sets, so
+ * the hs_slh_* calls refuse them. */
 typedef enum {
     HS_128F = 0, HS_192F = 1, HS_256F = 2, HS_TOY = 3,
     HS_128S = 4, HS_192S = 5, HS_256S = 6,
     HS_SHAKE_128F = 7, HS_SHAKE_192F = 8, HS_SHAKE_256F = 9,
-    HS_SHAKE_128S = 10, HS_SHAKE_192S = 11, HS_SHAKE_256S = 12
+    HS_SHAKE_128S = 10, HS_SHAKE_192S = 11, HS_SHAKE_256S = 12,
+    HS_ROBUST_128F = 13, HS_ROBUST_192F = 14, HS_ROBUST_256F = 15
 } hs_params;
-#define HS_NUM_PARAMS 13
+#define HS_NUM_PARAMS 16
 
 typedef enum {
     HS_OK = 0,

@@ -20,6 +20,9 @@ const SetOps* set_ops(int pset) {
     case 10: return &kOps_K128S;
     case 11: return &kOps_K192S;
     case 12: return &kOps_K256S;
+    case 13: return &kOps_R128F;
+    case 14: return &kOps_R192F;
+    case 15: return &kOps_R256F;
     }
     return nullptr;
 }
@@ -37,7 +40,8 @@ TuneSlots g_slots;
 auto& g_tune = g_slots.v;
 std::atomic<int> g_ck_default{2};
 // Default batch size below which TREE_Sign runs chain-parallel, per set.
-constexpr int kSplitDefault[kNumSets] = {8192, 2048, 4096, 0, 64, 64, 64, 8192, 2048, 4096, 64, 64, 64};
+constexpr int kSplitDefault[kNumSets] = {8192, 2048, 4096, 0, 64, 64, 64, 8192, 2048, 4096, 64, 64, 64,
+                                         8192, 2048, 4096};
 constexpr int kStrides[] = {0, 1, 2, 4, 8};
 }
 

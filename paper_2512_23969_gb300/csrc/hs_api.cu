@@ -58,6 +58,9 @@ static bool set_info(int p, SetInfo* s) {
     case 10: *s = HS_SETINFO(PK128s); return true;
     case 11: *s = HS_SETINFO(PK192s); return true;
     case 12: *s = HS_SETINFO(PK256s); return true;
+    case 13: *s = HS_SETINFO(PR128f); return true;
+    case 14: *s = HS_SETINFO(PR192f); return true;
+    case 15: *s = HS_SETINFO(PR256f); return true;
     }
 #undef HS_SETINFO
     return false;
@@ -602,6 +605,9 @@ HS_API hs_status hs_verify_batch(hs_params p, const uint8_t* pk, uint32_t num_ke
 // ----------------------------------------------------------- FIPS 205
 // The pure-signing prefix 0x00 || len(ctx) || ctx, or none for the
 // internal functions (ctx_len == HS_SLH_INTERNAL).
+// FIPS 205 defines no robust sets.
+static bool robust_set(hs_params p) { return (int)p >= HS_ROBUST_128F && (int)p <= HS_ROBUST_256F; }
+
 static hs_status slh_prefix(const uint8_t* ctx, uint32_t ctx_len, uint8_t* out, uint32_t* plen) {
     if (ctx_len == HS_SLH_INTERNAL) { *plen = 0; return HS_OK; }
     if (ctx_len > 255) return fail(HS_EINVAL, "context string of %u bytes (at most 255)", ctx_len);
@@ -616,6 +622,7 @@ static hs_status slh_prefix(const uint8_t* ctx, uint32_t ctx_len, uint8_t* out, 
 HS_API hs_status hs_slh_sign_batch(hs_params p, const uint8_t* sk, uint32_t num_keys, const uint32_t* key_idx,
                                    const uint8_t* ctx, uint32_t ctx_len, const uint8_t* msgs, const uint64_t* lens,
                                    uint32_t count, uint8_t* sigs, void* stream) {
+    if (robust_set(p)) return fail(HS_EINVAL, "FIPS 205 has no robust parameter sets");
     uint8_t pre[258];
     uint32_t plen = 0;
     const hs_status st = slh_prefix(ctx, ctx_len, pre, &plen);
@@ -627,6 +634,7 @@ HS_API hs_status hs_slh_sign_batch(hs_params p, const uint8_t* sk, uint32_t num_
 HS_API hs_status hs_slh_verify_batch(hs_params p, const uint8_t* pk, uint32_t num_keys, const uint32_t* key_idx,
                                      const uint8_t* ctx, uint32_t ctx_len, const uint8_t* msgs, const uint64_t* lens,
                                      const uint8_t* sigs, uint32_t count, uint8_t* ok, void* stream) {
+    if (robust_set(p)) return fail(HS_EINVAL, "FIPS 205 has no robust parameter sets");
     uint8_t pre[258];
     uint32_t plen = 0;
     const hs_status st = slh_prefix(ctx, ctx_len, pre, &plen);

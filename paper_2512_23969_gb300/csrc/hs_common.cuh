@@ -17,6 +17,7 @@
 #include "sha2.cuh"
 #include "adrs.cuh"
 #include "keccak.cuh"
+#include "robust.cuh"
 
 namespace hs {
 
@@ -65,26 +66,51 @@ __device__ __forceinline__ void thash512(const uint32_t ms[16], const Adrs& a, c
 
 // F / PRF: always SHA-256 over an n-byte payload (chain steps use FULL).
 // (SHAKE sets: ms256 holds PK.seed and the hash is SHAKE256, keccak.cuh.)
+// Robust sets: F hashes x masked (pks = PK.seed words); PRF passes
+// pks = nullptr, as PRF is never masked.
 template <class P, bool FULL = true>
-__device__ __forceinline__ void hashF(const uint32_t ms256[8], const Adrs& a, const uint32_t* x, uint32_t* out) {
-    if constexpr (P::SHAKE) shake_thash1<P::NW, P::NW>(ms256, a, x, out);
-    else thash256<P::NW, P::NW, FULL>(ms256, a, x, out);
+__device__ __forceinline__ void hashF(const uint32_t ms256[8], const Adrs& a, const uint32_t* x, uint32_t* out,
+                                      const uint32_t* pks = nullptr) {
+    if constexpr (P::SHAKE) {
+        shake_thash1<P::NW, P::NW>(ms256, a, x, out);
+    } else if constexpr (P::ROBUST) {
+        uint32_t xm[P::NW];
+#pragma unroll
+        for (int i = 0; i < P::NW; i++) xm[i] = x[i];
+        if (pks) mask_regs<false, P::NW, P::NW>(pks, a, xm);
+        thash256<P::NW, P::NW, FULL>(ms256, a, xm, out);
+    } else {
+        thash256<P::NW, P::NW, FULL>(ms256, a, x, out);
+    }
 }
 
-// H: two n-byte children; SHA-512 for n > 16.
+// H: two n-byte children; SHA-512 for n > 16.  Robust sets: the children
+// masked first (pks = PK.seed words).
+template <class P>
+__device__ __forceinline__ void hashH_ms(const uint32_t* ms256, const uint32_t* ms512, const Adrs& a,
+                                         const uint32_t* lr, uint32_t* out, const uint32_t* pks = nullptr);
 template <class P>
 __device__ __forceinline__ void hashH(const KeyBlock& kb, const Adrs& a, const uint32_t* lr, uint32_t* out) {
-    if constexpr (P::SHAKE) shake_thash1<P::NW, 2 * P::NW>(kb.ms256, a, lr, out);
-    else if constexpr (P::BIG) thash512<2 * P::NW, P::NW>(kb.ms512, a, lr, out);
-    else thash256<2 * P::NW, P::NW, false>(kb.ms256, a, lr, out);
+    hashH_ms<P>(kb.ms256, kb.ms512, a, lr, out, kb.pk_seed);
 }
 // Same, with the midstates passed separately (kernels that keep them in registers).
 template <class P>
 __device__ __forceinline__ void hashH_ms(const uint32_t* ms256, const uint32_t* ms512, const Adrs& a,
-                                         const uint32_t* lr, uint32_t* out) {
-    if constexpr (P::SHAKE) shake_thash1<P::NW, 2 * P::NW>(ms256, a, lr, out);
-    else if constexpr (P::BIG) thash512<2 * P::NW, P::NW>(ms512, a, lr, out);
-    else thash256<2 * P::NW, P::NW, false>(ms256, a, lr, out);
+                                         const uint32_t* lr, uint32_t* out, const uint32_t* pks) {
+    if constexpr (P::SHAKE) {
+        shake_thash1<P::NW, 2 * P::NW>(ms256, a, lr, out);
+    } else if constexpr (P::ROBUST) {
+        uint32_t m[2 * P::NW];
+#pragma unroll
+        for (int i = 0; i < 2 * P::NW; i++) m[i] = lr[i];
+        mask_regs<P::BIG, P::NW, 2 * P::NW>(pks, a, m);
+        if constexpr (P::BIG) thash512<2 * P::NW, P::NW>(ms512, a, m, out);
+        else thash256<2 * P::NW, P::NW, false>(ms256, a, m, out);
+    } else if constexpr (P::BIG) {
+        thash512<2 * P::NW, P::NW>(ms512, a, lr, out);
+    } else {
+        thash256<2 * P::NW, P::NW, false>(ms256, a, lr, out);
+    }
 }
 
 // Streaming T_l: SHA-x over ADRSc || v_0 || ... || v_{l-1} after the

@@ -125,9 +125,10 @@ struct SetOps {
 };
 extern const SetOps kOps_128F, kOps_192F, kOps_256F, kOps_Toy, kOps_128S, kOps_192S, kOps_256S;
 extern const SetOps kOps_K128F, kOps_K192F, kOps_K256F, kOps_K128S, kOps_K192S, kOps_K256S;
+extern const SetOps kOps_R128F, kOps_R192F, kOps_R256F;
 // 128f, 192f, 256f, toy, 128s, 192s, 256s, then the SHAKE instantiations of
-// 128f .. 256s
-constexpr int kNumSets = 13;
+// 128f .. 256s, then the robust SHA2 instantiations of 128f, 192f, 256f
+constexpr int kNumSets = 16;
 
 // Shape of a parameter set for host code (false for an unknown id).
 struct SetShape { int n, d, sig, leaves, k; };

@@ -9,9 +9,13 @@ namespace hs {
 // N: hash bytes, H: hypertree height, D: layers, A: FORS height, K: FORS trees.
 // BIG: H, T_l, H_msg, PRF_msg use SHA-512 (n = 24 / 32).
 // SHAKE_: the SHAKE256 instantiation (a variant; the paper uses SHA-2).
-template <int N_, int H_, int D_, int A_, int K_, bool SHAKE_ = false>
+// ROBUST_: the robust SHA2 instantiation (a variant): F, H and T_l hash
+// their input masked by MGF1 of PK.seed and the address (robust.cuh).
+template <int N_, int H_, int D_, int A_, int K_, bool SHAKE_ = false, bool ROBUST_ = false>
 struct Params {
+    static_assert(!(SHAKE_ && ROBUST_), "robust: SHA2 sets only");
     static constexpr bool SHAKE = SHAKE_;
+    static constexpr bool ROBUST = ROBUST_;
     static constexpr int N = N_;
     static constexpr int H = H_;
     static constexpr int D = D_;
@@ -51,6 +55,11 @@ using PK256f = Params<32, 68, 17, 9, 35, true>;
 using PK128s = Params<16, 63, 7, 12, 14, true>;
 using PK192s = Params<24, 63, 7, 14, 17, true>;
 using PK256s = Params<32, 64, 8, 14, 22, true>;
+
+// The robust SHA2 instantiation of the f sets.
+using PR128f = Params<16, 66, 22, 6, 33, false, true>;
+using PR192f = Params<24, 66, 22, 8, 33, false, true>;
+using PR256f = Params<32, 68, 17, 9, 35, false, true>;
 
 static_assert(P128f::SIG_BYTES == 17088, "128f signature size");
 static_assert(P192f::SIG_BYTES == 35664, "192f signature size");

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) utree_kernel(const KeyBlock* __restrict__
     const Pipes<POL> pp(one);
     uint32_t* mychk = ck ? chk_u + ((size_t)id * LV + l) * (size_t)P::LEN * (16u / ck) * NW : nullptr;
     uint32_t node[NW];
-    wots_leaf<P, POL>(ms256, msT, skseed, d.layer, d.tree, l, node, mychk, ck, pp);
+    wots_leaf<P, POL>(ms256, msT, skseed, d.layer, d.tree, l, node, mychk, ck, pp, kb.pk_seed);
     uint32_t* tn = nodes + (size_t)id * 2 * LV * NW;
 #pragma unroll
     for (int w = 0; w < NW; w++) tn[(LV + l) * NW + w] = node[w];
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(128) utree_kernel(const KeyBlock* __restrict__
             uint32_t lr[2 * NW];
 #pragma unroll
             for (int w = 0; w < NW; w++) { lr[w] = node[w]; lr[NW + w] = other[w]; }
-            hashH_ms<P>(ms256, msT, make_adrs(d.layer, d.tree, T_TREE, 0, z, l >> z), lr, node);
+            hashH_ms<P>(ms256, msT, make_adrs(d.layer, d.tree, T_TREE, 0, z, l >> z), lr, node, kb.pk_seed);
 #pragma unroll
             for (int w = 0; w < NW; w++) tn[((LV >> z) + (l >> z)) * NW + w] = node[w];
         }

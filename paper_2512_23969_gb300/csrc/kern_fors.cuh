@@ -157,11 +157,18 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
             for (int w = 0; w < NW; w++) node[w] = skseed[w];
 #pragma unroll 1
             for (int s = 0; s < 2; s++) {
-                if constexpr (kCtx) {
+                if constexpr (kCtx && P::ROBUST) {
+                    // the leaf F (s = 1) hashes sk masked with its own address; PRF does not
+                    uint32_t xm[NW];
+#pragma unroll
+                    for (int w = 0; w < NW; w++) xm[w] = node[w];
+                    if (s == 1) mask_regs<false, NW, NW>(kb.pk_seed, make_adrs(0, tree, T_FORS_TREE, kp, 0, g), xm);
+                    chain_step<POL, NW>(cxs[s], ms256, g, xm, node, pp);
+                } else if constexpr (kCtx) {
                     chain_step<POL, NW>(cxs[s], ms256, g, node, node, pp);
                 } else {
                     hashF_p<P, POL>(ms256, make_adrs(0, tree, s == 0 ? T_FORS_PRF : T_FORS_TREE, kp, 0, g), node,
-                                    node, pp);
+                                    node, pp, s == 0 ? nullptr : kb.pk_seed);
                 }
                 if (s == 0 && t == gs) store_be<NW>(sf, node);
             }
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
                 z++;
                 idx >>= 1;
                 hashH_p<P, POL>(ms256, ms512,
-                                make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node, pp);
+                                make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node, pp, kb.pk_seed);
                 if (z < (uint32_t)A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
             }
             if (z < (uint32_t)RI) stk.store(z, node);
@@ -194,7 +201,7 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
                 z++;
                 idx >>= 1;
                 hashH_p<P, POL>(ms256, ms512,
-                                make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node, pp);
+                                make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node, pp, kb.pk_seed);
                 if (z < (uint32_t)A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
             }
             if (z < (uint32_t)R) stk.store_outer(z, node);
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
 #pragma unroll
             for (int w = 0; w < NW; w++) { lr[w] = node[w]; lr[NW + w] = other[w]; }
             const uint32_t idx = L >> (z - R);
-            hashH_p<P, POL>(ms256, ms512, make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node, pp);
+            hashH_p<P, POL>(ms256, ms512, make_adrs(0, tree, T_FORS_TREE, kp, z, (i << (A - z)) + idx), lr, node, pp, kb.pk_seed);
             if (z < A && idx == ((gs >> z) ^ 1u)) store_be<NW>(sf + (size_t)(1 + z) * P::N, node);
         }
     }
@@ -243,6 +250,8 @@ __global__ void fors_pk_kernel(const KeyBlock* __restrict__ keys, const MsgInfo*
         for (int i = 0; i < P::K; i++) ts.template push_n<NW>(r + i * NW);
         ts.template finish<NW>(P::K * P::N, out);
     } else {
+        // robust: mask this message's roots in place (scratch, read once)
+        if constexpr (P::ROBUST) mask_mem<P::BIG, NW, P::K * NW>(kb.pk_seed, a, const_cast<uint32_t*>(r));
         tl_from_mem<P::BIG, P::K * NW, NW>(P::BIG ? kb.ms512 : kb.ms256, a, r, out);
     }
 #pragma unroll

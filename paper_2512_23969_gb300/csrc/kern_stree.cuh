@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(128, MINB) bleaf_kernel(const KeyBlock* __rest
     uint32_t* mychk = (ck != 0 && l == sl)
                           ? chk + ((size_t)m * P::D + j) * (size_t)P::LEN * (16u / ck) * NW : nullptr;
     uint32_t node[NW];
-    wots_leaf<P, POL, ILP>(ms256, msT, skseed, j, tree, l, node, mychk, ck, pp);
+    wots_leaf<P, POL, ILP>(ms256, msT, skseed, j, tree, l, node, mychk, ck, pp, kb.pk_seed);
     uint32_t* out = leafv + (((size_t)m * P::D + j) * LV + l) * NW;
 #pragma unroll
     for (int w = 0; w < NW; w++) out[w] = node[w];
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(128) wtree_leaf_kernel(const KeyBlock* __restr
     const Pipes<POL> pp(one);
     uint32_t* mychk = ck ? chk_u + ((size_t)id * LV + l) * (size_t)P::LEN * (16u / ck) * NW : nullptr;
     uint32_t node[NW];
-    wots_leaf<P, POL>(ms256, msT, skseed, d.layer, d.tree, l, node, mychk, ck, pp);
+    wots_leaf<P, POL>(ms256, msT, skseed, d.layer, d.tree, l, node, mychk, ck, pp, kb.pk_seed);
     uint32_t* tn = nodes + (size_t)id * 2 * LV * NW;
 #pragma unroll
     for (int w = 0; w < NW; w++) tn[((size_t)LV + l) * NW + w] = node[w];
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(128) bkeygen_leaf_kernel(const KeyBlock* __res
     for (int w = 0; w < NW; w++) skseed[w] = kb.sk_seed[w];
     const Pipes<POL> pp(one);
     uint32_t node[NW];
-    wots_leaf<P, POL>(ms256, msT, skseed, (uint32_t)P::D - 1, 0ull, l, node, nullptr, 0u, pp);
+    wots_leaf<P, POL>(ms256, msT, skseed, (uint32_t)P::D - 1, 0ull, l, node, nullptr, 0u, pp, kb.pk_seed);
 #pragma unroll
     for (int w = 0; w < NW; w++) leafv[((size_t)key * LV + l) * NW + w] = node[w];
 }

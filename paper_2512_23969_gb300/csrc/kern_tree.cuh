@@ -56,12 +56,14 @@ __device__ __forceinline__ void store_checkpoint(uint32_t* d, const uint32_t* x)
 // ILP = 2 (SHA-2 only): the thread runs its chains two at a time, the two
 // chains' compressions interleaved (more independent work per thread, more
 // registers); the last chain of an odd len runs alone.  Same bytes.
+// pks: PK.seed words (the robust sets' masks; unused by the others).
 template <class P, int POL, int ILP = 1>
 __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t* msT, const uint32_t* skseed,
                                           uint32_t layer, uint64_t tree, uint32_t kp, uint32_t* out,
-                                          uint32_t* chk, uint32_t ck, const Pipes<POL>& pp) {
+                                          uint32_t* chk, uint32_t ck, const Pipes<POL>& pp, const uint32_t* pks) {
     constexpr int NW = P::NW;
-    static_assert(ILP == 1 || (ILP == 2 && !P::SHAKE), "two chains per thread: SHA-2 sets only");
+    static_assert(ILP == 1 || (ILP == 2 && !P::SHAKE && !P::ROBUST),
+                  "two chains per thread: simple SHA-2 sets only");
     // SHA-2: chain ends go to a per-thread array (local memory) and T_len
     // runs over it afterwards, so no hash state is live across the chain
     // loop; SHAKE streams them into its own buffer.
@@ -124,6 +126,23 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
                 a.w4 = i << 16;
                 a.half = s == 0 ? 0u : s - 1u;
                 hashF_p<P, POL>(ms256, a, x, x, pp);
+            } else if constexpr (P::ROBUST) {
+                if (s <= 1) {
+                    Adrs a = (s == 0) ? aprf : ahash;
+                    a.w4 = i << 16;
+                    chain_ctx<POL>(ms256, a, cx, pp);
+                }
+                // F steps hash x masked with their own address; PRF (s = 0) does not
+                uint32_t xm[NW];
+#pragma unroll
+                for (int w = 0; w < NW; w++) xm[w] = x[w];
+                if (s > 0) {
+                    Adrs ah = ahash;
+                    ah.w4 = i << 16;
+                    ah.half = s - 1u;
+                    mask_regs<false, NW, NW>(pks, ah, xm);
+                }
+                chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, xm, x, pp);
             } else {
                 if (s <= 1) {
                     Adrs a = (s == 0) ? aprf : ahash;
@@ -141,8 +160,13 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
             for (int w = 0; w < NW; w++) ends[i * NW + w] = x[w];
         }
     }
-    if constexpr (P::SHAKE) ts.template finish<NW>(P::LEN * P::N, out);
-    else tl_from_mem_p<P::BIG, P::LEN * NW, NW, POL>(msT, make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0), ends, out, pp);
+    if constexpr (P::SHAKE) {
+        ts.template finish<NW>(P::LEN * P::N, out);
+    } else {
+        const Adrs apk = make_adrs(layer, tree, T_WOTS_PK, kp, 0, 0);
+        if constexpr (P::ROBUST) mask_mem<P::BIG, NW, P::LEN * NW>(pks, apk, ends);
+        tl_from_mem_p<P::BIG, P::LEN * NW, NW, POL>(msT, apk, ends, out, pp);
+    }
 }
 
 // Merkle levels of one XMSS tree held by an aligned lane group (one leaf
@@ -152,7 +176,7 @@ template <class P>
 __device__ __forceinline__ void merkle_finish(const uint32_t* ms256, const uint32_t* msT, unsigned gmask,
                                               uint32_t m, uint32_t j, uint32_t l, uint32_t sl, uint64_t tree,
                                               uint32_t* node, uint8_t* __restrict__ sigs,
-                                              uint32_t* __restrict__ roots) {
+                                              uint32_t* __restrict__ roots, const uint32_t* pks) {
     constexpr int NW = P::NW, HP = P::HP;
     uint8_t* auth = sigs + (size_t)m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES +
                     (size_t)P::LEN * P::N;
@@ -168,7 +192,7 @@ __device__ __forceinline__ void merkle_finish(const uint32_t* ms256, const uint3
 #pragma unroll
             for (int w = 0; w < NW; w++) { lr[w] = node[w]; lr[NW + w] = other[w]; }
             const uint32_t idx = l >> z;
-            hashH_ms<P>(ms256, msT, make_adrs(j, tree, T_TREE, 0, z, idx), lr, node);
+            hashH_ms<P>(ms256, msT, make_adrs(j, tree, T_TREE, 0, z, idx), lr, node, pks);
             if (z < HP && idx == ((sl >> z) ^ 1u)) store_be<NW>(auth + (size_t)z * P::N, node);
         }
     }
@@ -207,6 +231,9 @@ __global__ void __launch_bounds__(128, MINB) tree_kernel(const KeyBlock* __restr
     for (int w = 0; w < (P::BIG ? 16 : 8); w++) msT[w] = P::BIG ? kb.ms512[w] : kb.ms256[w];
 #pragma unroll
     for (int w = 0; w < NW; w++) skseed[w] = kb.sk_seed[w];
+    uint32_t pks[P::ROBUST ? NW : 1];
+#pragma unroll
+    for (int w = 0; w < (P::ROBUST ? NW : 1); w++) pks[w] = P::ROBUST ? kb.pk_seed[w] : 0u;
 
     const uint64_t tree = layer_tree<P>(info.idx_tree, (int)j);
     const uint32_t sl = layer_leaf<P>(info.idx_tree, info.idx_leaf, (int)j);
@@ -215,9 +242,9 @@ __global__ void __launch_bounds__(128, MINB) tree_kernel(const KeyBlock* __restr
     uint32_t* mychk = (ck != 0 && l == sl)
                           ? chk + ((size_t)m * P::D + j) * (size_t)P::LEN * (16u / ck) * NW : nullptr;
     uint32_t node[NW];
-    wots_leaf<P, POL, ILP>(ms256, msT, skseed, j, tree, l, node, mychk, ck, pp);
+    wots_leaf<P, POL, ILP>(ms256, msT, skseed, j, tree, l, node, mychk, ck, pp, pks);
 
-    merkle_finish<P>(ms256, msT, gmask, m, j, l, sl, tree, node, sigs, roots);
+    merkle_finish<P>(ms256, msT, gmask, m, j, l, sl, tree, node, sigs, roots, pks);
 }
 
 // TREE_Sign, chain-parallel form for batches too small to fill the GPU with
@@ -261,6 +288,16 @@ __global__ void __launch_bounds__(128) chains_kernel(const KeyBlock* __restrict_
         if constexpr (P::SHAKE) {
             hashF_p<P, POL>(ms256, make_adrs(j, tree, s == 0 ? T_WOTS_PRF : T_WOTS_HASH, l, i, s == 0 ? 0u : s - 1u),
                             x, x, pp);
+        } else if constexpr (P::ROBUST) {
+            if (s <= 1) {
+                Adrs a = make_adrs(j, tree, s == 0 ? T_WOTS_PRF : T_WOTS_HASH, l, i, 0);
+                chain_ctx<POL>(ms256, a, cx, pp);
+            }
+            uint32_t xm[NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) xm[w] = x[w];
+            if (s > 0) mask_regs<false, NW, NW>(kb.pk_seed, make_adrs(j, tree, T_WOTS_HASH, l, i, s - 1u), xm);
+            chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, xm, x, pp);
         } else {
             if (s <= 1) {
                 Adrs a = make_adrs(j, tree, s == 0 ? T_WOTS_PRF : T_WOTS_HASH, l, i, 0);
@@ -309,9 +346,12 @@ __global__ void __launch_bounds__(128) leaves_kernel(const KeyBlock* __restrict_
         for (int i = 0; i < LEN; i++) ts.template push_n<NW>(e + i * NW);
         ts.template finish<NW>(LEN * P::N, node);
     } else {
-        tl_from_mem<P::BIG, LEN * NW, NW>(msT, make_adrs(j, tree, T_WOTS_PK, l, 0, 0), e, node);
+        const Adrs apk = make_adrs(j, tree, T_WOTS_PK, l, 0, 0);
+        // robust: mask this leaf's own chain ends in place (scratch, read once)
+        if constexpr (P::ROBUST) mask_mem<P::BIG, NW, LEN * NW>(kb.pk_seed, apk, const_cast<uint32_t*>(e));
+        tl_from_mem<P::BIG, LEN * NW, NW>(msT, apk, e, node);
     }
-    merkle_finish<P>(ms256, msT, gmask, m, j, l, sl, tree, node, sigs, roots);
+    merkle_finish<P>(ms256, msT, gmask, m, j, l, sl, tree, node, sigs, roots, kb.pk_seed);
 }
 
 // Key generation: PK.root = root of tree 0 of the top layer d-1.  One lane
@@ -358,7 +398,7 @@ __global__ void __launch_bounds__(128) keygen_kernel(const uint8_t* __restrict__
     const uint32_t top = (uint32_t)P::D - 1;
     uint32_t node[NW];
     const Pipes<kChainPol> pp(one);
-    wots_leaf<P, kChainPol>(ms256, msT, skseed, top, 0ull, l, node, nullptr, 0u, pp);
+    wots_leaf<P, kChainPol>(ms256, msT, skseed, top, 0ull, l, node, nullptr, 0u, pp, pkseed);
 #pragma unroll
     for (int z = 1; z <= HP; z++) {
         const int step = 1 << (z - 1);
@@ -369,7 +409,7 @@ __global__ void __launch_bounds__(128) keygen_kernel(const uint8_t* __restrict__
             uint32_t lr[2 * NW];
 #pragma unroll
             for (int w = 0; w < NW; w++) { lr[w] = node[w]; lr[NW + w] = other[w]; }
-            hashH_ms<P>(ms256, msT, make_adrs(top, 0ull, T_TREE, 0, z, l >> z), lr, node);
+            hashH_ms<P>(ms256, msT, make_adrs(top, 0ull, T_TREE, 0, z, l >> z), lr, node, pkseed);
         }
     }
     if (l == 0) {

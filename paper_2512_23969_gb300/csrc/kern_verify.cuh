@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(128) vfors_kernel(const KeyBlock* __restrict__
     const uint32_t g = (i << A) + info.fors_idx[i];
     uint32_t sk[NW], node[NW];
     load_be<NW>(s, sk);
-    hashF<P, false>(ms256, make_adrs(0, info.idx_tree, T_FORS_TREE, info.idx_leaf, 0, g), sk, node);
+    hashF<P, false>(ms256, make_adrs(0, info.idx_tree, T_FORS_TREE, info.idx_leaf, 0, g), sk, node, kb.pk_seed);
 #pragma unroll 1
     for (int z = 0; z < A; z++) {
         const uint32_t gz = g >> z;
@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(128) vfors_kernel(const KeyBlock* __restrict__
             lr[w] = (gz & 1) ? au[w] : node[w];
             lr[NW + w] = (gz & 1) ? node[w] : au[w];
         }
-        hashH_ms<P>(ms256, msT, make_adrs(0, info.idx_tree, T_FORS_TREE, info.idx_leaf, z + 1, gz >> 1), lr, node);
+        hashH_ms<P>(ms256, msT, make_adrs(0, info.idx_tree, T_FORS_TREE, info.idx_leaf, z + 1, gz >> 1), lr, node,
+                    kb.pk_seed);
     }
     uint32_t* r = fors_roots + ((size_t)m * K + i) * NW;
 #pragma unroll
@@ -196,6 +197,12 @@ __global__ void __launch_bounds__(128) vchain_kernel(const KeyBlock* __restrict_
 #pragma unroll 1
             for (uint32_t q = digit; q < 15u; q++)
                 hashF_p<P, POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, q), x, x, pp);
+        } else if constexpr (P::ROBUST) {
+            ChainCtx cx;
+            const Adrs ah = make_adrs(j, tree, T_WOTS_HASH, kp, i, 0);
+            chain_ctx<POL>(ms256, ah, cx, pp);
+#pragma unroll 1
+            for (uint32_t q = digit; q < 15u; q++) chain_step_p<P, POL>(cx, ms256, ah, q, x, x, pp, kb.pk_seed);
         } else {
             ChainCtx cx;
             chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, 0), cx, pp);
@@ -230,7 +237,10 @@ __device__ __forceinline__ void layer_root(const KeyBlock* __restrict__ keys, co
         for (int i = 0; i < LEN; i++) ts.template push_n<NW>(e + i * NW);
         ts.template finish<NW>(LEN * P::N, node);
     } else {
-        tl_from_mem<P::BIG, LEN * NW, NW>(msT, make_adrs(j, tree, T_WOTS_PK, kp, 0, 0), e, node);
+        const Adrs apk = make_adrs(j, tree, T_WOTS_PK, kp, 0, 0);
+        // robust: mask this message's chain ends of the layer in place (scratch, read once)
+        if constexpr (P::ROBUST) mask_mem<P::BIG, NW, LEN * NW>(kb.pk_seed, apk, const_cast<uint32_t*>(e));
+        tl_from_mem<P::BIG, LEN * NW, NW>(msT, apk, e, node);
     }
     const uint8_t* auth = sigs + (size_t)m * P::SIG_BYTES + P::N + P::FORS_BYTES + (size_t)j * P::LAYER_BYTES +
                           (size_t)LEN * P::N;
@@ -244,7 +254,7 @@ __device__ __forceinline__ void layer_root(const KeyBlock* __restrict__ keys, co
             lr[w] = (iz & 1) ? au[w] : node[w];
             lr[NW + w] = (iz & 1) ? node[w] : au[w];
         }
-        hashH_ms<P>(ms256, msT, make_adrs(j, tree, T_TREE, 0, z + 1, iz >> 1), lr, node);
+        hashH_ms<P>(ms256, msT, make_adrs(j, tree, T_TREE, 0, z + 1, iz >> 1), lr, node, kb.pk_seed);
     }
 #pragma unroll
     for (int w = 0; w < NW; w++) vroot[(size_t)m * NW + w] = node[w];

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) wots_kernel(const KeyBlock* __restrict__ 
 #pragma unroll 1
         for (uint32_t q = base; q < digit; q++) {
             a.half = q;
-            hashF_p<P, POL>(ms256, a, x, x, pp);
+            hashF_p<P, POL>(ms256, a, x, x, pp, kb.pk_seed);
         }
     } else {
 #pragma unroll
@@ -89,6 +89,14 @@ __global__ void __launch_bounds__(256) wots_kernel(const KeyBlock* __restrict__ 
             hashF_p<P, POL>(ms256, make_adrs(j, tree, T_WOTS_PRF, kp, i, 0), x, x, pp);
 #pragma unroll 1
             for (uint32_t q = 0; q < digit; q++) hashF_p<P, POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, q), x, x, pp);
+        } else if constexpr (P::ROBUST) {
+        ChainCtx cx;
+        chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_PRF, kp, i, 0), cx, pp);
+        chain_step<POL, NW>(cx, ms256, 0u, x, x, pp);           // PRF: not masked
+        if (digit > 0) chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, 0), cx, pp);
+#pragma unroll 1
+        for (uint32_t q = 0; q < digit; q++)
+            chain_step_p<P, POL>(cx, ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, 0), q, x, x, pp, kb.pk_seed);
         } else {
         ChainCtx cx;
         chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_PRF, kp, i, 0), cx, pp);

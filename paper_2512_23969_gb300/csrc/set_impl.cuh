@@ -231,12 +231,12 @@ struct SetImpl {
 // The compiled variants of TREE_Sign's per-leaf kernel for one set, as
 // (min blocks per SM, addition policy, chains per thread): the default
 // (0, tree_pol<P>(), 1); the other addition policy and two interleaved
-// chains per thread (SHA-2 sets other than toy); and MB_ALT min blocks
+// chains per thread (simple SHA-2 sets other than toy); and MB_ALT min blocks
 // (0 = none) -- each alternative with the other two at their defaults.
 template <class P, int MB_ALT>
 struct TreeVariants {
     static constexpr int PD = tree_pol<P>();
-    static constexpr bool kAlts = !P::SHAKE && P::LEAVES >= 8;   // not SHAKE, not the toy set
+    static constexpr bool kAlts = !P::SHAKE && !P::ROBUST && P::LEAVES >= 8;   // simple SHA-2, not toy
     static constexpr int PA = PD == 7 ? 15 : 7;
     static bool has(int minb, int pol, int ilp) {
         if (minb == 0 && pol == PD && ilp == 1) return true;

@@ -184,11 +184,40 @@ __device__ __forceinline__ void hashF_fast(const uint32_t ms[8], const Adrs& a, 
 
 // F / PRF of a parameter set: the chain-specialised SHA-256 call above, or
 // one SHAKE256 block for the SHAKE sets (ms256 then holds PK.seed).
+// Robust sets: pks = PK.seed words masks the payload (F); nullptr = PRF.
 template <class P, int POL>
 __device__ __forceinline__ void hashF_p(const uint32_t ms256[8], const Adrs& a, const uint32_t* x, uint32_t* out,
-                                        const Pipes<POL>& pp) {
-    if constexpr (P::SHAKE) shake_thash1<P::NW, P::NW>(ms256, a, x, out);
-    else hashF_fast<POL, P::NW>(ms256, a, x, out, pp);
+                                        const Pipes<POL>& pp, const uint32_t* pks = nullptr) {
+    if constexpr (P::SHAKE) {
+        shake_thash1<P::NW, P::NW>(ms256, a, x, out);
+    } else if constexpr (P::ROBUST) {
+        uint32_t xm[P::NW];
+#pragma unroll
+        for (int i = 0; i < P::NW; i++) xm[i] = x[i];
+        if (pks) mask_regs<false, P::NW, P::NW>(pks, a, xm);
+        hashF_fast<POL, P::NW>(ms256, a, xm, out, pp);
+    } else {
+        hashF_fast<POL, P::NW>(ms256, a, x, out, pp);
+    }
+}
+
+// One chain step F(WOTS_HASH(.., hash q), x) with the chain's context: the
+// robust sets mask x with the step's own address first (a: the chain's
+// WOTS_HASH address; its half word is set to q here).
+template <class P, int POL>
+__device__ __forceinline__ void chain_step_p(const ChainCtx& cx, const uint32_t ms256[8], Adrs a, uint32_t q,
+                                             const uint32_t* x, uint32_t* out, const Pipes<POL>& pp,
+                                             const uint32_t* pks) {
+    if constexpr (P::ROBUST) {
+        uint32_t xm[P::NW];
+#pragma unroll
+        for (int i = 0; i < P::NW; i++) xm[i] = x[i];
+        a.half = q;
+        mask_regs<false, P::NW, P::NW>(pks, a, xm);
+        chain_step<POL, P::NW>(cx, ms256, q, xm, out, pp);
+    } else {
+        chain_step<POL, P::NW>(cx, ms256, q, x, out, pp);
+    }
 }
 
 // The same compression as sha256_compress_rolled (16 rounds unrolled in a
@@ -254,12 +283,16 @@ __device__ __forceinline__ void tl_from_mem_p(const uint32_t* ms, const Adrs& a,
 // it is one SHA-256 block (n = 16); SHA-512 (n > 16) and SHAKE as hashH_ms.
 template <class P, int POL>
 __device__ __forceinline__ void hashH_p(const uint32_t* ms256, const uint32_t* ms512, const Adrs& a,
-                                        const uint32_t* lr, uint32_t* out, const Pipes<POL>& pp) {
+                                        const uint32_t* lr, uint32_t* out, const Pipes<POL>& pp,
+                                        const uint32_t* pks = nullptr) {
     if constexpr (P::SHAKE || P::BIG) {
-        hashH_ms<P>(ms256, ms512, a, lr, out);
+        hashH_ms<P>(ms256, ms512, a, lr, out, pks);
     } else {
-        uint32_t W[16], st[8];
-        fill_block<16, 2 * P::NW>(W, a, lr);
+        uint32_t W[16], st[8], m[2 * P::NW];
+#pragma unroll
+        for (int i = 0; i < 2 * P::NW; i++) m[i] = lr[i];
+        if constexpr (P::ROBUST) mask_regs<false, P::NW, 2 * P::NW>(pks, a, m);
+        fill_block<16, 2 * P::NW>(W, a, m);
         W[15] = (64 + 22 + 8 * P::NW) * 8;
 #pragma unroll
         for (int i = 0; i < 8; i++) st[i] = ms256[i];

@@ -11,11 +11,13 @@ import os
 import numpy as np
 
 PARAMS = {"128f": 0, "192f": 1, "256f": 2, "toy": 3, "128s": 4, "192s": 5, "256s": 6,
-          "shake-128f": 7, "shake-192f": 8, "shake-256f": 9, "shake-128s": 10, "shake-192s": 11, "shake-256s": 12}
+          "shake-128f": 7, "shake-192f": 8, "shake-256f": 9, "shake-128s": 10, "shake-192s": 11, "shake-256s": 12,
+          "robust-128f": 13, "robust-192f": 14, "robust-256f": 15}
 N_BYTES = {"128f": 16, "192f": 24, "256f": 32, "toy": 16, "128s": 16, "192s": 24, "256s": 32}
 N_BYTES.update({"shake-" + k: v for k, v in list(N_BYTES.items()) if k != "toy"})
-NUM_PARAMS = 13
-_N_BY_ID = [16, 24, 32, 16, 16, 24, 32, 16, 24, 32, 16, 24, 32]
+N_BYTES.update({"robust-" + k: N_BYTES[k] for k in ("128f", "192f", "256f")})
+NUM_PARAMS = 16
+_N_BY_ID = [16, 24, 32, 16, 16, 24, 32, 16, 24, 32, 16, 24, 32, 16, 24, 32]
 STATUS = {0: "HS_OK", 1: "HS_EINVAL", 2: "HS_ENOMEM", 3: "HS_ECUDA", 4: "HS_ETIMEOUT", 5: "HS_EKEY",
           6: "HS_ECANCELED", 7: "HS_EBUDGET"}
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libhs.so")
@@ -537,7 +539,7 @@ class Server:
 
 
 SIG_BY_ID = {0: 17088, 1: 35664, 2: 49856, 3: 1456, 4: 7856, 5: 16224, 6: 29792,
-             7: 17088, 8: 35664, 9: 49856, 10: 7856, 11: 16224, 12: 29792}
+             7: 17088, 8: 35664, 9: 49856, 10: 7856, 11: 16224, 12: 29792, 13: 17088, 14: 35664, 15: 49856}
 
 
 def hs_set_host_direct(on=True):

@@ -16,6 +16,7 @@ import numpy as np
 
 N_BYTES = {"128f": 16, "192f": 24, "256f": 32, "toy": 16, "128s": 16, "192s": 24, "256s": 32}
 N_BYTES.update({"shake-" + k: v for k, v in list(N_BYTES.items()) if k != "toy"})
+N_BYTES.update({"robust-" + k: N_BYTES[k] for k in ("128f", "192f", "256f")})
 BASE_SEED = 23969
 
 

@@ -35,7 +35,8 @@ def test_exports_every_declared_symbol(lib):
 
 def test_size_queries_match_oracle(lib, O):
     names = ("128f", "192f", "256f", "toy", "128s", "192s", "256s",
-             "shake-128f", "shake-192f", "shake-256f", "shake-128s", "shake-192s", "shake-256s")
+             "shake-128f", "shake-192f", "shake-256f", "shake-128s", "shake-192s", "shake-256s",
+             "robust-128f", "robust-192f", "robust-256f")
     for pid, ps in enumerate(names):
         P = O.params(ps)
         for fn, want in (("hs_sig_bytes", P.sig_bytes), ("hs_pk_bytes", 2 * P.n),
@@ -55,7 +56,7 @@ def test_count_zero_and_bad_enum_need_no_gpu(lib):
     lib.hs_sign_batch.restype = C.c_int
     lib.hs_sign_batch.argtypes = [C.c_int, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_uint32, C.c_void_p, C.c_void_p]
-    assert lib.hs_sign_batch(13, None, 1, None, None, None, 1, None, None) == 1     # HS_EINVAL
+    assert lib.hs_sign_batch(16, None, 1, None, None, None, 1, None, None) == 1     # HS_EINVAL
     assert lib.hs_sign_batch(0, None, 1, None, None, None, 0, None, None) == 0      # count 0: no-op
     lib.hs_last_error.restype = C.c_char_p
     assert b"parameter set" in lib.hs_last_error()
