@@ -452,9 +452,10 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
     for name, fn in (("plain_per_set_calls", splain),
                      ("one_graph_launch", lambda: hs.hs_sign_mixed(sjobs, use_graph=True, stream=stream)),
                      ("streams_no_graph", lambda: hs.hs_sign_mixed(sjobs, use_graph=False, stream=stream))):
-        ms = _time_steps(fn, stream, flush, max(steps, 5), warmup)
+        ms = sorted(_time_steps(fn, stream, flush, 20, warmup))     # short steps: 20, median reported too
         sout[name] = {"value": round(stotal * len(ms) / (sum(ms) / 1e3), 1), "unit": "signatures/s",
-                      "ms_per_step": round(sum(ms) / len(ms), 3)}
+                      "ms_per_step": round(sum(ms) / len(ms), 3), "median_ms": round(ms[len(ms) // 2], 3),
+                      "min_ms": round(ms[0], 3)}
     try:
         sout["stage_ms_per_set"] = stage_breakdown(hs, sjobs, stream, flush)
     except Exception as exc:

@@ -130,6 +130,12 @@ hs_status hs_sign_batch(hs_params p, const uint8_t *sk, uint32_t num_keys,
  *   use_graph: 1 = the whole fork/join sequence is captured into one CUDA
  *             graph and launched once; 0 = the same launches go out directly
  * Asynchronous on 'stream'; signatures are identical to hs_sign_batch's.
+ * The graph form keeps its graph and its scratch (a device buffer the
+ * library owns, grown as needed and kept until the process exits) from
+ * call to call: a call with the same jobs (same buffers, counts and sets)
+ * and the same tuning relaunches the graph without capturing it again; a
+ * call of the same shape updates it in place.  Graph-form calls on a
+ * device share that buffer, so each waits on the GPU for the previous one.
  * Errors: HS_EINVAL (bad set, NULL or host buffer, more than 16 jobs),
  * HS_ENOMEM, HS_ECUDA.  Key-index errors go to the status word.
  * Calls must not be issued concurrently from several host threads.

@@ -10,12 +10,15 @@
 // use_graph the whole fork/join sequence is stream-captured into one graph
 // and launched once; without it the same launches go out directly (the
 // "plain" per-stage form that the graph form is measured against).  The
-// instantiated graph is kept per device: a later call whose DAG has the
+// instantiated graph is kept per device, with its scratch at a fixed device
+// address: a later call with the same batches and launch choices relaunches
+// it unchanged (no capture: one cudaGraphLaunch), and one whose DAG has the
 // same shape (same sets, batch-size class and options; only pointers and
 // counts differ) updates its kernel arguments in place
 // (cudaGraphExecUpdate) instead of instantiating anew.
 #include <cuda_runtime.h>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 #include <vector>
 #include "hs_launch.h"
@@ -32,7 +35,18 @@ struct MixedDev {
     bool init = false;
     std::mutex mu;                      // one call at a time per device: shared streams and graph
     cudaGraphExec_t exec = nullptr;     // last instantiated graph, reused when the DAG shape matches
-    uint64_t instantiations = 0, updates = 0;
+    uint64_t instantiations = 0, updates = 0, replays = 0;
+    // Graph form: its scratch is one device buffer at a fixed address, so
+    // that the instantiated graph stays valid from call to call; a call
+    // whose batches and launch choices equal the last graph's relaunches it
+    // as it is.  Every graph launch waits for the previous one (gdone):
+    // they share the buffer.
+    void* gscratch = nullptr;
+    size_t gcap = 0;
+    cudaEvent_t gdone = nullptr;
+    bool gdone_valid = false;
+    std::vector<Batch> last_bs;
+    std::vector<int> last_choice;
     cudaStream_t capture;               // graphs are captured here, launched on the caller's stream
     cudaStream_t side[2 * kMaxJobs];
     cudaEvent_t fork, msg[kMaxJobs], fors[kMaxJobs], done[kMaxJobs];
@@ -57,7 +71,8 @@ hs_status mixed_dev(MixedDev** out) {
         bool ok = cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking) == cudaSuccess;
         for (int i = 0; i < 2 * kMaxJobs && ok; i++)
             ok = cudaStreamCreateWithFlags(&d.side[i], cudaStreamNonBlocking) == cudaSuccess;
-        ok = ok && cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&d.gdone, cudaEventDisableTiming) == cudaSuccess;
         for (int i = 0; i < kMaxJobs && ok; i++)
             ok = cudaEventCreateWithFlags(&d.msg[i], cudaEventDisableTiming) == cudaSuccess &&
                  cudaEventCreateWithFlags(&d.fors[i], cudaEventDisableTiming) == cudaSuccess &&
@@ -81,6 +96,24 @@ bool is_dev(const void* p, int dev) {
         return false;
     }
     return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+}
+
+// The choices the launchers make at launch time from the tuning state (FORS
+// lanes, TREE_Sign variant), per batch: a graph captured under other
+// choices must be captured again.
+std::vector<int> launch_choices(const std::vector<Batch>& bs) {
+    std::vector<int> c;
+    for (const Batch& b : bs) {
+        c.push_back(fors_lanes(b.pset, b.count));
+        c.push_back(tune_get(b.pset, 1));
+        c.push_back(tune_get(b.pset, 3));
+        c.push_back(tune_get(b.pset, 4));
+    }
+    return c;
+}
+
+bool same_batches(const std::vector<Batch>& a, const std::vector<Batch>& b) {
+    return a.size() == b.size() && (a.empty() || memcmp(a.data(), b.data(), a.size() * sizeof(Batch)) == 0);
 }
 
 // Enqueue every job's stage DAG (fork from / join into 'origin').
@@ -156,21 +189,49 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
     if (st != HS_OK) return st;
     uint32_t* status = device_status_word();
     if (!status) return mx_fail(HS_ECUDA, "hs_sign_mixed: device state unavailable");
+    std::lock_guard<std::mutex> lk(d->mu);
     void* base = nullptr;
-    cudaError_t e = pool_alloc(&base, total, s);
+    cudaError_t e = cudaSuccess;
+    if (use_graph && total > d->gcap) {       // grow the graph's fixed scratch
+        if (d->gdone_valid) cudaEventSynchronize(d->gdone);
+        cudaFree(d->gscratch);
+        d->gscratch = nullptr;
+        d->gcap = 0;
+        d->last_bs.clear();                   // the old graph points into the old buffer
+        e = cudaMalloc(&d->gscratch, total);
+        if (e == cudaSuccess) d->gcap = total;
+    } else if (!use_graph) {
+        e = pool_alloc(&base, total, s);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();                  // consumed here: reported by the status below
         char buf[200];
         snprintf(buf, sizeof(buf), "hs_sign_mixed: scratch of %zu bytes: %s", total, cudaGetErrorString(e));
         return mx_fail(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA, buf);
     }
+    if (use_graph) base = d->gscratch;
     for (size_t j = 0; j < bs.size(); j++) {
         bs[j].status = status;
         carve_scratch(bs[j], static_cast<char*>(base) + off[j]);
     }
     {
-    std::lock_guard<std::mutex> lk(d->mu);
     if (use_graph) {
+        const std::vector<int> choice = launch_choices(bs);
+        if (d->exec && same_batches(bs, d->last_bs) && choice == d->last_choice) {
+            // the same batches as the last graph: relaunch it as it is
+            if (d->gdone_valid) e = cudaStreamWaitEvent(s, d->gdone, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(d->exec, s);
+            if (e == cudaSuccess) e = cudaEventRecord(d->gdone, s);
+            d->gdone_valid = e == cudaSuccess;
+            if (e == cudaSuccess) {
+                d->replays++;
+                return HS_OK;
+            }
+            char buf[200];
+            snprintf(buf, sizeof(buf), "hs_sign_mixed: %s", cudaGetErrorString(e));
+            cudaGetLastError();
+            return mx_fail(HS_ECUDA, buf);
+        }
         cudaGraph_t g = nullptr;
         // Capture on a library stream (the caller's may be the legacy default
         // stream, which cannot be captured); the graph is launched on 'stream'.
@@ -195,7 +256,16 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
             if (e == cudaSuccess) d->instantiations++;
             else d->exec = nullptr;
         }
+        if (e == cudaSuccess && d->gdone_valid) e = cudaStreamWaitEvent(s, d->gdone, 0);
         if (e == cudaSuccess) e = cudaGraphLaunch(d->exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(d->gdone, s);
+        d->gdone_valid = e == cudaSuccess;
+        if (e == cudaSuccess) {
+            d->last_bs = bs;
+            d->last_choice = choice;
+        } else {
+            d->last_bs.clear();
+        }
         if (g) cudaGraphDestroy(g);
     } else {
         e = enqueue_jobs(*d, bs, s);
@@ -205,8 +275,10 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
             for (size_t i = 0; i < 2 * bs.size(); i++) cudaStreamSynchronize(d->side[i]);
     }
     }
-    cudaError_t ef = cudaFreeAsync(base, s);
-    if (e == cudaSuccess) e = ef;
+    if (!use_graph) {
+        cudaError_t ef = cudaFreeAsync(base, s);
+        if (e == cudaSuccess) e = ef;
+    }
     if (e != cudaSuccess) {
         char buf[200];
         snprintf(buf, sizeof(buf), "hs_sign_mixed: %s", cudaGetErrorString(e));

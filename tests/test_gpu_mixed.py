@@ -75,3 +75,51 @@ def test_graph_reuse_across_calls(hs):
         torch.cuda.synchronize()
         for d, ref in zip(jobs, refs):
             assert torch.equal(d["sigs"], ref), (shape, seed, d["params"])
+
+
+def test_graph_relaunched_for_identical_calls(hs):
+    """Calls with the same batches relaunch the kept graph without capturing
+    it again; the bytes are exact each time, also when the inputs change in
+    place between calls, after a call of another shape, and when a tuning
+    choice changes (which captures the graph again)."""
+    import torch
+    from paper_2512_23969_gb300 import autotune
+
+    jobs, wls = [], []
+    for k, (ps, count) in enumerate((("128f", 9), ("256f", 3))):
+        wl = inputs.make(ps, count, num_keys=2, lengths=("uniform", 1, 300), seed=960 + k)
+        pk, sk = hs.hs_keygen(ps, _dev(wl.seeds))
+        jobs.append({"params": ps, "sk": sk, "msgs": _dev(wl.msgs), "lens": _dev(wl.lens),
+                     "key_idx": _dev(wl.key_idx), "num_keys": 2,
+                     "sigs": torch.zeros(count * hs.sig_bytes(ps), dtype=torch.uint8, device="cuda")})
+        wls.append(wl)
+
+    def refs():
+        return [hs.hs_sign_batch(d["params"], d["sk"], d["msgs"], d["lens"], key_idx=d["key_idx"], num_keys=2)
+                .view(-1).clone() for d in jobs]
+
+    def check(tag):
+        want = refs()
+        for d in jobs:
+            d["sigs"].zero_()
+        hs.hs_sign_mixed(jobs, use_graph=True)
+        torch.cuda.synchronize()
+        for d, w in zip(jobs, want):
+            assert torch.equal(d["sigs"], w), (tag, d["params"])
+
+    check("first")
+    check("relaunch")
+    jobs[0]["msgs"].add_(1)                       # new message bytes at the same addresses
+    check("new inputs")
+    saved = autotune.get("256f", "fors_lanes")
+    try:
+        autotune.set("256f", "fors_lanes", 8 if saved != 8 else 16)
+        check("other FORS lanes")
+    finally:
+        autotune.set("256f", "fors_lanes", saved)
+    other = inputs.make("toy", 5, num_keys=1, lengths=8, seed=970)
+    _, osk = hs.hs_keygen("toy", _dev(other.seeds))
+    hs.hs_sign_mixed([{"params": "toy", "sk": osk, "msgs": _dev(other.msgs), "lens": _dev(other.lens),
+                       "num_keys": 1, "sigs": torch.zeros(5 * hs.sig_bytes("toy"), dtype=torch.uint8,
+                                                         device="cuda")}], use_graph=True)
+    check("after another shape")
