@@ -823,11 +823,11 @@ def run_own(args):
     # the same workload through the plain per-stage kernels: no chain
     # checkpoints, so WOTS+_Sign recomputes every chain from its secret
     plain = None
-    if rank == 0:
+    if rank == 0 and args.plain_steps > 0:
         hs.hs_set_chain_checkpoint(0)
         try:
             hs.hs_profile_enable(True)
-            pms = _time_steps(step, stream, flush, max(3, args.steps // 2), 3)
+            pms = _time_steps(step, stream, flush, args.plain_steps, 3)
             pprof = hs.hs_profile_read()
             hs.hs_profile_enable(False)
         finally:
@@ -915,6 +915,8 @@ def main():
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--plain-steps", type=int, default=10,
+                    help="steps of the same workload with WOTS+_Sign recomputing its chains (0 = skip)")
     ap.add_argument("--ref-step-seconds", type=float, default=10.0)
     ap.add_argument("--params", default="128f",
                     choices=["128f", "192f", "256f", "128s", "192s", "256s", "shake-128f", "shake-192f", "shake-256f",
