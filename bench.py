@@ -907,7 +907,7 @@ def run_own(args):
 def main():
     import faulthandler
     faulthandler.enable()
-    faulthandler.dump_traceback_later(300, repeat=True)     # stacks on stderr if a stage stalls
+    faulthandler.dump_traceback_later(1200, repeat=True)    # stacks on stderr if a stage stalls
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)

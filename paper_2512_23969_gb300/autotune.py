@@ -33,13 +33,18 @@ STAGE_OF_KNOB = {"fors_lanes": ("fors",), "tree_policy": ("tree",), "tree_chains
                  "tree_min_blocks": ("tree",), "checkpoint": ("tree", "wots")}
 DEFAULT_COUNTS = {"128f": 16384, "192f": 8192, "256f": 8192, "toy": 4096, "128s": 512, "192s": 256, "256s": 256,
                   "shake-128f": 4096, "shake-192f": 2048, "shake-256f": 2048, "shake-128s": 256, "shake-192s": 256,
-                  "shake-256s": 256}
+                  "shake-256s": 256, "robust-128f": 8192, "robust-192f": 4096, "robust-256f": 4096}
 # batch sizes at which the two TREE_Sign forms are compared, per family
-SPLIT_COUNTS = {"f": (64, 256, 1024, 2048, 4096, 8192), "s": (8, 16, 32, 64, 128, 256),
-                "shake-f": (64, 256, 1024, 2048, 4096, 8192), "shake-s": (4, 8, 16, 32, 64, 128)}
+# (down to a few messages: the per-leaf form is latency-bound below one wave
+# of threads, so its time hardly falls with the batch while the chain-
+# parallel form's does)
+SPLIT_COUNTS = {"f": (8, 16, 32, 64, 128, 256, 1024, 2048, 4096, 8192), "s": (8, 16, 32, 64, 128, 256),
+                "shake-f": (8, 16, 32, 64, 128, 256, 1024, 2048, 4096, 8192), "shake-s": (4, 8, 16, 32, 64, 128)}
 
 
 def _family(ps):
+    if ps.startswith("robust-"):
+        ps = ps[len("robust-"):]
     base = ps[len("shake-"):] if ps.startswith("shake-") else ps
     fam = "s" if base.endswith("s") else "f"
     return ("shake-" + fam) if ps.startswith("shake-") else fam
@@ -177,7 +182,9 @@ def save(result, path=CACHE):
     if os.path.exists(path):
         with open(path) as f:
             data = json.load(f)
-    data.setdefault(device_key(), {}).update(result)      # keep the sets not tuned this time
+    entry = data.setdefault(device_key(), {})
+    for ps, knobs in result.items():                     # keep the sets and knobs not tuned this time
+        entry.setdefault(ps, {}).update(knobs)
     with open(path, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
 
@@ -202,7 +209,12 @@ def apply(path=CACHE):
 
 if __name__ == "__main__":
     import sys
-    sets = sys.argv[1:] or list(DEFAULT_COUNTS)
-    res = tune(sets)
+    args = sys.argv[1:]
+    if args and args[0] == "--split-only":     # re-measure only the TREE_Sign form threshold
+        sets = args[1:] or list(DEFAULT_COUNTS)
+        res = {ps: {"tree_split_below": tune_split(ps)} for ps in sets}
+    else:
+        sets = args or list(DEFAULT_COUNTS)
+        res = tune(sets)
     save(res)
     print(json.dumps(res, indent=1))

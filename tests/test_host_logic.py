@@ -88,9 +88,11 @@ def test_tuning_cache_merges_and_applies(tmp_path, monkeypatch):
     path = str(tmp_path / "tuned.json")
     autotune.save({"128f": {"fors_lanes": {"best": 4}}}, path)
     autotune.save({"192f": {"tree_min_blocks": {"best": 4}}}, path)       # another set: kept side by side
-    autotune.save({"128f": {"tree_split_below": {"best": 1024}}}, path)   # same set: replaced
+    autotune.save({"128f": {"tree_split_below": {"best": 1024}}}, path)   # same set, another knob: kept too
+    autotune.save({"128f": {"fors_lanes": {"best": 2}}}, path)            # same knob: replaced
     data = json.load(open(path))["TEST-DEVICE|sm103|152SM"]
-    assert set(data) == {"128f", "192f"} and data["128f"] == {"tree_split_below": {"best": 1024}}
+    assert set(data) == {"128f", "192f"}
+    assert data["128f"] == {"tree_split_below": {"best": 1024}, "fors_lanes": {"best": 2}}
     before = {(ps, k): autotune.get(ps, k) for ps in ("128f", "192f") for k in autotune.KNOBS}
     try:
         autotune.save({"128f": {"fors_lanes": {"best": 8}, "tree_split_below": {"best": 512}},
