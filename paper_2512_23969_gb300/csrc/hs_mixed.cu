@@ -44,6 +44,8 @@ struct MixedDev {
     void* gscratch = nullptr;
     size_t gcap = 0;
     cudaEvent_t gdone = nullptr;
+    cudaEvent_t gin = nullptr;          // the caller's stream up to the call
+    cudaStream_t glaunch = nullptr;     // graph launches (idle between calls)
     bool gdone_valid = false;
     std::vector<Batch> last_bs;
     std::vector<int> last_choice;
@@ -68,11 +70,13 @@ hs_status mixed_dev(MixedDev** out) {
     std::lock_guard<std::mutex> lk(g_mx_mu);
     MixedDev& d = g_mx[dev];
     if (!d.init) {
-        bool ok = cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking) == cudaSuccess;
+        bool ok = cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&d.glaunch, cudaStreamNonBlocking) == cudaSuccess;
         for (int i = 0; i < 2 * kMaxJobs && ok; i++)
             ok = cudaStreamCreateWithFlags(&d.side[i], cudaStreamNonBlocking) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&d.gdone, cudaEventDisableTiming) == cudaSuccess;
+             cudaEventCreateWithFlags(&d.gdone, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&d.gin, cudaEventDisableTiming) == cudaSuccess;
         for (int i = 0; i < kMaxJobs && ok; i++)
             ok = cudaEventCreateWithFlags(&d.msg[i], cudaEventDisableTiming) == cudaSuccess &&
                  cudaEventCreateWithFlags(&d.fors[i], cudaEventDisableTiming) == cudaSuccess &&
@@ -114,6 +118,22 @@ std::vector<int> launch_choices(const std::vector<Batch>& bs) {
 
 bool same_batches(const std::vector<Batch>& a, const std::vector<Batch>& b) {
     return a.size() == b.size() && (a.empty() || memcmp(a.data(), b.data(), a.size() * sizeof(Batch)) == 0);
+}
+
+// Launch the kept graph after the work queued on 'origin', and make origin
+// wait for it.  The graph goes to a library stream of its own (idle
+// between calls; it runs the graph launches in order, so each follows the
+// previous one's use of the scratch), fenced by events, rather than into
+// 'origin' itself: a graph launched behind other work in a busy stream
+// started ~0.14 ms later (96-message mixed batch after a 256 MB fill, 5.59
+// vs 5.44 ms for the same launches on plain streams).
+cudaError_t launch_graph(MixedDev& d, cudaStream_t origin) {
+    cudaError_t e = cudaEventRecord(d.gin, origin);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(d.glaunch, d.gin, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(d.exec, d.glaunch);
+    if (e == cudaSuccess) e = cudaEventRecord(d.gdone, d.glaunch);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, d.gdone, 0);
+    return e;
 }
 
 // Enqueue every job's stage DAG (fork from / join into 'origin').
@@ -219,9 +239,7 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
         const std::vector<int> choice = launch_choices(bs);
         if (d->exec && same_batches(bs, d->last_bs) && choice == d->last_choice) {
             // the same batches as the last graph: relaunch it as it is
-            if (d->gdone_valid) e = cudaStreamWaitEvent(s, d->gdone, 0);
-            if (e == cudaSuccess) e = cudaGraphLaunch(d->exec, s);
-            if (e == cudaSuccess) e = cudaEventRecord(d->gdone, s);
+            e = launch_graph(*d, s);
             d->gdone_valid = e == cudaSuccess;
             if (e == cudaSuccess) {
                 d->replays++;
@@ -256,9 +274,7 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
             if (e == cudaSuccess) d->instantiations++;
             else d->exec = nullptr;
         }
-        if (e == cudaSuccess && d->gdone_valid) e = cudaStreamWaitEvent(s, d->gdone, 0);
-        if (e == cudaSuccess) e = cudaGraphLaunch(d->exec, s);
-        if (e == cudaSuccess) e = cudaEventRecord(d->gdone, s);
+        if (e == cudaSuccess) e = launch_graph(*d, s);
         d->gdone_valid = e == cudaSuccess;
         if (e == cudaSuccess) {
             d->last_bs = bs;
