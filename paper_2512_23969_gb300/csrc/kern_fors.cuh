@@ -138,9 +138,11 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
     // -> 43.6 ms per 16384 / 8192 signatures).
     constexpr bool kCtx = !P::SHAKE && ((uint64_t)K << A) <= 65536u;
     ChainCtx cxs[kCtx ? 2 : 1];
+    MaskCtx<NW> mk;                                // robust sets: the leaf F masks
     if constexpr (kCtx) {
         chain_ctx<POL>(ms256, make_adrs(0, tree, T_FORS_PRF, kp, 0, 0), cxs[0], pp);
         chain_ctx<POL>(ms256, make_adrs(0, tree, T_FORS_TREE, kp, 0, 0), cxs[1], pp);
+        if constexpr (P::ROBUST) mask_ctx<POL, NW>(kb.pk_seed, make_adrs(0, tree, T_FORS_TREE, kp, 0, 0), mk, pp);
     }
     SibStack<R, RI, NW, (R <= 7)> stk;                 // left siblings, levels 0..R-1
     uint32_t node[NW];
@@ -162,7 +164,12 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
                     uint32_t xm[NW];
 #pragma unroll
                     for (int w = 0; w < NW; w++) xm[w] = node[w];
-                    if (s == 1) mask_regs<false, NW, NW>(kb.pk_seed, make_adrs(0, tree, T_FORS_TREE, kp, 0, g), xm);
+                    if (s == 1) {
+                        uint32_t m[NW];
+                        mask_step<POL, NW>(mk, g, m, pp);
+#pragma unroll
+                        for (int w = 0; w < NW; w++) xm[w] ^= m[w];
+                    }
                     chain_step<POL, NW>(cxs[s], ms256, g, xm, node, pp);
                 } else if constexpr (kCtx) {
                     chain_step<POL, NW>(cxs[s], ms256, g, node, node, pp);

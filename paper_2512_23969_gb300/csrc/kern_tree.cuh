@@ -117,6 +117,7 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
 #pragma unroll
         for (int w = 0; w < NW; w++) x[w] = skseed[w];
         ChainCtx cx;
+        MaskCtx<NW> mk;                          // robust sets: the chain's F masks
         // step 0: PRF(WOTS_PRF(kp, chain i, hash 0)) = chain position 0;
         // step s >= 1: F(WOTS_HASH(kp, chain i, hash s-1)) = position s.
 #pragma unroll 1
@@ -131,16 +132,17 @@ __device__ __forceinline__ void wots_leaf(const uint32_t* ms256, const uint32_t*
                     Adrs a = (s == 0) ? aprf : ahash;
                     a.w4 = i << 16;
                     chain_ctx<POL>(ms256, a, cx, pp);
+                    if (s == 1) mask_ctx<POL, NW>(pks, a, mk, pp);
                 }
                 // F steps hash x masked with their own address; PRF (s = 0) does not
                 uint32_t xm[NW];
 #pragma unroll
                 for (int w = 0; w < NW; w++) xm[w] = x[w];
                 if (s > 0) {
-                    Adrs ah = ahash;
-                    ah.w4 = i << 16;
-                    ah.half = s - 1u;
-                    mask_regs<false, NW, NW>(pks, ah, xm);
+                    uint32_t m[NW];
+                    mask_step<POL, NW>(mk, s - 1u, m, pp);
+#pragma unroll
+                    for (int w = 0; w < NW; w++) xm[w] ^= m[w];
                 }
                 chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, xm, x, pp);
             } else {
@@ -283,6 +285,7 @@ __global__ void __launch_bounds__(128) chains_kernel(const KeyBlock* __restrict_
     const uint32_t ck_mask = ck ? ck - 1u : 0u, ck_shift = ck ? (uint32_t)(__ffs(ck) - 1) : 0u;
     if (ck != 0 && l == sl) mychk = chk + (((size_t)m * P::D + j) * (size_t)LEN + i) * per_chain * NW;
     ChainCtx cx;
+    MaskCtx<NW> mk;                              // robust sets: the chain's F masks
 #pragma unroll 1
     for (uint32_t s = 0; s < 16; s++) {
         if constexpr (P::SHAKE) {
@@ -292,11 +295,17 @@ __global__ void __launch_bounds__(128) chains_kernel(const KeyBlock* __restrict_
             if (s <= 1) {
                 Adrs a = make_adrs(j, tree, s == 0 ? T_WOTS_PRF : T_WOTS_HASH, l, i, 0);
                 chain_ctx<POL>(ms256, a, cx, pp);
+                if (s == 1) mask_ctx<POL, NW>(kb.pk_seed, a, mk, pp);
             }
             uint32_t xm[NW];
 #pragma unroll
             for (int w = 0; w < NW; w++) xm[w] = x[w];
-            if (s > 0) mask_regs<false, NW, NW>(kb.pk_seed, make_adrs(j, tree, T_WOTS_HASH, l, i, s - 1u), xm);
+            if (s > 0) {
+                uint32_t mm[NW];
+                mask_step<POL, NW>(mk, s - 1u, mm, pp);
+#pragma unroll
+                for (int w = 0; w < NW; w++) xm[w] ^= mm[w];
+            }
             chain_step<POL, NW>(cx, ms256, s == 0 ? 0u : s - 1u, xm, x, pp);
         } else {
             if (s <= 1) {

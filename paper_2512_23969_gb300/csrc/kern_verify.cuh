@@ -199,10 +199,12 @@ __global__ void __launch_bounds__(128) vchain_kernel(const KeyBlock* __restrict_
                 hashF_p<P, POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, q), x, x, pp);
         } else if constexpr (P::ROBUST) {
             ChainCtx cx;
+            MaskCtx<NW> mk;
             const Adrs ah = make_adrs(j, tree, T_WOTS_HASH, kp, i, 0);
             chain_ctx<POL>(ms256, ah, cx, pp);
+            mask_ctx<POL, NW>(kb.pk_seed, ah, mk, pp);
 #pragma unroll 1
-            for (uint32_t q = digit; q < 15u; q++) chain_step_p<P, POL>(cx, ms256, ah, q, x, x, pp, kb.pk_seed);
+            for (uint32_t q = digit; q < 15u; q++) chain_step_p<P, POL>(cx, mk, ms256, q, x, x, pp);
         } else {
             ChainCtx cx;
             chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, 0), cx, pp);

@@ -91,12 +91,16 @@ __global__ void __launch_bounds__(256) wots_kernel(const KeyBlock* __restrict__ 
             for (uint32_t q = 0; q < digit; q++) hashF_p<P, POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, q), x, x, pp);
         } else if constexpr (P::ROBUST) {
         ChainCtx cx;
+        MaskCtx<NW> mk;
         chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_PRF, kp, i, 0), cx, pp);
         chain_step<POL, NW>(cx, ms256, 0u, x, x, pp);           // PRF: not masked
-        if (digit > 0) chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, 0), cx, pp);
+        if (digit > 0) {
+            const Adrs ah = make_adrs(j, tree, T_WOTS_HASH, kp, i, 0);
+            chain_ctx<POL>(ms256, ah, cx, pp);
+            mask_ctx<POL, NW>(kb.pk_seed, ah, mk, pp);
+        }
 #pragma unroll 1
-        for (uint32_t q = 0; q < digit; q++)
-            chain_step_p<P, POL>(cx, ms256, make_adrs(j, tree, T_WOTS_HASH, kp, i, 0), q, x, x, pp, kb.pk_seed);
+        for (uint32_t q = 0; q < digit; q++) chain_step_p<P, POL>(cx, mk, ms256, q, x, x, pp);
         } else {
         ChainCtx cx;
         chain_ctx<POL>(ms256, make_adrs(j, tree, T_WOTS_PRF, kp, i, 0), cx, pp);

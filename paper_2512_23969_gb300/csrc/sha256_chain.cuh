@@ -139,6 +139,99 @@ __device__ __forceinline__ void chain_ctx(const uint32_t ms[8], const Adrs& a, C
     x.c[4] = W[4];
 }
 
+// ---- robust F masks with a per-chain context --------------------------
+// The mask of a chain's F step q is MGF1-SHA-256(PK.seed || ADRSc(q), n)
+// block 0: message words 0 .. K-1 (K = NW + 5: PK.seed and the chain's
+// address up to the hash index) are the same for every step of the chain,
+// word K holds q, then the counter's low half and the pad, zeros, the
+// length.  So the state after rounds 0 .. K-1 and the fixed-word terms of
+// schedule words 16 .. 16 + K - 1 are computed once per chain, and a step
+// runs rounds K .. 63 (at n = 32 the length does not fit the block: a
+// second block of zeros and the length follows, whose whole schedule is a
+// compile-time constant).  Same bytes as mgf1_256_block.
+template <int NW>
+struct MaskCtx {
+    uint32_t s[8];
+    uint32_t c[NW + 5];
+};
+
+// Rounds [t0, t1) of a compression whose message words 0 .. K-1 are not
+// in W but folded into c[]: schedule word 16 + j takes its terms W[j],
+// sigma0(W[j + 1]) and W[j + 9] from c[j] wherever their index is below K.
+template <int POL, int K, int t0, int t1>
+struct RoundsPre {
+    __device__ static __forceinline__ void run(uint32_t v[8], uint32_t W[16], const uint32_t* c, const Pipes<POL>& p) {
+        constexpr int t = t0;
+        if constexpr (t >= 16 && t < 16 + K) {
+            constexpr int j = t - 16;
+            uint32_t w = s1_256(W[(t - 2) & 15]) + c[j];
+            if constexpr (j + 1 >= K) w += s0_256(W[(t - 15) & 15]);
+            if constexpr (j + 9 >= K) w += W[(t - 7) & 15];
+            W[t & 15] = w;
+        } else if constexpr (t >= 16) {
+            W[t & 15] = s1_256(W[(t - 2) & 15]) + W[(t - 7) & 15] + s0_256(W[(t - 15) & 15]) + W[t & 15];
+        }
+        round256<POL, t>(v, W[t & 15], p);
+        if constexpr (t0 + 1 < t1) RoundsPre<POL, K, t0 + 1, t1>::run(v, W, c, p);
+    }
+};
+
+template <int POL, int NW, int t>
+__device__ __forceinline__ void mask_ctx_rounds(uint32_t s[8], const uint32_t* W, const Pipes<POL>& p) {
+    round256<POL, t>(s, W[t], p);
+    if constexpr (t + 1 < NW + 5) mask_ctx_rounds<POL, NW, t + 1>(s, W, p);
+}
+
+// Context of the masks of one chain (a: its WOTS_HASH / FORS_TREE address;
+// only the half word varies between its steps).
+template <int POL, int NW>
+__device__ __forceinline__ void mask_ctx(const uint32_t* pks, const Adrs& a, MaskCtx<NW>& m, const Pipes<POL>& p) {
+    constexpr int K = NW + 5;
+    uint32_t W[K];
+#pragma unroll
+    for (int i = 0; i < NW; i++) W[i] = pks[i];
+    W[NW] = a.w0; W[NW + 1] = a.w1; W[NW + 2] = a.w2; W[NW + 3] = a.w3; W[NW + 4] = a.w4;
+    sha256_iv(m.s);
+    mask_ctx_rounds<POL, NW, 0>(m.s, W, p);
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        uint32_t c = W[j];
+        if (j + 1 < K) c += s0_256(W[j + 1]);
+        if (j + 9 < K) c += W[j + 9];
+        m.c[j] = c;
+    }
+}
+
+// The first NW words of the mask of the step whose half word is 'half'.
+template <int POL, int NW>
+__device__ __forceinline__ void mask_step(const MaskCtx<NW>& m, uint32_t half, uint32_t* out, const Pipes<POL>& p) {
+    constexpr int K = NW + 5;
+    constexpr uint32_t L = 4 * NW + 26;            // PK.seed || ADRSc || counter bytes
+    uint32_t W[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) W[i] = 0u;
+    W[K] = half << 16;                             // counter 0: its high half is 0
+    W[K + 1] = 0x8000u;                            // counter low half 0, then the pad byte
+    if constexpr (L + 9 <= 64) W[15] = L * 8;
+    uint32_t v[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = m.s[i];
+    RoundsPre<POL, K, K, 64>::run(v, W, m.c, p);
+    uint32_t st[8];
+    sha256_iv(st);
+#pragma unroll
+    for (int i = 0; i < 8; i++) st[i] += v[i];
+    if constexpr (L + 9 > 64) {                    // n = 32: zeros and the length
+        uint32_t W2[16];
+#pragma unroll
+        for (int i = 0; i < 15; i++) W2[i] = 0u;
+        W2[15] = L * 8;
+        sha256_compress_full(st, W2);
+    }
+#pragma unroll
+    for (int i = 0; i < NW; i++) out[i] = st[i];
+}
+
 // Message words 5..15 of a one-block call: low half of the last address word,
 // NW payload words at a 2-byte offset, 0x80 pad, zeros, bit length.
 template <int NW>
@@ -201,20 +294,18 @@ __device__ __forceinline__ void hashF_p(const uint32_t ms256[8], const Adrs& a, 
     }
 }
 
-// One chain step F(WOTS_HASH(.., hash q), x) with the chain's context: the
-// robust sets mask x with the step's own address first (a: the chain's
-// WOTS_HASH address; its half word is set to q here).
+// One chain step F(WOTS_HASH(.., hash q), x) with the chain's context; the
+// robust sets mask x first with the step's mask (mk: the chain's mask
+// context; unused by the other sets).
 template <class P, int POL>
-__device__ __forceinline__ void chain_step_p(const ChainCtx& cx, const uint32_t ms256[8], Adrs a, uint32_t q,
-                                             const uint32_t* x, uint32_t* out, const Pipes<POL>& pp,
-                                             const uint32_t* pks) {
+__device__ __forceinline__ void chain_step_p(const ChainCtx& cx, const MaskCtx<P::NW>& mk, const uint32_t ms256[8],
+                                             uint32_t q, const uint32_t* x, uint32_t* out, const Pipes<POL>& pp) {
     if constexpr (P::ROBUST) {
-        uint32_t xm[P::NW];
+        uint32_t m[P::NW];
+        mask_step<POL, P::NW>(mk, q, m, pp);
 #pragma unroll
-        for (int i = 0; i < P::NW; i++) xm[i] = x[i];
-        a.half = q;
-        mask_regs<false, P::NW, P::NW>(pks, a, xm);
-        chain_step<POL, P::NW>(cx, ms256, q, xm, out, pp);
+        for (int i = 0; i < P::NW; i++) m[i] ^= x[i];
+        chain_step<POL, P::NW>(cx, ms256, q, m, out, pp);
     } else {
         chain_step<POL, P::NW>(cx, ms256, q, x, out, pp);
     }
