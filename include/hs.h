@@ -252,6 +252,14 @@ hs_status hs_set_chain_checkpoint(uint32_t stride);
  *   HS_TUNE_CHECKPOINT      this set's chain checkpoint stride (0, 1, 2, 4,
  *                           8; see hs_set_chain_checkpoint, which sets every
  *                           set's stride at once)
+ *   HS_TUNE_TREE_STEP_US,   measured costs of the two TREE_Sign forms (0 =
+ *   HS_TUNE_TREE_SPLIT_NS   not measured): the per-leaf form's time for one
+ *                           warp per SM sub-partition, in us, and the
+ *                           chain-parallel form's time per message, in ns.
+ *                           At or above HS_TUNE_TREE_SPLIT_BELOW, a batch
+ *                           within four such per-leaf steps takes the form
+ *                           they predict faster (the per-leaf time grows in
+ *                           whole steps); any value >= 0 is accepted
  * TREE_Sign's per-leaf kernel is compiled for its default combination of
  * min blocks, policy and chains per thread, and for each alternative value
  * of one knob with the other two at their defaults (min blocks 0, the
@@ -264,7 +272,8 @@ hs_status hs_set_chain_checkpoint(uint32_t stride);
  */
 typedef enum {
     HS_TUNE_FORS_LANES = 0, HS_TUNE_TREE_MIN_BLOCKS = 1, HS_TUNE_TREE_SPLIT_BELOW = 2,
-    HS_TUNE_TREE_POLICY = 3, HS_TUNE_TREE_CHAINS = 4, HS_TUNE_CHECKPOINT = 5
+    HS_TUNE_TREE_POLICY = 3, HS_TUNE_TREE_CHAINS = 4, HS_TUNE_CHECKPOINT = 5,
+    HS_TUNE_TREE_STEP_US = 6, HS_TUNE_TREE_SPLIT_NS = 7
 } hs_tune_knob;
 int hs_tune_options(hs_params p, int knob, int32_t *values, int max);
 hs_status hs_tune_set(hs_params p, int knob, int32_t value);

@@ -25,7 +25,9 @@ import numpy as np
 from . import hs, inputs
 
 KNOBS = {"fors_lanes": 0, "tree_min_blocks": 1, "tree_split_below": 2, "tree_policy": 3, "tree_chains": 4,
-         "checkpoint": 5}
+         "checkpoint": 5, "tree_step_us": 6, "tree_split_ns": 7}
+# knobs whose values are measured quantities rather than compiled variants
+FREE_KNOBS = ("tree_split_below", "tree_step_us", "tree_split_ns")
 # the stages each knob changes, timed together; in tuning order (TREE_Sign's
 # policy and chains per thread before its min blocks: the alternatives of
 # each are compiled only with the other two at their defaults)
@@ -122,12 +124,52 @@ def _stage_ms(params, wl, sk, dev, sigs, stage, reps):
     return best
 
 
+def _shape(ps):
+    """(d, 2^h') of a set, for the per-leaf form's warp count."""
+    n = {"128f": (22, 8), "192f": (22, 8), "256f": (17, 16), "toy": (2, 4), "128s": (7, 512), "192s": (7, 512),
+         "256s": (8, 256)}
+    base = ps.split("-")[-1]
+    return n[base]
+
+
+def tune_tree_costs(ps, reps=3, verbose=True):
+    """The per-leaf TREE_Sign time of one step (a warp per SM sub-partition:
+    the per-leaf time grows in whole steps) and the chain-parallel time per
+    message, measured at one and at four steps' worth of messages."""
+    import torch
+    d, leaves = _shape(ps)
+    smsp = 4 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    one = max(1, (smsp * 32) // (d * leaves))
+    saved = get(ps, "tree_split_below")
+    set(ps, "tree_step_us", 0)
+    set(ps, "tree_split_ns", 0)
+    try:
+        wl, sk, dev, sigs = _batch(ps, one)
+        set(ps, "tree_split_below", 0)
+        leaf_ms = _stage_ms(ps, wl, sk, dev, sigs, "tree", reps)
+        wl, sk, dev, sigs = _batch(ps, 4 * one)
+        set(ps, "tree_split_below", 1 << 30)
+        split_ms = _stage_ms(ps, wl, sk, dev, sigs, "tree", reps)
+    finally:
+        set(ps, "tree_split_below", saved)
+    step_us, split_ns = int(round(leaf_ms * 1e3)), int(round(split_ms * 1e6 / (4 * one)))
+    set(ps, "tree_step_us", step_us)
+    set(ps, "tree_split_ns", split_ns)
+    if verbose:
+        print("tune %s tree costs: per-leaf step %d us (%d msgs), chain-parallel %d ns per message"
+              % (ps, step_us, one, split_ns), flush=True)
+    return {"tree_step_us": {"best": step_us, "messages": one},
+            "tree_split_ns": {"best": split_ns, "messages": 4 * one}}
+
+
 def tune_split(ps, counts=None, reps=3, verbose=True):
     """Batch size below which the chain-parallel TREE_Sign is faster: time
     the TREE stage in both forms at growing batch sizes."""
     counts = counts or SPLIT_COUNTS[_family(ps)]
     rows = {}
     below = 0
+    set(ps, "tree_step_us", 0)                 # forms forced by the threshold alone while timing
+    set(ps, "tree_split_ns", 0)
     for count in counts:
         wl, sk, dev, sigs = _batch(ps, count)
         ms = {}
@@ -155,6 +197,7 @@ def tune(params_list=("128f", "192f", "256f"), counts=None, reps=3, verbose=True
         ref = None
         result[ps] = {}
         result[ps]["tree_split_below"] = tune_split(ps, reps=reps, verbose=verbose)
+        result[ps].update(tune_tree_costs(ps, reps=reps, verbose=verbose))
         for knob in ("tree_min_blocks", "tree_chains"):   # 0 min blocks, 1 chain: every policy is compiled there
             try_set(ps, knob, options(ps, knob)[0])
         for knob, stage in STAGE_OF_KNOB.items():
@@ -196,13 +239,14 @@ def apply(path=CACHE):
     with open(path) as f:
         data = json.load(f)
     entry = data.get(device_key(), {})
-    order = ("tree_split_below", "fors_lanes", "tree_min_blocks", "tree_policy", "tree_chains", "checkpoint")
+    order = ("tree_split_below", "tree_step_us", "tree_split_ns", "fors_lanes", "tree_min_blocks", "tree_policy",
+             "tree_chains", "checkpoint")
     for ps, knobs in entry.items():
         if ps not in hs.PARAMS:
             continue
         for knob in order:                  # min blocks first: the others' alternatives need its default
             rec = knobs.get(knob)
-            if rec is not None and (knob == "tree_split_below" or rec.get("best") in options(ps, knob)):
+            if rec is not None and (knob in FREE_KNOBS or rec.get("best") in options(ps, knob)):
                 try_set(ps, knob, rec["best"])
     return entry
 
@@ -210,9 +254,9 @@ def apply(path=CACHE):
 if __name__ == "__main__":
     import sys
     args = sys.argv[1:]
-    if args and args[0] == "--split-only":     # re-measure only the TREE_Sign form threshold
+    if args and args[0] == "--split-only":     # re-measure only the TREE_Sign form choice
         sets = args[1:] or list(DEFAULT_COUNTS)
-        res = {ps: {"tree_split_below": tune_split(ps)} for ps in sets}
+        res = {ps: dict({"tree_split_below": tune_split(ps)}, **tune_tree_costs(ps)) for ps in sets}
     else:
         sets = args or list(DEFAULT_COUNTS)
         res = tune(sets)

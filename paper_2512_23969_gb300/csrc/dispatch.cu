@@ -56,7 +56,8 @@ int tune_get(int pset, int knob) {
     case 2: return kSplitDefault[pset];
     case 3: return o->tree_pol_default;
     case 4: return 1;
-    default: return g_ck_default.load();
+    case 5: return g_ck_default.load();
+    default: return 0;                  // 6, 7: no cost model
     }
 }
 
@@ -81,7 +82,8 @@ int tune_options(int pset, int knob, int32_t* values, int max) {
     case 2: for (int v : {0, 256, 512, 1024, 2048, 4096, 8192}) buf[n++] = v; break;   // suggestions: any value works
     case 3: for (int v : {7, 15}) if (o->tree_has(0, v, 1)) buf[n++] = v; break;
     case 4: for (int v : {1, 2}) if (o->tree_has(0, o->tree_pol_default, v)) buf[n++] = v; break;
-    default: for (int v : kStrides) buf[n++] = v; break;
+    case 5: for (int v : kStrides) buf[n++] = v; break;
+    default: buf[n++] = 0; break;       // 6, 7: measured coefficients, any value >= 0
     }
     for (int i = 0; i < n && i < max; i++)
         if (values) values[i] = buf[i];
@@ -90,7 +92,38 @@ int tune_options(int pset, int knob, int32_t* values, int max) {
 
 bool tree_split(int pset, uint32_t count) {
     const int below = tune_get(pset, 2);
-    return below > 0 && count < (uint32_t)below;
+    if (below > 0 && count < (uint32_t)below) return true;
+    // Above the threshold, the per-leaf form's time is a staircase: one
+    // warp per SM sub-partition already keeps the ALU pipe busy, so it
+    // takes about step_us x ceil(warps / sub-partitions), while the
+    // chain-parallel form's time grows with the batch (split_ns per
+    // message).  Within the first few steps, where a batch just past a step
+    // wastes most of its last one, take the form predicted faster.
+    const int step_us = tune_get(pset, 6), split_ns = tune_get(pset, 7);
+    SetShape sh{};
+    if (step_us <= 0 || split_ns <= 0 || !set_shape(pset, &sh)) return false;
+    const uint64_t warps = ((uint64_t)count * sh.d * sh.leaves + 31) / 32, smsp = 4ull * (uint64_t)sm_count();
+    const uint64_t steps = (warps + smsp - 1) / smsp;
+    if (steps > 4) return false;
+    return (uint64_t)split_ns * count < (uint64_t)step_us * 1000ull * steps;
+}
+
+// SM count of the current device (looked up once per device).
+int sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    int v = cache[dev].load();
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        return 152;
+    }
+    cache[dev].store(v);
+    return v;
 }
 
 int fors_lanes(int pset, uint32_t count) {
@@ -98,12 +131,7 @@ int fors_lanes(int pset, uint32_t count) {
     SetShape sh{};
     if (!o || !set_shape(pset, &sh)) return -1;
     int lpt = tune_get(pset, 0);
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-        cudaGetLastError();
-        sms = 152;
-    }
-    const uint64_t want = (uint64_t)sms * 1024;
+    const uint64_t want = (uint64_t)sm_count() * 1024;
     while ((uint64_t)count * sh.k * lpt < want) {
         int wider = 0;                    // smallest compiled value above lpt
         for (int i = 0; i < o->n_fors_lpt; i++)
@@ -117,9 +145,9 @@ int fors_lanes(int pset, uint32_t count) {
 bool tune_set(int pset, int knob, int value) {
     const SetOps* o = set_ops(pset);
     if (!o || knob < 0 || knob >= kNumKnobs) return false;
-    if (knob == 2) {                      // any batch-size threshold
+    if (knob == 2 || knob == 6 || knob == 7) {   // a batch-size threshold, cost coefficients
         if (value < 0) return false;
-        g_tune[pset][2].store(value);
+        g_tune[pset][knob].store(value);
         return true;
     }
     if (knob == 1 || knob == 3 || knob == 4) {   // a compiled TREE_Sign combination

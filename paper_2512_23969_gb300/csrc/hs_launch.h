@@ -138,8 +138,9 @@ const SetOps* set_ops(int pset);
 // Tuned launch shape per set (knob 0 = FORS lanes per tree, 1 = TREE min
 // blocks, 2 = batch size below which TREE_Sign runs chain-parallel, 3 =
 // TREE_Sign addition policy, 4 = TREE_Sign chains per thread, 5 = chain
-// checkpoint stride).
-constexpr int kNumKnobs = 6;
+// checkpoint stride, 6 = per-leaf TREE_Sign time of one warp per SM
+// sub-partition (us), 7 = chain-parallel TREE_Sign time per message (ns)).
+constexpr int kNumKnobs = 8;
 int tune_get(int pset, int knob);
 bool tune_set(int pset, int knob, int value);
 // Compiled values of a knob (returns how many; -1 for bad arguments).
@@ -147,6 +148,8 @@ int tune_options(int pset, int knob, int32_t* values, int max);
 // Process-wide checkpoint stride: the value of every set whose knob 5 is unset.
 void set_default_checkpoint(uint32_t stride);
 bool tree_split(int pset, uint32_t count);
+// SM count of the current device (cached per device).
+int sm_count();
 // Lanes per FORS tree for a batch of 'count' messages: the tuned value, or
 // for a batch too small to give the launch about 1024 threads per SM, the
 // next wider compiled lane groups (fewer leaves per lane, same bytes).
