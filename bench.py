@@ -317,7 +317,32 @@ def _time_steps(fn, stream, flush, steps, warmup):
     return ms
 
 
-def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
+def sha_mix_time_ms(c256, c512, mix, sm_count, mhz):
+    """Time the compressions would take at the SHA-mix peak (ms)."""
+    per_s = lambda rate: rate * sm_count * mhz * 1e6
+    return 1e3 * (c256 / per_s(mix["sha256_per_clk_sm"]) + (c512 / per_s(mix["sha512_per_clk_sm"]) if c512 else 0.0))
+
+
+def sha_mix_roofline(mix, sm_count, mhz, comps, count, ms, alu_rate):
+    """TREE_Sign against the SHA-mix peak: the scheme's compressions of one
+    launch (every chain step counted as a whole compression) at the probe's
+    rate, over the launch's measured time.  A kernel that shortens its
+    compressions (chain contexts, folded constant words) can exceed 1."""
+    out = {"probe": mix, "sm_mhz": mhz,
+           "c256_peak_per_s": round(mix["sha256_per_clk_sm"] * sm_count * mhz * 1e6, 1),
+           "c512_peak_per_s": round(mix["sha512_per_clk_sm"] * sm_count * mhz * 1e6, 1),
+           "alu_efficiency_of_mix": {
+               "sha256": round(mix["sha256_per_clk_sm"] * ALU_C256 / alu_rate, 4),
+               "sha512": round(mix["sha512_per_clk_sm"] * ALU_C512 / alu_rate, 4)},
+           "basis": "hs_probe_sha_mix: the signer's SHA-256 (64 rounds unrolled) and SHA-512 (16 rounds x 5) "
+                    "compressions back to back per thread, one full-occupancy wave, SM cycle counters"}
+    if comps and ms > 0:
+        ideal = sha_mix_time_ms(comps[0] * count, comps[1] * count, mix, sm_count, mhz)
+        out["tree_frac"] = round(ideal / ms, 4)
+    return out
+
+
+def measure_other_configs(hs, inputs, args, stream, flush, alu_peak, mix=None, sm_count=0, mhz=0.0):
     import torch
     res = {}
     dev = lambda x: torch.from_numpy(x).cuda()
@@ -354,6 +379,11 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak):
                        st: round(alu_ops_per_sig(ps, st) * wl.count / (prof[st] / 1e3) / 1e12 / alu_peak, 4)
                        for st in ("tree", "fors") if prof.get(st, 0) > 0} if not ps.startswith("robust-") else None),
                    "verified": int(ok.sum().item()) == wl.count}
+        if mix and ps in STAGE_WORK:
+            res[ps]["sha_mix_frac"] = {
+                st: round(sha_mix_time_ms(STAGE_WORK[ps][st][0] * wl.count, STAGE_WORK[ps][st][1] * wl.count,
+                                          mix, sm_count, mhz) / prof[st], 4)
+                for st in ("tree", "fors") if prof.get(st, 0) > 0}
     # the bench workload again with tree sharing on (same signatures, less work)
     log("128f with tree sharing")
     wl = inputs.config(1)
@@ -610,7 +640,7 @@ def summarize(line):
     r = line.get("roofline") or {}
     sm = {"sig_per_s": line.get("value"), "e2e_sig_per_s": (line.get("e2e") or {}).get("value"),
           "alu_frac_executed": r.get("frac"), "alu_frac_full_compression": r.get("frac_full_compression"),
-          "issue_frac": r.get("issue_frac")}
+          "issue_frac": r.get("issue_frac"), "sha_mix_frac": (r.get("sha_mix") or {}).get("tree_frac")}
     p = line.get("plain_per_stage") or {}
     sm["plain_per_stage_sig_per_s"] = p.get("value")
     sv = line.get("serving") or {}
@@ -632,6 +662,8 @@ def summarize(line):
     for ps in ("192f", "256f"):
         if isinstance(oc.get(ps), dict):
             sm[ps + "_sig_per_s"] = oc[ps].get("value")
+            if oc[ps].get("sha_mix_frac"):
+                sm[ps + "_sha_mix_frac"] = oc[ps]["sha_mix_frac"]
     return sm
 
 
@@ -818,6 +850,11 @@ def run_own(args):
                 "measured_pipes_lane_ops_per_clk_per_sm": pipes}
     if clk.get("sm_mhz") and achieved:
         roofline["frac_at_sampled_clock"] = round(achieved / (sm_count * alu_rate * clk["sm_mhz"] * 1e6 / 1e12), 4)
+    # the SHA-mix peak: compressions/s the signer's own SHA-2 code reaches on
+    # its own (hs_probe_sha_mix), at the SM clock sampled during the run
+    mix = hs.hs_probe_sha_mix()
+    mix_mhz = clk.get("sm_mhz") or sm_mhz_peak
+    roofline["sha_mix"] = sha_mix_roofline(mix, sm_count, mix_mhz, tree_c, count, tree_ms, alu_rate)
 
     # the same workload through the plain per-stage kernels: no chain
     # checkpoints, so WOTS+_Sign recomputes every chain from its secret
@@ -842,7 +879,7 @@ def run_own(args):
     others = {}
     if args.other_configs and rank == 0:
         try:
-            others = measure_other_configs(hs, inputs, args, stream, flush, alu_peak)
+            others = measure_other_configs(hs, inputs, args, stream, flush, alu_peak, mix, sm_count, mix_mhz)
         except Exception as exc:      # keep the main line; report what failed
             others = {"error": repr(exc)[:300]}
 

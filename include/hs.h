@@ -208,6 +208,21 @@ int hs_profile_read(float *ms, const char **names, int max);
  */
 int hs_probe_int_pipes(float *rates, int max);
 
+/*
+ * hs_probe_sha_mix -- measure the ceiling of the SHA-2 instruction mix
+ * itself on the current GPU, for the roofline's "SHA-mix peak" (the scheme's
+ * work is SHA-256 / SHA-512 compressions, FIPS 180-4 Sec. 6.2 / 6.4, and the
+ * signer does not depend on this call).  The signer's own compression
+ * functions run back to back on an independent state per thread, one wave
+ * of full-occupancy blocks, timed by SM cycle counters.  Writes up to 'max'
+ * rates: 0 SHA-256 compressions per clock per SM (all 64 rounds), 1 SHA-512
+ * compressions per clock per SM (80 rounds on 32-bit halves), 2 64-bit
+ * additions (two 32-bit halves and a carry) in lane-operations per clock
+ * per SM.  Synchronizes the device and allocates a few KB temporarily.
+ * Returns the number of rates written, or -1 on a CUDA error.
+ */
+int hs_probe_sha_mix(float *rates, int max);
+
 /* Number of kernels one hs_sign_batch call launches (for launch accounting). */
 int hs_sign_kernel_count(void);
 
@@ -260,6 +275,14 @@ hs_status hs_set_chain_checkpoint(uint32_t stride);
  *                           within four such per-leaf steps takes the form
  *                           they predict faster (the per-leaf time grows in
  *                           whole steps); any value >= 0 is accepted
+ *   HS_TUNE_MSG_WARP_BELOW  batches of fewer messages than this hash each
+ *                           message (PRF_msg, H_msg; Sec. II-A) with a whole
+ *                           warp: the message schedules of up to 32 blocks
+ *                           are computed at once, one block per lane, so a
+ *                           long message's serial hash runs only its rounds
+ *                           (SHA-2 sets; the SHAKE sets accept 0 only);
+ *                           0 = always a thread per message; any value >= 0
+ *                           is accepted
  * TREE_Sign's per-leaf kernel is compiled for its default combination of
  * min blocks, policy and chains per thread, and for each alternative value
  * of one knob with the other two at their defaults (min blocks 0, the
@@ -273,7 +296,7 @@ hs_status hs_set_chain_checkpoint(uint32_t stride);
 typedef enum {
     HS_TUNE_FORS_LANES = 0, HS_TUNE_TREE_MIN_BLOCKS = 1, HS_TUNE_TREE_SPLIT_BELOW = 2,
     HS_TUNE_TREE_POLICY = 3, HS_TUNE_TREE_CHAINS = 4, HS_TUNE_CHECKPOINT = 5,
-    HS_TUNE_TREE_STEP_US = 6, HS_TUNE_TREE_SPLIT_NS = 7
+    HS_TUNE_TREE_STEP_US = 6, HS_TUNE_TREE_SPLIT_NS = 7, HS_TUNE_MSG_WARP_BELOW = 8
 } hs_tune_knob;
 int hs_tune_options(hs_params p, int knob, int32_t *values, int max);
 hs_status hs_tune_set(hs_params p, int knob, int32_t value);

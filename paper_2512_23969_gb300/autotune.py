@@ -25,9 +25,9 @@ import numpy as np
 from . import hs, inputs
 
 KNOBS = {"fors_lanes": 0, "tree_min_blocks": 1, "tree_split_below": 2, "tree_policy": 3, "tree_chains": 4,
-         "checkpoint": 5, "tree_step_us": 6, "tree_split_ns": 7}
+         "checkpoint": 5, "tree_step_us": 6, "tree_split_ns": 7, "msg_warp_below": 8}
 # knobs whose values are measured quantities rather than compiled variants
-FREE_KNOBS = ("tree_split_below", "tree_step_us", "tree_split_ns")
+FREE_KNOBS = ("tree_split_below", "tree_step_us", "tree_split_ns", "msg_warp_below")
 # the stages each knob changes, timed together; in tuning order (TREE_Sign's
 # policy and chains per thread before its min blocks: the alternatives of
 # each are compiled only with the other two at their defaults)

@@ -43,6 +43,10 @@ std::atomic<int> g_ck_default{2};
 constexpr int kSplitDefault[kNumSets] = {8192, 2048, 4096, 0, 64, 64, 64, 8192, 2048, 4096, 64, 64, 64,
                                          8192, 2048, 4096};
 constexpr int kStrides[] = {0, 1, 2, 4, 8};
+// Default batch size below which the message stage runs a warp per message
+// (SHA-2 sets; the SHAKE sets always run a thread per message).
+constexpr int kMsgWarpDefault[kNumSets] = {512, 512, 512, 512, 512, 512, 512, 0, 0, 0, 0, 0, 0, 512, 512, 512};
+bool is_shake(int pset) { return pset >= 7 && pset <= 12; }
 }
 
 int tune_get(int pset, int knob) {
@@ -57,6 +61,7 @@ int tune_get(int pset, int knob) {
     case 3: return o->tree_pol_default;
     case 4: return 1;
     case 5: return g_ck_default.load();
+    case 8: return kMsgWarpDefault[pset];
     default: return 0;                  // 6, 7: no cost model
     }
 }
@@ -83,6 +88,10 @@ int tune_options(int pset, int knob, int32_t* values, int max) {
     case 3: for (int v : {7, 15}) if (o->tree_has(0, v, 1)) buf[n++] = v; break;
     case 4: for (int v : {1, 2}) if (o->tree_has(0, o->tree_pol_default, v)) buf[n++] = v; break;
     case 5: for (int v : kStrides) buf[n++] = v; break;
+    case 8:                             // suggestions: any value works (SHAKE sets: 0 only)
+        if (is_shake(pset)) buf[n++] = 0;
+        else for (int v : {0, 64, 256, 512, 1024, 4096}) buf[n++] = v;
+        break;
     default: buf[n++] = 0; break;       // 6, 7: measured coefficients, any value >= 0
     }
     for (int i = 0; i < n && i < max; i++)
@@ -145,8 +154,8 @@ int fors_lanes(int pset, uint32_t count) {
 bool tune_set(int pset, int knob, int value) {
     const SetOps* o = set_ops(pset);
     if (!o || knob < 0 || knob >= kNumKnobs) return false;
-    if (knob == 2 || knob == 6 || knob == 7) {   // a batch-size threshold, cost coefficients
-        if (value < 0) return false;
+    if (knob == 2 || knob == 6 || knob == 7 || knob == 8) {   // batch-size thresholds, cost coefficients
+        if (value < 0 || (knob == 8 && value > 0 && is_shake(pset))) return false;
         g_tune[pset][knob].store(value);
         return true;
     }

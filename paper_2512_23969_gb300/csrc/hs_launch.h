@@ -139,8 +139,9 @@ const SetOps* set_ops(int pset);
 // blocks, 2 = batch size below which TREE_Sign runs chain-parallel, 3 =
 // TREE_Sign addition policy, 4 = TREE_Sign chains per thread, 5 = chain
 // checkpoint stride, 6 = per-leaf TREE_Sign time of one warp per SM
-// sub-partition (us), 7 = chain-parallel TREE_Sign time per message (ns)).
-constexpr int kNumKnobs = 8;
+// sub-partition (us), 7 = chain-parallel TREE_Sign time per message (ns),
+// 8 = batch size below which the message stage runs a warp per message).
+constexpr int kNumKnobs = 9;
 int tune_get(int pset, int knob);
 bool tune_set(int pset, int knob, int value);
 // Compiled values of a knob (returns how many; -1 for bad arguments).

@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <vector>
 #include "../../include/hs.h"
+#include "sha2.cuh"
 
 #define HS_API extern "C" __attribute__((visibility("default")))
 
@@ -60,11 +61,121 @@ __global__ void __launch_bounds__(256) pipe_probe(int iters, uint32_t one, uint3
     }
 }
 
+// SHA-2 mix probes: the signer's own compression functions, run back to
+// back on an independent state per thread (a thread's next block is built
+// from its last result, so nothing is loop-invariant).  The rate is
+// compressions per clock per SM: the ceiling the SHA-2 instruction mix
+// itself reaches on this GPU, carry pairs and all, with no kernel overhead.
+// KIND 0: SHA-256, all 64 rounds unrolled (sha256_compress_full);
+// KIND 1: SHA-512, 16 rounds in a loop of 5 (sha512_compress);
+// KIND 2: 64-bit additions (add.u64, two 32-bit halves with a carry).
+template <int KIND>
+__global__ void __launch_bounds__(256) sha_probe(int iters, uint32_t seed, uint32_t* sink, long long* cyc,
+                                                 int* smid) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t s = 0;
+    __syncthreads();
+    const long long t0 = clock64();
+    if constexpr (KIND == 0) {
+        uint32_t st[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) st[i] = seed * (2u * i + 1u) + tid;
+        for (int it = 0; it < iters; it++) {
+            uint32_t W[16];
+#pragma unroll
+            for (int i = 0; i < 8; i++) { W[i] = st[i]; W[i + 8] = st[i] + 0x9e3779b9u * (i + 1); }
+            sha256_compress_full(st, W);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) s ^= st[i];
+    } else if constexpr (KIND == 1) {
+        uint64_t st[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) st[i] = ((uint64_t)(seed * (2u * i + 1u)) << 32) | (tid + i);
+        for (int it = 0; it < iters; it++) {
+            uint64_t W[16];
+#pragma unroll
+            for (int i = 0; i < 8; i++) { W[i] = st[i]; W[i + 8] = st[i] + 0x9e3779b97f4a7c15ull * (i + 1); }
+            sha512_compress(st, W);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) s ^= (uint32_t)st[i] ^ (uint32_t)(st[i] >> 32);
+    } else {
+        uint64_t a[8];
+        const uint64_t y = ((uint64_t)seed << 32) | (tid * 3u + 1u), z = y * 5u + 0x100000001ull;
+#pragma unroll
+        for (int i = 0; i < 8; i++) a[i] = y * (i + 7u);
+        for (int it = 0; it < iters; it++) {
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                asm volatile("add.u64 %0, %0, %1;" : "+l"(a[i]) : "l"(y));
+                asm volatile("add.u64 %0, %0, %1;" : "+l"(a[i]) : "l"(z));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) s ^= (uint32_t)a[i] ^ (uint32_t)(a[i] >> 32);
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    if (s == 0x12345678u) sink[0] = s;       // keeps the work alive; practically never stores
+    if (threadIdx.x == 0) {
+        cyc[blockIdx.x] = t1 - t0;
+        int id;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+        smid[blockIdx.x] = id;
+    }
+}
+
 template <int OP>
 cudaError_t run_probe(int blocks, int iters, uint32_t* sink, long long* cyc, int* smid) {
     pipe_probe<OP><<<blocks, 256>>>(iters, 1u, 7u, sink, cyc, smid);
     return cudaGetLastError();
 }
+
+template <int KIND>
+cudaError_t run_sha_probe(int blocks, int iters, uint32_t* sink, long long* cyc, int* smid) {
+    sha_probe<KIND><<<blocks, 256>>>(iters, 0x2512u, sink, cyc, smid);
+    return cudaGetLastError();
+}
+
+// Per-SM rate from one launch: the operations of an SM's blocks divided by
+// the longest of their cycle counts (all blocks of a launch are resident
+// at once), averaged over the SMs that ran blocks.
+float sm_rate(const std::vector<long long>& hc, const std::vector<int>& hs, double ops_per_block) {
+    std::vector<long long> maxc(1024, 0);
+    std::vector<int> nblk(1024, 0);
+    for (size_t b = 0; b < hc.size(); b++) {
+        const int s = hs[b] & 1023;
+        if (hc[b] > maxc[s]) maxc[s] = hc[b];
+        nblk[s]++;
+    }
+    double sum = 0;
+    int used = 0;
+    for (int s = 0; s < 1024; s++)
+        if (nblk[s] && maxc[s] > 0) { sum += ops_per_block * nblk[s] / (double)maxc[s]; used++; }
+    return used ? (float)(sum / used) : 0.f;
+}
+
+struct ProbeBufs {
+    uint32_t* sink = nullptr;
+    long long* cyc = nullptr;
+    int* smid = nullptr;
+    bool alloc(int blocks) {
+        return cudaMalloc(&sink, 64) == cudaSuccess && cudaMalloc(&cyc, sizeof(long long) * blocks) == cudaSuccess &&
+               cudaMalloc(&smid, sizeof(int) * blocks) == cudaSuccess;
+    }
+    ~ProbeBufs() {
+        if (sink) cudaFree(sink);
+        if (cyc) cudaFree(cyc);
+        if (smid) cudaFree(smid);
+    }
+    bool read(int blocks, std::vector<long long>& hc, std::vector<int>& hs) const {
+        hc.resize(blocks);
+        hs.resize(blocks);
+        return cudaMemcpy(hc.data(), cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost) == cudaSuccess &&
+               cudaMemcpy(hs.data(), smid, sizeof(int) * blocks, cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+};
 
 }  // namespace
 }  // namespace hs
@@ -79,48 +190,74 @@ HS_API int hs_probe_int_pipes(float* rates, int max) {
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
     const int blocks = sms * 8, iters = 2048;
-    uint32_t* sink = nullptr;
-    long long* cyc = nullptr;
-    int* smid = nullptr;
-    if (cudaMalloc(&sink, 64) != cudaSuccess) return -1;
-    if (cudaMalloc(&cyc, sizeof(long long) * blocks) != cudaSuccess) { cudaFree(sink); return -1; }
-    if (cudaMalloc(&smid, sizeof(int) * blocks) != cudaSuccess) { cudaFree(sink); cudaFree(cyc); return -1; }
-    std::vector<long long> hc(blocks);
-    std::vector<int> hs(blocks);
+    ProbeBufs pb;
+    if (!pb.alloc(blocks)) { cudaGetLastError(); return -1; }
+    std::vector<long long> hc;
+    std::vector<int> hs;
     int n = 0;
     cudaError_t e = cudaSuccess;
     for (int op = 0; op < 7 && n < max; op++) {
         for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {   // first run warms up
             switch (op) {
-            case 0: e = run_probe<0>(blocks, iters, sink, cyc, smid); break;
-            case 1: e = run_probe<1>(blocks, iters, sink, cyc, smid); break;
-            case 2: e = run_probe<2>(blocks, iters, sink, cyc, smid); break;
-            case 3: e = run_probe<3>(blocks, iters, sink, cyc, smid); break;
-            case 4: e = run_probe<4>(blocks, iters, sink, cyc, smid); break;
-            case 5: e = run_probe<5>(blocks, iters, sink, cyc, smid); break;
-            case 6: e = run_probe<6>(blocks, iters, sink, cyc, smid); break;
+            case 0: e = run_probe<0>(blocks, iters, pb.sink, pb.cyc, pb.smid); break;
+            case 1: e = run_probe<1>(blocks, iters, pb.sink, pb.cyc, pb.smid); break;
+            case 2: e = run_probe<2>(blocks, iters, pb.sink, pb.cyc, pb.smid); break;
+            case 3: e = run_probe<3>(blocks, iters, pb.sink, pb.cyc, pb.smid); break;
+            case 4: e = run_probe<4>(blocks, iters, pb.sink, pb.cyc, pb.smid); break;
+            case 5: e = run_probe<5>(blocks, iters, pb.sink, pb.cyc, pb.smid); break;
+            case 6: e = run_probe<6>(blocks, iters, pb.sink, pb.cyc, pb.smid); break;
             }
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
         }
-        if (e != cudaSuccess) break;
-        cudaMemcpy(hc.data(), cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost);
-        cudaMemcpy(hs.data(), smid, sizeof(int) * blocks, cudaMemcpyDeviceToHost);
-        std::vector<long long> maxc(1024, 0);
-        std::vector<int> nblk(1024, 0);
-        for (int b = 0; b < blocks; b++) {
-            const int s = hs[b] & 1023;
-            if (hc[b] > maxc[s]) maxc[s] = hc[b];
-            nblk[s]++;
-        }
-        const double ops_per_block = 256.0 * iters * 8 * 2;
-        double sum = 0;
-        int used = 0;
-        for (int s = 0; s < 1024; s++)
-            if (nblk[s] && maxc[s] > 0) { sum += ops_per_block * nblk[s] / (double)maxc[s]; used++; }
-        rates[n++] = used ? (float)(sum / used) : 0.f;
+        if (e != cudaSuccess || !pb.read(blocks, hc, hs)) break;
+        rates[n++] = sm_rate(hc, hs, 256.0 * iters * 8 * 2);
     }
-    cudaFree(sink);
-    cudaFree(cyc);
-    cudaFree(smid);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e == cudaSuccess ? n : -1;
+}
+
+// SHA-2 mix rates: 0 SHA-256 compressions, 1 SHA-512 compressions, per
+// clock per SM; 2 64-bit additions in lane-ops per clock per SM.  Each
+// probe's grid is one wave of its occupancy limit.  Synchronizes the
+// device; allocates and frees a small device buffer.  Returns the number
+// of rates written (<= max) or -1 on a CUDA error.
+HS_API int hs_probe_sha_mix(float* rates, int max) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    int per_sm[3] = {0, 0, 0};
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], sha_probe<0>, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], sha_probe<1>, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], sha_probe<2>, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    const int iters[3] = {96, 32, 2048};
+    const double ops[3] = {256.0 * iters[0], 256.0 * iters[1], 256.0 * iters[2] * 8 * 2};
+    int maxb = 0;
+    for (int k = 0; k < 3; k++) {
+        if (per_sm[k] < 1) per_sm[k] = 1;
+        if (sms * per_sm[k] > maxb) maxb = sms * per_sm[k];
+    }
+    ProbeBufs pb;
+    if (!pb.alloc(maxb)) { cudaGetLastError(); return -1; }
+    std::vector<long long> hc;
+    std::vector<int> hs;
+    int n = 0;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && n < max; k++) {
+        const int blocks = sms * per_sm[k];
+        for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {   // first run warms up
+            switch (k) {
+            case 0: e = run_sha_probe<0>(blocks, iters[k], pb.sink, pb.cyc, pb.smid); break;
+            case 1: e = run_sha_probe<1>(blocks, iters[k], pb.sink, pb.cyc, pb.smid); break;
+            case 2: e = run_sha_probe<2>(blocks, iters[k], pb.sink, pb.cyc, pb.smid); break;
+            }
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
+        if (e != cudaSuccess || !pb.read(blocks, hc, hs)) break;
+        rates[n++] = sm_rate(hc, hs, ops[k]);
+    }
+    if (e != cudaSuccess) cudaGetLastError();
     return e == cudaSuccess ? n : -1;
 }

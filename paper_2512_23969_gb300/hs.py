@@ -58,6 +58,8 @@ def load():
     L.hs_sign_batch_noalloc.restype = C.c_int
     L.hs_probe_int_pipes.argtypes = [C.POINTER(C.c_float), C.c_int]
     L.hs_probe_int_pipes.restype = C.c_int
+    L.hs_probe_sha_mix.argtypes = [C.POINTER(C.c_float), C.c_int]
+    L.hs_probe_sha_mix.restype = C.c_int
     L.hs_sign_mixed.argtypes = [C.c_void_p, C.c_uint32, C.c_int, C.c_void_p]
     L.hs_sign_mixed.restype = C.c_int
     L.hs_server_create.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]
@@ -381,6 +383,19 @@ def hs_probe_int_pipes():
     if n < 0:
         raise HSError(3, "hs_probe_int_pipes failed")
     return {PIPE_FORMS[i]: round(float(r[i]), 2) for i in range(n)}
+
+
+SHA_MIX_FORMS = ("sha256_per_clk_sm", "sha512_per_clk_sm", "add64_lane_ops_per_clk_sm")
+
+
+def hs_probe_sha_mix():
+    """{form: measured rate per clock per SM} of the SHA-2 instruction mix on
+    the current GPU: SHA-256 and SHA-512 compressions, and 64-bit additions."""
+    r = (C.c_float * 4)()
+    n = load().hs_probe_sha_mix(r, 4)
+    if n < 0:
+        raise HSError(3, "hs_probe_sha_mix failed")
+    return {SHA_MIX_FORMS[i]: round(float(r[i]), 5 if i < 2 else 2) for i in range(n)}
 
 
 class SignJob(C.Structure):
