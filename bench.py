@@ -134,6 +134,19 @@ def exec_alu_per_sig(ps, stage):
     return alu_ops_per_sig(ps, stage)
 
 
+def exec_split_per_sig(ps, stage):
+    """(SHA-256 ALU ops, SHA-512 blocks) per signature of a stage as the
+    kernels execute them: the SHA-256 part on the executed basis above, the
+    SHA-512 blocks (T_l, H, T_k at n = 24 / 32) whole."""
+    n, d, hp, a, k, length = SET_SHAPE[ps]
+    big = n > 16
+    total = exec_alu_per_sig(ps, stage)
+    if not big:
+        return total, 0
+    c512 = STAGE_WORK[ps][stage][1]
+    return total - c512 * ALU_C512, c512
+
+
 def ops_per_sig(ps, stage):
     if ps in KECCAK_WORK:          # Keccak is all ALU work: the two bases coincide
         return KECCAK_WORK[ps][stage] * ALU_KECCAK
@@ -317,28 +330,33 @@ def _time_steps(fn, stream, flush, steps, warmup):
     return ms
 
 
-def sha_mix_time_ms(c256, c512, mix, sm_count, mhz):
-    """Time the compressions would take at the SHA-mix peak (ms)."""
+def sha_mix_time_ms(ps, stage, count, mix, sm_count, mhz):
+    """Time a stage's executed SHA-2 work would take at the SHA-mix peak
+    (ms): its SHA-256 ALU ops in compression equivalents (1024 each) at the
+    probe's SHA-256 rate, its SHA-512 blocks at the probe's SHA-512 rate."""
     per_s = lambda rate: rate * sm_count * mhz * 1e6
-    return 1e3 * (c256 / per_s(mix["sha256_per_clk_sm"]) + (c512 / per_s(mix["sha512_per_clk_sm"]) if c512 else 0.0))
+    alu256, c512 = exec_split_per_sig(ps, stage)
+    return 1e3 * count * (alu256 / ALU_C256 / per_s(mix["sha256_per_clk_sm"]) +
+                          (c512 / per_s(mix["sha512_per_clk_sm"]) if c512 else 0.0))
 
 
-def sha_mix_roofline(mix, sm_count, mhz, comps, count, ms, alu_rate):
-    """TREE_Sign against the SHA-mix peak: the scheme's compressions of one
-    launch (every chain step counted as a whole compression) at the probe's
-    rate, over the launch's measured time.  A kernel that shortens its
-    compressions (chain contexts, folded constant words) can exceed 1."""
+def sha_mix_roofline(mix, sm_count, mhz, ps, count, ms, alu_rate):
+    """TREE_Sign against the SHA-mix peak: the time its executed SHA-2 work
+    takes at the rates the signer's own compression code reaches alone
+    (hs_probe_sha_mix), over the launch's measured time."""
     out = {"probe": mix, "sm_mhz": mhz,
            "c256_peak_per_s": round(mix["sha256_per_clk_sm"] * sm_count * mhz * 1e6, 1),
            "c512_peak_per_s": round(mix["sha512_per_clk_sm"] * sm_count * mhz * 1e6, 1),
            "alu_efficiency_of_mix": {
                "sha256": round(mix["sha256_per_clk_sm"] * ALU_C256 / alu_rate, 4),
-               "sha512": round(mix["sha512_per_clk_sm"] * ALU_C512 / alu_rate, 4)},
-           "basis": "hs_probe_sha_mix: the signer's SHA-256 (64 rounds unrolled) and SHA-512 (16 rounds x 5) "
-                    "compressions back to back per thread, one full-occupancy wave, SM cycle counters"}
-    if comps and ms > 0:
-        ideal = sha_mix_time_ms(comps[0] * count, comps[1] * count, mix, sm_count, mhz)
-        out["tree_frac"] = round(ideal / ms, 4)
+               "sha512": round(mix["sha512_per_clk_sm"] * ALU_C512 / alu_rate, 4),
+               "sha256_plain": round(mix.get("sha256_plain_per_clk_sm", 0.0) * ALU_C256 / alu_rate, 4)},
+           "basis": "hs_probe_sha_mix: the signer's SHA-256 round code (64 rounds unrolled, additions on "
+                    "IMAD) and SHA-512 compression (16 rounds x 5) back to back per thread, one "
+                    "full-occupancy wave, SM cycle counters; the kernel's executed work priced at those "
+                    "rates (chain steps as 926-942 / 1024 of a compression)"}
+    if ps in SET_SHAPE and ms > 0:
+        out["tree_frac"] = round(sha_mix_time_ms(ps, "tree", count, mix, sm_count, mhz) / ms, 4)
     return out
 
 
@@ -379,10 +397,9 @@ def measure_other_configs(hs, inputs, args, stream, flush, alu_peak, mix=None, s
                        st: round(alu_ops_per_sig(ps, st) * wl.count / (prof[st] / 1e3) / 1e12 / alu_peak, 4)
                        for st in ("tree", "fors") if prof.get(st, 0) > 0} if not ps.startswith("robust-") else None),
                    "verified": int(ok.sum().item()) == wl.count}
-        if mix and ps in STAGE_WORK:
+        if mix and ps in SET_SHAPE:
             res[ps]["sha_mix_frac"] = {
-                st: round(sha_mix_time_ms(STAGE_WORK[ps][st][0] * wl.count, STAGE_WORK[ps][st][1] * wl.count,
-                                          mix, sm_count, mhz) / prof[st], 4)
+                st: round(sha_mix_time_ms(ps, st, wl.count, mix, sm_count, mhz) / prof[st], 4)
                 for st in ("tree", "fors") if prof.get(st, 0) > 0}
     # the bench workload again with tree sharing on (same signatures, less work)
     log("128f with tree sharing")
@@ -854,7 +871,7 @@ def run_own(args):
     # its own (hs_probe_sha_mix), at the SM clock sampled during the run
     mix = hs.hs_probe_sha_mix()
     mix_mhz = clk.get("sm_mhz") or sm_mhz_peak
-    roofline["sha_mix"] = sha_mix_roofline(mix, sm_count, mix_mhz, tree_c, count, tree_ms, alu_rate)
+    roofline["sha_mix"] = sha_mix_roofline(mix, sm_count, mix_mhz, ps, count, tree_ms, alu_rate)
 
     # the same workload through the plain per-stage kernels: no chain
     # checkpoints, so WOTS+_Sign recomputes every chain from its secret

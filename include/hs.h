@@ -215,10 +215,13 @@ int hs_probe_int_pipes(float *rates, int max);
  * signer does not depend on this call).  The signer's own compression
  * functions run back to back on an independent state per thread, one wave
  * of full-occupancy blocks, timed by SM cycle counters.  Writes up to 'max'
- * rates: 0 SHA-256 compressions per clock per SM (all 64 rounds), 1 SHA-512
- * compressions per clock per SM (80 rounds on 32-bit halves), 2 64-bit
- * additions (two 32-bit halves and a carry) in lane-operations per clock
- * per SM.  Synchronizes the device and allocates a few KB temporarily.
+ * rates: 0 SHA-256 compressions per clock per SM (all 64 rounds, with the
+ * signer's round code: additions on the FMA pipe), 1 SHA-512 compressions
+ * per clock per SM (80 rounds on 32-bit halves), 2 64-bit additions (two
+ * 32-bit halves and a carry) in lane-operations per clock per SM, 3 SHA-256
+ * compressions per clock per SM as FIPS 180-4 writes them (every addition
+ * left to the compiler).  Synchronizes the device and allocates a few KB
+ * temporarily.
  * Returns the number of rates written, or -1 on a CUDA error.
  */
 int hs_probe_sha_mix(float *rates, int max);

@@ -186,6 +186,39 @@ def tune_split(ps, counts=None, reps=3, verbose=True):
     return {"best": below, "ms": rows}
 
 
+MSG_COUNTS = (64, 128, 256, 512, 1024, 2048, 4096)
+
+
+def tune_msg_warp(ps, counts=MSG_COUNTS, reps=3, verbose=True):
+    """Batch size below which the message stage runs a warp per message:
+    time the stage in both forms at growing batch sizes, with the serving
+    workload's lengths (log-uniform 16 B - 4 KB).  The SHAKE sets have only
+    the thread form (0)."""
+    import torch
+    if ps.startswith("shake-"):
+        set(ps, "msg_warp_below", 0)
+        return {"best": 0}
+    rows = {}
+    below = 0
+    for count in counts:
+        wl = inputs.make(ps, count, 16, ("loguniform", 16, 4096), 4343 + count)
+        pk, sk = hs.hs_keygen(ps, torch.from_numpy(wl.seeds).cuda())
+        dev = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("msgs", "lens", "key_idx")}
+        sigs = torch.empty(count * hs.sig_bytes(ps), dtype=torch.uint8, device="cuda")
+        ms = {}
+        for form, thr in (("warp", 1 << 30), ("thread", 0)):
+            set(ps, "msg_warp_below", thr)
+            ms[form] = _stage_ms(ps, wl, sk, dev, sigs, "message", reps)
+        rows[str(count)] = {k: round(v, 4) for k, v in ms.items()}
+        if verbose:
+            print("tune %s message form at %d: warp %.4f ms, thread %.4f ms" % (ps, count, ms["warp"], ms["thread"]),
+                  flush=True)
+        if ms["warp"] < ms["thread"]:
+            below = count * 2 if count == counts[-1] else counts[counts.index(count) + 1]
+    set(ps, "msg_warp_below", below)
+    return {"best": below, "ms": rows, "lengths": "log-uniform 16 B - 4 KB, 16 keys"}
+
+
 def tune(params_list=("128f", "192f", "256f"), counts=None, reps=3, verbose=True):
     """Time every compiled variant of every knob; apply and return the best
     ({params: {knob: {"best": v, "ms": {v: ms}}}})."""
@@ -198,6 +231,7 @@ def tune(params_list=("128f", "192f", "256f"), counts=None, reps=3, verbose=True
         result[ps] = {}
         result[ps]["tree_split_below"] = tune_split(ps, reps=reps, verbose=verbose)
         result[ps].update(tune_tree_costs(ps, reps=reps, verbose=verbose))
+        result[ps]["msg_warp_below"] = tune_msg_warp(ps, reps=reps, verbose=verbose)
         for knob in ("tree_min_blocks", "tree_chains"):   # 0 min blocks, 1 chain: every policy is compiled there
             try_set(ps, knob, options(ps, knob)[0])
         for knob, stage in STAGE_OF_KNOB.items():
@@ -240,7 +274,7 @@ def apply(path=CACHE):
         data = json.load(f)
     entry = data.get(device_key(), {})
     order = ("tree_split_below", "tree_step_us", "tree_split_ns", "fors_lanes", "tree_min_blocks", "tree_policy",
-             "tree_chains", "checkpoint")
+             "tree_chains", "checkpoint", "msg_warp_below")
     for ps, knobs in entry.items():
         if ps not in hs.PARAMS:
             continue
@@ -257,6 +291,9 @@ if __name__ == "__main__":
     if args and args[0] == "--split-only":     # re-measure only the TREE_Sign form choice
         sets = args[1:] or list(DEFAULT_COUNTS)
         res = {ps: dict({"tree_split_below": tune_split(ps)}, **tune_tree_costs(ps)) for ps in sets}
+    elif args and args[0] == "--msg-only":     # re-measure only the message stage's form choice
+        sets = args[1:] or list(DEFAULT_COUNTS)
+        res = {ps: {"msg_warp_below": tune_msg_warp(ps)} for ps in sets}
     else:
         sets = args or list(DEFAULT_COUNTS)
         res = tune(sets)

@@ -56,14 +56,22 @@ __device__ __forceinline__ void wk256_store(const uint32_t w[16], uint32_t* o) {
 }
 
 // The 64 SHA-256 rounds and the feed-forward, W_t + K_t read from wk.
+// Latency form: the new e is d + T1 = (d + h + W_t + K_t) + Sigma1(e) +
+// Ch(e, f, g), with the first sum formed before Sigma1 is ready (h and d
+// are known rounds ahead), so only one three-input addition follows
+// Sigma1 on the serial path; the empty asm keeps the compiler from folding
+// that sum back into d + T1.  Measured 13 % faster than d + T1 in the warp
+// form; the same restructuring made the SHA-512 rounds 8 % slower.
 __device__ __forceinline__ void rounds256_wk(uint32_t st[8], const uint32_t* wk) {
     uint32_t a = st[0], b = st[1], c = st[2], d = st[3], e = st[4], f = st[5], g = st[6], h = st[7];
 #define HS_RW256(a, b, c, d, e, f, g, h, x)                         \
     do {                                                            \
-        const uint32_t t1_ = h + S1_256(e) + ch32(e, f, g) + (x);   \
-        const uint32_t t2_ = S0_256(a) + maj32(a, b, c);            \
-        d += t1_;                                                   \
-        h = t1_ + t2_;                                              \
+        const uint32_t hx_ = h + (x);                               \
+        uint32_t dhx_ = d + hx_;                                    \
+        asm("" : "+r"(dhx_));                                       \
+        const uint32_t s1_ = S1_256(e), ch_ = ch32(e, f, g);        \
+        d = dhx_ + s1_ + ch_;                                       \
+        h = (hx_ + s1_ + ch_) + S0_256(a) + maj32(a, b, c);         \
     } while (0)
 #pragma unroll
     for (int t = 0; t < 64; t += 8) {

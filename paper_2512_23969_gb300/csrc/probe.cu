@@ -12,6 +12,7 @@
 #include <vector>
 #include "../../include/hs.h"
 #include "sha2.cuh"
+#include "sha256_chain.cuh"
 
 #define HS_API extern "C" __attribute__((visibility("default")))
 
@@ -66,17 +67,34 @@ __global__ void __launch_bounds__(256) pipe_probe(int iters, uint32_t one, uint3
 // from its last result, so nothing is loop-invariant).  The rate is
 // compressions per clock per SM: the ceiling the SHA-2 instruction mix
 // itself reaches on this GPU, carry pairs and all, with no kernel overhead.
-// KIND 0: SHA-256, all 64 rounds unrolled (sha256_compress_full);
+// KIND 0: SHA-256 with the signer's round code (all 64 rounds unrolled,
+//         round additions on IMAD: Rounds256 with the chain policy);
 // KIND 1: SHA-512, 16 rounds in a loop of 5 (sha512_compress);
-// KIND 2: 64-bit additions (add.u64, two 32-bit halves with a carry).
+// KIND 2: 64-bit additions (add.u64, two 32-bit halves with a carry);
+// KIND 3: SHA-256 as FIPS 180-4 writes it (sha256_compress_full).
 template <int KIND>
-__global__ void __launch_bounds__(256) sha_probe(int iters, uint32_t seed, uint32_t* sink, long long* cyc,
-                                                 int* smid) {
+__global__ void __launch_bounds__(256) sha_probe(int iters, uint32_t seed, uint32_t one, uint32_t* sink,
+                                                 long long* cyc, int* smid) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t s = 0;
     __syncthreads();
     const long long t0 = clock64();
     if constexpr (KIND == 0) {
+        const Pipes<kChainPol> pp(one);
+        uint32_t st[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) st[i] = seed * (2u * i + 1u) + tid;
+        for (int it = 0; it < iters; it++) {
+            uint32_t W[16], v[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) { W[i] = st[i]; W[i + 8] = st[i] + 0x9e3779b9u * (i + 1); v[i] = st[i]; }
+            Rounds256<kChainPol, false, 0, 64>::run(v, W, nullptr, pp);
+#pragma unroll
+            for (int i = 0; i < 8; i++) st[i] += v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) s ^= st[i];
+    } else if constexpr (KIND == 3) {
         uint32_t st[8];
 #pragma unroll
         for (int i = 0; i < 8; i++) st[i] = seed * (2u * i + 1u) + tid;
@@ -134,7 +152,7 @@ cudaError_t run_probe(int blocks, int iters, uint32_t* sink, long long* cyc, int
 
 template <int KIND>
 cudaError_t run_sha_probe(int blocks, int iters, uint32_t* sink, long long* cyc, int* smid) {
-    sha_probe<KIND><<<blocks, 256>>>(iters, 0x2512u, sink, cyc, smid);
+    sha_probe<KIND><<<blocks, 256>>>(iters, 0x2512u, 1u, sink, cyc, smid);
     return cudaGetLastError();
 }
 
@@ -216,8 +234,9 @@ HS_API int hs_probe_int_pipes(float* rates, int max) {
     return e == cudaSuccess ? n : -1;
 }
 
-// SHA-2 mix rates: 0 SHA-256 compressions, 1 SHA-512 compressions, per
-// clock per SM; 2 64-bit additions in lane-ops per clock per SM.  Each
+// SHA-2 mix rates: 0 SHA-256 compressions (the signer's round code), 1
+// SHA-512 compressions, per clock per SM; 2 64-bit additions in lane-ops
+// per clock per SM; 3 SHA-256 compressions as FIPS 180-4 writes them.  Each
 // probe's grid is one wave of its occupancy limit.  Synchronizes the
 // device; allocates and frees a small device buffer.  Returns the number
 // of rates written (<= max) or -1 on a CUDA error.
@@ -225,17 +244,19 @@ HS_API int hs_probe_sha_mix(float* rates, int max) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-    int per_sm[3] = {0, 0, 0};
+    constexpr int kKinds = 4;
+    int per_sm[kKinds] = {0, 0, 0, 0};
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], sha_probe<0>, 256, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], sha_probe<1>, 256, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], sha_probe<2>, 256, 0) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], sha_probe<2>, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[3], sha_probe<3>, 256, 0) != cudaSuccess) {
         cudaGetLastError();
         return -1;
     }
-    const int iters[3] = {96, 32, 2048};
-    const double ops[3] = {256.0 * iters[0], 256.0 * iters[1], 256.0 * iters[2] * 8 * 2};
+    const int iters[kKinds] = {96, 32, 2048, 96};
+    const double ops[kKinds] = {256.0 * iters[0], 256.0 * iters[1], 256.0 * iters[2] * 8 * 2, 256.0 * iters[3]};
     int maxb = 0;
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < kKinds; k++) {
         if (per_sm[k] < 1) per_sm[k] = 1;
         if (sms * per_sm[k] > maxb) maxb = sms * per_sm[k];
     }
@@ -245,13 +266,14 @@ HS_API int hs_probe_sha_mix(float* rates, int max) {
     std::vector<int> hs;
     int n = 0;
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 3 && n < max; k++) {
+    for (int k = 0; k < kKinds && n < max; k++) {
         const int blocks = sms * per_sm[k];
         for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {   // first run warms up
             switch (k) {
             case 0: e = run_sha_probe<0>(blocks, iters[k], pb.sink, pb.cyc, pb.smid); break;
             case 1: e = run_sha_probe<1>(blocks, iters[k], pb.sink, pb.cyc, pb.smid); break;
             case 2: e = run_sha_probe<2>(blocks, iters[k], pb.sink, pb.cyc, pb.smid); break;
+            case 3: e = run_sha_probe<3>(blocks, iters[k], pb.sink, pb.cyc, pb.smid); break;
             }
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
         }

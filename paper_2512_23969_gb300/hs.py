@@ -385,17 +385,18 @@ def hs_probe_int_pipes():
     return {PIPE_FORMS[i]: round(float(r[i]), 2) for i in range(n)}
 
 
-SHA_MIX_FORMS = ("sha256_per_clk_sm", "sha512_per_clk_sm", "add64_lane_ops_per_clk_sm")
+SHA_MIX_FORMS = ("sha256_per_clk_sm", "sha512_per_clk_sm", "add64_lane_ops_per_clk_sm", "sha256_plain_per_clk_sm")
 
 
 def hs_probe_sha_mix():
     """{form: measured rate per clock per SM} of the SHA-2 instruction mix on
-    the current GPU: SHA-256 and SHA-512 compressions, and 64-bit additions."""
+    the current GPU: SHA-256 (the signer's round code) and SHA-512
+    compressions, 64-bit additions, and SHA-256 as FIPS 180-4 writes it."""
     r = (C.c_float * 4)()
     n = load().hs_probe_sha_mix(r, 4)
     if n < 0:
         raise HSError(3, "hs_probe_sha_mix failed")
-    return {SHA_MIX_FORMS[i]: round(float(r[i]), 5 if i < 2 else 2) for i in range(n)}
+    return {SHA_MIX_FORMS[i]: round(float(r[i]), 2 if i == 2 else 5) for i in range(n)}
 
 
 class SignJob(C.Structure):

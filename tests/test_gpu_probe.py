@@ -25,7 +25,9 @@ def test_sha_mix_rates_respect_the_alu_pipe(hs):
     r = hs.hs_probe_sha_mix()
     assert set(r) == set(hs.SHA_MIX_FORMS)
     c256, c512, add64 = r["sha256_per_clk_sm"], r["sha512_per_clk_sm"], r["add64_lane_ops_per_clk_sm"]
-    assert 0 < c256 * 1024 <= 1.05 * alu, (c256, alu)
+    plain = r["sha256_plain_per_clk_sm"]
+    for rate in (c256, plain):
+        assert 0 < rate * 1024 <= 1.05 * alu, (rate, alu)
     assert 0 < c512 * 2624 <= 1.05 * alu, (c512, alu)
     assert c512 < c256
     assert 1.0 < add64 <= 130.0, add64
