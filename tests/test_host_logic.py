@@ -201,3 +201,21 @@ def test_checkpoint_stride_per_set_and_process_wide():
         assert not autotune.try_set("128f", "checkpoint", 3)
     finally:
         hs.hs_set_chain_checkpoint(2)
+
+
+def test_message_form_knob():
+    """HS_TUNE_MSG_WARP_BELOW: any threshold >= 0 for the SHA-2 sets (a warp
+    per message below it), 0 only for the SHAKE sets, whose message stage has
+    only the thread form.  No CUDA call is made."""
+    assert autotune.get("128f", "msg_warp_below") in autotune.options("128f", "msg_warp_below")
+    assert autotune.options("shake-128f", "msg_warp_below") == [0]
+    assert autotune.get("shake-256s", "msg_warp_below") == 0
+    saved = autotune.get("192f", "msg_warp_below")
+    try:
+        autotune.set("192f", "msg_warp_below", 777)          # not a listed suggestion: still accepted
+        assert autotune.get("192f", "msg_warp_below") == 777
+        assert not autotune.try_set("192f", "msg_warp_below", -1)
+        assert not autotune.try_set("shake-192f", "msg_warp_below", 64)
+        autotune.set("shake-192f", "msg_warp_below", 0)
+    finally:
+        autotune.set("192f", "msg_warp_below", saved)
