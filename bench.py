@@ -684,6 +684,17 @@ def summarize(line):
     return sm
 
 
+def run_probe_only():
+    """The roofline's peak probes alone (hs_probe_int_pipes, hs_probe_sha_mix):
+    one JSON line of per-clock-per-SM rates."""
+    from paper_2512_23969_gb300 import build as hs_build
+    hs_build.build()
+    from paper_2512_23969_gb300 import hs
+    hs.load()
+    print(json.dumps({"int_pipes_lane_ops_per_clk_sm": hs.hs_probe_int_pipes(), "sha_mix": hs.hs_probe_sha_mix()}))
+    return 0
+
+
 def run_verify_only(args):
     """Verification of the bench batch: 1 signing call, then 3 timed
     hs_verify_batch calls (CUDA events); prints one JSON line."""
@@ -985,6 +996,8 @@ def main():
                     help="p99 latency bound that defines the sustained serving capacity")
     ap.add_argument("--verify-only", action="store_true",
                     help="sign the batch once, then time hs_verify_batch on it (3 calls) and print one line")
+    ap.add_argument("--probe-only", action="store_true",
+                    help="run the integer-pipe and SHA-2 mix probes only and print one line (profiler captures)")
     ap.add_argument("--count", type=int, default=16384,
                     help="messages per step (smaller counts are for profiler captures)")
     args = ap.parse_args()
@@ -994,6 +1007,8 @@ def main():
         return run_reference(args)
     if args.verify_only:
         return run_verify_only(args)
+    if args.probe_only:
+        return run_probe_only()
     return run_own(args)
 
 
