@@ -1,5 +1,6 @@
 // dispatch.cu -- routes each launch to the parameter set's table with the
 // tuned launch shape (see hs_tune_set in include/hs.h).
+#include <algorithm>
 #include <atomic>
 #include "hs_launch.h"
 
@@ -115,6 +116,10 @@ bool tree_split(int pset, uint32_t count) {
     const uint64_t steps = (warps + smsp - 1) / smsp;
     if (steps > 4) return false;
     return (uint64_t)split_ns * count < (uint64_t)step_us * 1000ull * steps;
+}
+
+bool msg_warp(int pset, uint32_t count) {
+    return !is_shake(pset) && count < (uint32_t)std::max(0, tune_get(pset, 8));
 }
 
 // SM count of the current device (looked up once per device).

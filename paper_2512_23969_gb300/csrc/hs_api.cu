@@ -493,6 +493,7 @@ static hs_status run_batch(const hs_keyset* ks, bool verify, hs_params p, const 
     b.status = d->status;
     b.ck = verify ? 0u : (ks ? ks->ck : chain_checkpoint_stride(p));
     b.split = !verify && tree_split(p, count);
+    b.msg_warp = msg_warp(p, count);
     b.verify = verify;
     if (ks && ks->layers) {
         b.dedup_layer = ks->first_layer;

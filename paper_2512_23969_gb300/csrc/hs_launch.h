@@ -68,6 +68,9 @@ struct Batch {
     const uint8_t* prefix;    // device, prefix_len bytes
     uint32_t prefix_len;
     uint32_t* status;         // per-device status word
+    // message stage: a warp per message (SHA-2 sets, small batches; the
+    // form is fixed with the batch, like 'split')
+    bool msg_warp;
 };
 
 // Record the text hs_last_error() returns on the calling thread.
@@ -149,6 +152,8 @@ int tune_options(int pset, int knob, int32_t* values, int max);
 // Process-wide checkpoint stride: the value of every set whose knob 5 is unset.
 void set_default_checkpoint(uint32_t stride);
 bool tree_split(int pset, uint32_t count);
+// Whether a batch's message stage runs a warp per message (knob 8).
+bool msg_warp(int pset, uint32_t count);
 // SM count of the current device (cached per device).
 int sm_count();
 // Lanes per FORS tree for a batch of 'count' messages: the tuned value, or

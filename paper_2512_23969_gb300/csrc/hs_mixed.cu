@@ -198,6 +198,7 @@ HS_API hs_status hs_sign_mixed(const hs_sign_job* jobs, uint32_t njobs, int use_
         b.sigs = jb.sigs;
         b.ck = chain_checkpoint_stride(b.pset);
         b.split = tree_split(b.pset, b.count);
+        b.msg_warp = msg_warp(b.pset, b.count);
         plan_dedup(b);
         bs.push_back(b);
         off.push_back(total);

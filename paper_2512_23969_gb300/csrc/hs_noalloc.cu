@@ -122,6 +122,7 @@ HS_API hs_status hs_sign_batch_noalloc(hs_params p, const uint8_t* sk, uint32_t 
     b.sigs = sigs;
     b.ck = 0;
     b.split = split;
+    b.msg_warp = msg_warp(p, count);
     // Key-index errors go to the status word hs_check_status reads when the
     // library has already set it up on this device (by any earlier call);
     // otherwise to a word at the start of the array, which nothing reads.

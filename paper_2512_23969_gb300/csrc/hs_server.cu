@@ -225,6 +225,14 @@ bool admit(ServerImpl& sv, Slot& slot) {
     size_t pending_all = 0;
     for (int q = 0; q < kNumSets; q++) pending_all += sv.pending[q].size();
     const size_t share = std::max<size_t>(kMinShare, pending_all / sv.cfg.max_inflight);
+    // The message stage's warp form (a warp per message) only for a batch
+    // that has the GPU to itself: it shortens a small batch's serial message
+    // hashing when the GPU is otherwise idle, but in a server whose batches
+    // overlap it measured worse at high load (the serving mix at 85k
+    // requests/s: p99 17.5-18.0 ms with it, 11.6-12.2 ms without; at 75k
+    // 4.3 vs 4.6 ms).
+    bool alone = true;
+    for (const Slot& o : sv.slots) alone = alone && (&o == &slot || !o.busy);
     // take requests while the cumulative need fits what the arenas could give
     size_t count = 0, msg_bytes = 0;
     const size_t limit = std::min<size_t>(std::min<size_t>(sv.cfg.max_batch, share), sv.pending[p].size());
@@ -288,6 +296,7 @@ bool admit(ServerImpl& sv, Slot& slot) {
         b.cache_tpk = ks->tpk;
     }
     b.split = tree_split(p, (uint32_t)count);
+    b.msg_warp = alone && msg_warp(p, (uint32_t)count);
     b.status = device_status_word();
     carve_scratch(b, d + o_scr);
     b.keys = ks->kb;                              // resident midstates, not scratch

@@ -31,7 +31,7 @@ struct SetImpl {
     }
     static cudaError_t message(const Batch& b, bool verify, cudaStream_t s) {
         if constexpr (!P::SHAKE) {
-            if (b.count < (uint32_t)tune_get(b.pset, 8)) {     // a warp per message
+            if (b.msg_warp) {                               // a warp per message
                 const uint32_t T = 32 * kMsgWarpsPerBlock, G = (b.count + kMsgWarpsPerBlock - 1) / kMsgWarpsPerBlock;
                 message_warp_kernel<P><<<G, T, 0, s>>>(b.keys, b.num_keys, b.key_idx, b.msgs, b.offsets, b.count,
                                                        b.sigs, b.infos, b.status, verify ? 1 : 0, b.prefix,
