@@ -285,7 +285,9 @@ hs_status hs_set_chain_checkpoint(uint32_t stride);
  *                           long message's serial hash runs only its rounds
  *                           (SHA-2 sets; the SHAKE sets accept 0 only);
  *                           0 = always a thread per message; any value >= 0
- *                           is accepted
+ *                           is accepted.  The server (hs_server_*) takes this
+ *                           form only for a batch with no other batch of
+ *                           its own in flight
  * TREE_Sign's per-leaf kernel is compiled for its default combination of
  * min blocks, policy and chains per thread, and for each alternative value
  * of one knob with the other two at their defaults (min blocks 0, the
