@@ -95,12 +95,13 @@ KECCAK_WORK = {"shake-128f": _keccak_work(16, 22, 3, 6, 33, 35), "shake-192f": _
 # every compression in full; the signing kernels skip part of it, bit for
 # bit the same result:
 #  * a WOTS+ chain step (and a FORS leaf PRF / F where k 2^a <= 2^16) takes
-#    its state after rounds 0..4 and sigma0 of message words 1..4 from a
-#    context computed once per chain (per hash type), and runs rounds 5..63;
+#    its state after rounds 0..4, round 5 up to its message word, and sigma0
+#    of message words 1..4 from a context computed once per chain (per hash
+#    type), and runs rounds 6..63;
 #  * its message words 6 + n/4 .. 14 are zero and word 15 is a constant, so
 #    their sigma0 / sigma1 terms fold away in the unrolled schedule.
-# So one such step costs 59 x 10 + 4 x (46 sigma1 + 34 + n/4 sigma0) ALU
-# ops, and a chain 2 contexts (5 x 10 + 4 x 4 each) plus 16 steps.  T_l, H
+# So one such step costs 58 x 10 + 4 x (46 sigma1 + 34 + n/4 sigma0) ALU
+# ops, and a chain 2 contexts (6 x 10 + 4 x 4 each) plus 16 steps.  T_l, H
 # and T_k run the rolled compression in full (1024 / 2624 per block).
 SET_SHAPE = {  # n, d, h', a, k, len
     "128f": (16, 22, 3, 6, 33, 35), "192f": (24, 22, 3, 8, 33, 51), "256f": (32, 17, 4, 9, 35, 67),
@@ -111,7 +112,7 @@ def _step_alu(nw, ctx=True):
     """ALU ops of one one-block F / PRF compression over nw payload words."""
     s1 = 48 - 2
     s0 = 48 - (9 - nw) - 1 - (4 if ctx else 0)
-    return (59 if ctx else 64) * 10 + 4 * (s1 + s0)
+    return (58 if ctx else 64) * 10 + 4 * (s1 + s0)
 
 
 def exec_alu_per_sig(ps, stage):
@@ -123,7 +124,7 @@ def exec_alu_per_sig(ps, stage):
     nw, big = n // 4, n > 16
     c_blk = ALU_C512 if big else ALU_C256
     if stage == "tree":
-        chain = 2 * (5 * 10 + 4 * 4) + 16 * _step_alu(nw)
+        chain = 2 * (6 * 10 + 4 * 4) + 16 * _step_alu(nw)
         tl_blocks = -(-(22 + length * n + (17 if big else 9)) // (128 if big else 64))
         leaves = d * (1 << hp)
         return leaves * (length * chain + tl_blocks * c_blk) + d * ((1 << hp) - 1) * c_blk
@@ -354,7 +355,7 @@ def sha_mix_roofline(mix, sm_count, mhz, ps, count, ms, alu_rate):
            "basis": "hs_probe_sha_mix: the signer's SHA-256 round code (64 rounds unrolled, additions on "
                     "IMAD) and SHA-512 compression (16 rounds x 5) back to back per thread, one "
                     "full-occupancy wave, SM cycle counters; the kernel's executed work priced at those "
-                    "rates (chain steps as 926-942 / 1024 of a compression)"}
+                    "rates (chain steps as 916-932 / 1024 of a compression)"}
     if ps in SET_SHAPE and ms > 0:
         out["tree_frac"] = round(sha_mix_time_ms(ps, "tree", count, mix, sm_count, mhz) / ms, 4)
     return out
@@ -865,7 +866,7 @@ def run_own(args):
                 "issue_frac": round(issue_achieved / issue_peak, 4) if issue_achieved else None,
                 "peak_basis": "ALU pipe %.1f lane-ops/clk/SM (measured LOP3/SHF rate) x %d SMs x %.0f MHz"
                               % (alu_rate, sm_count, sm_mhz_peak),
-                "work_basis": "ALU-pipe ops as executed: chain steps run rounds 5..63 with sigma terms of "
+                "work_basis": "ALU-pipe ops as executed: chain steps run rounds 6..63 with sigma terms of "
                               "constant words folded (%d per 128f step), T_len / H in full (%d per SHA-256 "
                               "block, %d per SHA-512); %.4g per launch; frac_full_compression prices every "
                               "compression in full (%.4g per launch)"

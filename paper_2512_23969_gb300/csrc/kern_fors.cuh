@@ -130,9 +130,10 @@ __global__ void __launch_bounds__(256) fors_kernel(const KeyBlock* __restrict__ 
     // Leaf hashes with a chain context: PRF and F of every leaf of this
     // message share address words 0..4 (layer, tree, type, key pair, height
     // 0 and the top half of the leaf index, which is 0 while k * 2^a <=
-    // 2^16), so rounds 0..4 of each are computed once here and a leaf hash
-    // runs rounds 5..63 -- the same compression as the chain steps of
-    // TREE_Sign, bit for bit.  The two contexts are read at a run-time
+    // 2^16), so rounds 0..4 of each (and round 5 up to its message word)
+    // are computed once here and a leaf hash runs rounds 6..63 -- the same
+    // compression as the chain steps of TREE_Sign, bit for bit.  The two
+    // contexts are read at a run-time
     // index (local memory): 60 registers instead of 79 for a register
     // select, and as fast or faster (FORS 128f 6.39 -> 6.19 ms, 256f 45.2
     // -> 43.6 ms per 16384 / 8192 signatures).

@@ -12,9 +12,10 @@
 //
 // WOTS+ chains: within one chain every F call has the same first 5 message
 // words (the compressed address up to the hash index), so the state after
-// rounds 0..4 and the address-only parts of message words 16..20 are
-// computed once per chain (ChainCtx) and each of the chain's F steps runs
-// rounds 5..63 only.  The result is the same compression, bit for bit.
+// rounds 0..4, round 5 up to its message word, and the address-only parts
+// of message words 16..20 are computed once per chain (ChainCtx); each of
+// the chain's F steps adds W_5 into round 5's two sums and runs rounds
+// 6..63.  The result is the same compression, bit for bit.
 #pragma once
 #include <cstdint>
 #include "hs_common.cuh"
@@ -113,9 +114,12 @@ struct Rounds256 {
     }
 };
 
-// Chain-invariant part of an F call: state after rounds 0..4 (from the key
-// midstate, message words 0..4 = the address words) and the address-only
-// terms of message words 16..20.
+// Chain-invariant part of an F call: the state after rounds 0..4 (from the
+// key midstate, message words 0..4 = the address words) with round 5
+// applied except for its message word -- in the rotating layout of round 5,
+// s[6] = d + T1' and s[2] = T1' + T2 with T1' = h + Sigma1(e) + Ch(e, f, g)
+// + K_5, so that adding W_5 to both gives the new e and a -- and the
+// address-only terms of message words 16..20.
 struct ChainCtx {
     uint32_t s[8];
     uint32_t c[5];
@@ -132,6 +136,13 @@ __device__ __forceinline__ void chain_ctx(const uint32_t ms[8], const Adrs& a, C
     round256<POL, 2>(x.s, W[2], p);
     round256<POL, 3>(x.s, W[3], p);
     round256<POL, 4>(x.s, W[4], p);
+    {   // round 5 without W_5 (a = s[3], b = s[4], c = s[5], d = s[6], e = s[7], f = s[0], g = s[1], h = s[2])
+        const uint32_t e = x.s[7], f = x.s[0], g = x.s[1], a = x.s[3], b = x.s[4], c = x.s[5];
+        const uint32_t t1 = x.s[2] + S1_256(e) + ((e & f) ^ (~e & g)) + detail::kK256[5];
+        const uint32_t t2 = S0_256(a) + ((a & b) | (c & (a | b)));
+        x.s[6] += t1;
+        x.s[2] = t1 + t2;
+    }
     x.c[0] = s0_256(W[1]) + W[0];
     x.c[1] = s0_256(W[2]) + W[1];
     x.c[2] = s0_256(W[3]) + W[2];
@@ -255,7 +266,9 @@ __device__ __forceinline__ void chain_step(const ChainCtx& cx, const uint32_t ms
     uint32_t v[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) v[i] = cx.s[i];
-    Rounds256<POL, true, 5, 64>::run(v, W, cx.c, p);
+    v[6] = mad_add(v[6], W[5], p.one);            // round 5: its message word
+    v[2] = mad_add(v[2], W[5], p.one);
+    Rounds256<POL, true, 6, 64>::run(v, W, cx.c, p);
 #pragma unroll
     for (int i = 0; i < NW; i++) out[i] = v[i] + ms[i];
 }
