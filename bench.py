@@ -101,18 +101,29 @@ KECCAK_WORK = {"shake-128f": _keccak_work(16, 22, 3, 6, 33, 35), "shake-192f": _
 #  * its message words 6 + n/4 .. 14 are zero and word 15 is a constant, so
 #    their sigma0 / sigma1 terms fold away in the unrolled schedule.
 # So one such step costs 58 x 10 + 4 x (46 sigma1 + 34 + n/4 sigma0) ALU
-# ops, and a chain 2 contexts (6 x 10 + 4 x 4 each) plus 16 steps.  T_l, H
-# and T_k run the rolled compression in full (1024 / 2624 per block).
+# ops (at n = 16 two sigma1 fewer: words 17 and 19 depend on the address
+# alone and come from the context too), and a chain 2 contexts (6 x 10 +
+# 4 x 4 each, + 8 at n = 16) plus 16 steps.  T_l, H and T_k run the rolled
+# compression in full (1024 / 2624 per block).
 SET_SHAPE = {  # n, d, h', a, k, len
     "128f": (16, 22, 3, 6, 33, 35), "192f": (24, 22, 3, 8, 33, 51), "256f": (32, 17, 4, 9, 35, 67),
     "128s": (16, 7, 9, 12, 14, 35), "192s": (24, 7, 9, 14, 17, 51), "256s": (32, 8, 8, 14, 22, 67)}
 
 
 def _step_alu(nw, ctx=True):
-    """ALU ops of one one-block F / PRF compression over nw payload words."""
-    s1 = 48 - 2
+    """ALU ops of one one-block F / PRF compression over nw payload words
+    (at n = 16 the context also holds sigma1 of message words 17 and 19,
+    which depend on the address alone when words 10..14 are zero)."""
+    s1 = 48 - 2 - (2 if ctx and nw == 4 else 0)
     s0 = 48 - (9 - nw) - 1 - (4 if ctx else 0)
     return (58 if ctx else 64) * 10 + 4 * (s1 + s0)
+
+
+def _ctx_alu(nw):
+    """ALU ops of one chain context: rounds 0..5 (round 5 up to its message
+    word), sigma0 of message words 1..4, and at n = 16 sigma1 of words 17
+    and 19."""
+    return 6 * 10 + 4 * 4 + (8 if nw == 4 else 0)
 
 
 def exec_alu_per_sig(ps, stage):
@@ -124,7 +135,7 @@ def exec_alu_per_sig(ps, stage):
     nw, big = n // 4, n > 16
     c_blk = ALU_C512 if big else ALU_C256
     if stage == "tree":
-        chain = 2 * (6 * 10 + 4 * 4) + 16 * _step_alu(nw)
+        chain = 2 * _ctx_alu(nw) + 16 * _step_alu(nw)
         tl_blocks = -(-(22 + length * n + (17 if big else 9)) // (128 if big else 64))
         leaves = d * (1 << hp)
         return leaves * (length * chain + tl_blocks * c_blk) + d * ((1 << hp) - 1) * c_blk
@@ -355,7 +366,7 @@ def sha_mix_roofline(mix, sm_count, mhz, ps, count, ms, alu_rate):
            "basis": "hs_probe_sha_mix: the signer's SHA-256 round code (64 rounds unrolled, additions on "
                     "IMAD) and SHA-512 compression (16 rounds x 5) back to back per thread, one "
                     "full-occupancy wave, SM cycle counters; the kernel's executed work priced at those "
-                    "rates (chain steps as 916-932 / 1024 of a compression)"}
+                    "rates (chain steps as 908-932 / 1024 of a compression)"}
     if ps in SET_SHAPE and ms > 0:
         out["tree_frac"] = round(sha_mix_time_ms(ps, "tree", count, mix, sm_count, mhz) / ms, 4)
     return out

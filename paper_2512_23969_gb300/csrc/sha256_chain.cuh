@@ -87,11 +87,20 @@ __device__ __forceinline__ void round256(uint32_t v[8], uint32_t w, const Pipes<
 
 // Rounds [t0, t1) with the message schedule extended in the 16-word ring W.
 // PRE: words 0..4 are replaced by the chain constants c[] in words 16..20.
-template <int POL, bool PRE, int t0, int t1>
+// K16 (PRE, one-block calls at n = 16, whose words 10..14 are zero and 15
+// the constant length): words 17 and 19 and sigma1(W_19) depend on the
+// chain's address alone and come from k[0..2].
+template <int POL, bool PRE, int t0, int t1, bool K16 = false>
 struct Rounds256 {
-    __device__ static __forceinline__ void run(uint32_t v[8], uint32_t W[16], const uint32_t* c, const Pipes<POL>& p) {
+    __device__ static __forceinline__ void run(uint32_t v[8], uint32_t W[16], const uint32_t* c, const Pipes<POL>& p,
+                                               const uint32_t* k = nullptr) {
         constexpr int t = t0;
-        if constexpr (t >= 16 && (POL & 8)) {
+        if constexpr (K16 && (t == 17 || t == 19)) {
+            W[t & 15] = k[(t - 17) / 2];
+        } else if constexpr (K16 && t == 21) {   // sigma1(W19) + W14 (= 0) + sigma0(W6) + W5
+            if constexpr (POL & 8) W[t & 15] = mad_add(mad_add(k[2], s0_256(W[6]), p.one), W[5], p.one);
+            else W[t & 15] = k[2] + s0_256(W[6]) + W[5];
+        } else if constexpr (t >= 16 && (POL & 8)) {
             const uint32_t a = mad_add(s1_256(W[(t - 2) & 15]), W[(t - 7) & 15], p.one);
             if constexpr (PRE && t <= 19) {
                 W[t & 15] = mad_add(a, c[t - 16], p.one);
@@ -110,7 +119,7 @@ struct Rounds256 {
             }
         }
         round256<POL, t>(v, W[t & 15], p);
-        if constexpr (t0 + 1 < t1) Rounds256<POL, PRE, t0 + 1, t1>::run(v, W, c, p);
+        if constexpr (t0 + 1 < t1) Rounds256<POL, PRE, t0 + 1, t1, K16>::run(v, W, c, p, k);
     }
 };
 
@@ -119,10 +128,13 @@ struct Rounds256 {
 // applied except for its message word -- in the rotating layout of round 5,
 // s[6] = d + T1' and s[2] = T1' + T2 with T1' = h + Sigma1(e) + Ch(e, f, g)
 // + K_5, so that adding W_5 to both gives the new e and a -- and the
-// address-only terms of message words 16..20.
+// address-only terms of message words 16..20; and for the n = 16 block
+// (words 10..14 zero, word 15 the length 816) the address-only words 17
+// and 19 and sigma1(W_19) in k[].
 struct ChainCtx {
     uint32_t s[8];
     uint32_t c[5];
+    uint32_t k[3];
 };
 
 template <int POL>
@@ -148,6 +160,12 @@ __device__ __forceinline__ void chain_ctx(const uint32_t ms[8], const Adrs& a, C
     x.c[2] = s0_256(W[3]) + W[2];
     x.c[3] = s0_256(W[4]) + W[3];
     x.c[4] = W[4];
+    // n = 16: W17 = sigma1(W15) + W10 + c[1], W19 = sigma1(W17) + W12 + c[3]
+    // (unused, and removed by the compiler, at the other widths)
+    constexpr uint32_t kLen16 = (64 + 22 + 16) * 8;
+    x.k[0] = s1_256(kLen16) + x.c[1];
+    x.k[1] = s1_256(x.k[0]) + x.c[3];
+    x.k[2] = s1_256(x.k[1]);
 }
 
 // ---- robust F masks with a per-chain context --------------------------
@@ -268,7 +286,7 @@ __device__ __forceinline__ void chain_step(const ChainCtx& cx, const uint32_t ms
     for (int i = 0; i < 8; i++) v[i] = cx.s[i];
     v[6] = mad_add(v[6], W[5], p.one);            // round 5: its message word
     v[2] = mad_add(v[2], W[5], p.one);
-    Rounds256<POL, true, 6, 64>::run(v, W, cx.c, p);
+    Rounds256<POL, true, 6, 64, NW == 4>::run(v, W, cx.c, p, cx.k);
 #pragma unroll
     for (int i = 0; i < NW; i++) out[i] = v[i] + ms[i];
 }

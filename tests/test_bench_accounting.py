@@ -86,10 +86,14 @@ def _enumerated_step_alu(nw, ctx):
     constant bit length.  Sigma / sigma terms of a known word cost nothing."""
     known = set(range(6 + nw, 15)) | {15}
     hoisted = {1, 2, 3, 4} if ctx else set()
+    # W17 = sigma1(W15) + W10 + sigma0(W2) + W1 and W19 = sigma1(W17) + W12 +
+    # sigma0(W4) + W3 involve the address and known words only when words
+    # 10 and 12 are zero (nw = 4): their sigma1 terms come from the context
+    addr_only = {17, 19} if ctx and all(w in known for w in (10, 12)) else set()
     rounds = range(6, 64) if ctx else range(64)
     ops = 10 * len(rounds)                         # Sigma0, Sigma1 (4 each), Ch, Maj
     for t in range(16, 64):
-        if (t - 2) not in known:
+        if (t - 2) not in known and (t - 2) not in addr_only:
             ops += 4                               # sigma1(W[t-2])
         if (t - 15) not in known and (t - 15) not in hoisted:
             ops += 4                               # sigma0(W[t-15])
@@ -107,9 +111,9 @@ def test_executed_alu_never_exceeds_full_basis():
     for ps in SHA:
         for st in ("tree", "fors"):
             e, f = bench.exec_alu_per_sig(ps, st), bench.alu_ops_per_sig(ps, st)
-            assert 0.9 * f < e <= f, (ps, st)
-    # 128f TREE: 176 leaves x (35 chains x (2 x 76 + 16 x 916) + 10 x 1024) + 154 x 1024
-    assert bench.exec_alu_per_sig("128f", "tree") == 176 * (35 * (2 * 76 + 16 * 916) + 10 * 1024) + 154 * 1024
+            assert 0.85 * f < e <= f, (ps, st)      # the contexts skip at most 7 rounds' worth
+    # 128f TREE: 176 leaves x (35 chains x (2 x 84 + 16 x 908) + 10 x 1024) + 154 x 1024
+    assert bench.exec_alu_per_sig("128f", "tree") == 176 * (35 * (2 * 84 + 16 * 908) + 10 * 1024) + 154 * 1024
 
 
 def test_summary_lists_headline_figures():
