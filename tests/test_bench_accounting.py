@@ -129,3 +129,27 @@ def test_summary_lists_headline_figures():
     assert sm["plain_per_stage_sig_per_s"] == 0.8
     assert sm["serving_rho_0.75"]["p99_ms"] == 2 and sm["serving_sustained"]["rho"] == 0.9
     assert sm["mixed_small_ms"] == {"plain_per_set_calls": 1.5}
+
+
+def test_sha_mix_pricing():
+    """The SHA-2 mix fraction prices a stage's executed SHA-256 ALU work in
+    compression equivalents (1024 each) at the probe's SHA-256 rate and its
+    SHA-512 blocks at the probe's SHA-512 rate: a kernel running exactly at
+    the probe's rates reads 1.0."""
+    mix = {"sha256_per_clk_sm": 0.05, "sha512_per_clk_sm": 0.02}
+    sms, mhz, count = 152, 2000.0, 1000
+    for ps in SHA:
+        for st in ("tree", "fors"):
+            alu256, c512 = bench.exec_split_per_sig(ps, st)
+            assert alu256 + c512 * bench.ALU_C512 == bench.exec_alu_per_sig(ps, st)
+            per_s = lambda r: r * sms * mhz * 1e6
+            want_ms = 1e3 * count * (alu256 / 1024 / per_s(0.05) + c512 / per_s(0.02))
+            assert abs(bench.sha_mix_time_ms(ps, st, count, mix, sms, mhz) - want_ms) < 1e-9 * want_ms
+    ms = bench.sha_mix_time_ms("128f", "tree", count, mix, sms, mhz)
+    r = bench.sha_mix_roofline(dict(mix, sha256_plain_per_clk_sm=0.04), sms, mhz, "128f", count, ms, 64.0)
+    assert abs(r["tree_frac"] - 1.0) < 1e-4
+    assert r["alu_efficiency_of_mix"]["sha256"] == round(0.05 * 1024 / 64.0, 4)
+    assert r["alu_efficiency_of_mix"]["sha512"] == round(0.02 * 2624 / 64.0, 4)
+    # the SHA-512 sets' stages carry SHA-512 blocks, the n = 16 sets none
+    assert bench.exec_split_per_sig("128f", "fors")[1] == 0
+    assert bench.exec_split_per_sig("256f", "fors")[1] == bench.STAGE_WORK["256f"]["fors"][1]
