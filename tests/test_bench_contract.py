@@ -1,7 +1,7 @@
 """bench.py's reference arm (the CPU oracle timed on the host cores) prints
 exactly one JSON line carrying the keys of the bench contract, and under a
-multi-rank launch only rank 0 prints; the GPU arm's line is checked on the
-GPU by the driver's own run."""
+multi-rank launch only rank 0 prints.  The GPU arm's line needs a GPU and
+is not checked here."""
 import json
 import os
 import subprocess
